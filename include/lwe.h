@@ -1,0 +1,218 @@
+/*
+ * lwe.h -- C ABI of the GB300 (sm_103a) plain-LWE KEM library (liblwe.so).
+ *
+ * The scheme is the plain-LWE key encapsulation mechanism of arxiv
+ * 2606.01211 (Liberati et al.), Sec. 2.1, Alg. 1-5, written in matrix form
+ * with nbar = mbar = 8:
+ *
+ *   KeyGen   (Alg. 1):  A <- sample(seedA);  S, E <- chi;  B = A S + E mod q
+ *   Encrypt  (Alg. 2):  S', E', E'' <- chi;  B' = S' A + E';  V = S' B + E'';
+ *                       C = V + Enc(mu)
+ *   Decrypt  (Alg. 3):  M = C - B' S;  mu = Dec(M)
+ *   Encaps   (Alg. 4):  c = Encrypt(pk, mu);  K = H(H(H(pk) || mu) || H(c))
+ *   Decaps   (Alg. 5):  re-encrypt and compare; on mismatch K = H(z || H(c))
+ *                       (Fujisaki-Okamoto transform with implicit rejection)
+ *
+ * q = 2^logq.  A is expanded from a 16-byte seed with AES-128 in counter
+ * mode on the device (Sec. 3.3: device-resident random number generation);
+ * the noise is drawn from a rounded-Gaussian CDF table by inverse sampling
+ * of the same kind of counter stream.
+ *
+ * Conventions shared by every entry point below:
+ *   - Every buffer argument is a DEVICE pointer (cudaMalloc'd or a torch
+ *     tensor's storage) owned by the caller, unless marked "host".  The
+ *     library never frees or keeps caller buffers.
+ *   - Buffers must be 16-byte aligned.  Misaligned or NULL required
+ *     pointers return LWE_EINVAL before anything is launched.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Every call is asynchronous on that stream: results are
+ *     valid once the stream has been synchronised.  The calls enqueue work
+ *     and return; they never synchronise the device and never allocate
+ *     device memory (workspaces belong to the lwe_ctx and are sized when it
+ *     is created).
+ *   - Return value: LWE_OK (0) or a negative LWE_E* code.  Launch failures
+ *     surface as LWE_ECUDA (the CUDA error string is kept for
+ *     lwe_last_cuda_error()).  Waits inside kernels are bounded; a wait that
+ *     runs out sets the context's device error word (LWE_ETIMEOUT), read by
+ *     lwe_ctx_device_error().
+ *   - Byte layouts (all integers little-endian):
+ *       pk = seedA[16] || B (n x 8 uint16, row-major)
+ *       sk = S^T (8 x n int8, row-major) || z[32] || H(pk)[32] || pk
+ *       ct = B' (8 x n uint16, row-major) || C (8 x 8 uint16, row-major)
+ *       K  = 32 bytes
+ *     Batches are these objects back to back (item i at i * size).
+ *   - The library requires n % 16 == 0 and 16 <= n <= 65536.
+ */
+#ifndef LWE_H
+#define LWE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define LWE_OK 0
+#define LWE_EINVAL (-1)       /* bad argument, size, pointer or alignment */
+#define LWE_ENOMEM (-2)       /* workspace allocation failed (create only)  */
+#define LWE_ECUDA (-3)        /* a CUDA runtime call or launch failed       */
+#define LWE_ETIMEOUT (-4)     /* a bounded device wait ran out              */
+#define LWE_EUNSUPPORTED (-5) /* not supported on this device               */
+#define LWE_ECAPACITY (-6)    /* count exceeds the context's max_batch      */
+
+/* ---- parameters (Sec. 2.2; the values of the presets are the workloads'
+ *      parameter sets, each with nbar = mbar = 8) -------------------------- */
+typedef struct lwe_params {
+  uint32_t n;     /* LWE dimension                                         */
+  uint32_t nbar;  /* columns of S, must be 8                               */
+  uint32_t mbar;  /* rows of S', must be 8                                 */
+  uint32_t logq;  /* q = 2^logq, 2..16                                     */
+  uint32_t B;     /* message bits per coefficient of C, 1..4, B < logq    */
+  uint32_t clip;  /* noise bound c: samples lie in [-c, c], 1..15          */
+  double sigma;   /* standard deviation of the rounded Gaussian           */
+} lwe_params;
+
+enum {
+  LWE_P640 = 0,   /* n=640,   q=2^15, sigma=2.8, c=12, B=2 */
+  LWE_P976 = 1,   /* n=976,   q=2^16, sigma=2.3, c=10, B=3 */
+  LWE_P1344 = 2,  /* n=1344,  q=2^16, sigma=1.4, c=6,  B=4 */
+  LWE_P4096 = 3,  /* n=4096,  q=2^16, sigma=2.8, c=12, B=2 */
+  LWE_P16384 = 4, /* n=16384, q=2^16, sigma=2.8, c=12, B=1 */
+  LWE_P32768 = 5  /* n=32768, q=2^16, sigma=2.8, c=12, B=1 */
+};
+
+/* Fill *out with preset `id`.  Host only.  LWE_EINVAL for an unknown id. */
+int lwe_params_preset(int id, lwe_params *out);
+
+/* LWE_OK when *p is usable by this library (see the ranges above and the
+ * table condition of lwe_cdf_table).  Host only. */
+int lwe_params_check(const lwe_params *p);
+
+/* The inverse-sampling table of the noise distribution (Sec. 2.2, Tab. 1:
+ * Gaussian noise of width sigma).  Reading of the paper: p(k) is the mass
+ * of N(0, sigma^2) on [k - 1/2, k + 1/2] for |k| <= c, renormalised;
+ * T[k] = round_half_up(2^15 * (p(0) + 2 sum_{j=1..k} p(j))) - 1, k < c.
+ * A sample takes a 16-bit word w: t = w >> 1, |e| = #{k : t > T[k]},
+ * e < 0 iff w & 1.  Host only; writes T[0..clip-1].  LWE_EINVAL if the
+ * table is not strictly increasing or its last entry reaches 2^15 - 1. */
+int lwe_cdf_table(const lwe_params *p, uint16_t T[16]);
+
+/* Object sizes in bytes. Host only. */
+size_t lwe_pk_bytes(const lwe_params *p);
+size_t lwe_sk_bytes(const lwe_params *p);
+size_t lwe_ct_bytes(const lwe_params *p);
+
+/* ---- context ----------------------------------------------------------- */
+typedef struct lwe_ctx lwe_ctx;
+
+/* Create a context for parameters *p on CUDA device `device`, with
+ * workspaces for up to `max_batch` items per call (>= 1).  This is the only
+ * call that allocates device memory; it also uploads the AES table to the
+ * device and must not run during stream capture.  *out is set to NULL on
+ * failure.  Returns LWE_EINVAL, LWE_ENOMEM, LWE_ECUDA or LWE_EUNSUPPORTED
+ * (device is not sm_103). */
+int lwe_ctx_create(const lwe_params *p, uint32_t max_batch, int device,
+                   lwe_ctx **out);
+/* Free the context and its workspaces (synchronises the device first).
+ * NULL is accepted. */
+int lwe_ctx_destroy(lwe_ctx *ctx);
+
+/* Product path for Encrypt's S' A (Alg. 2): */
+enum {
+  LWE_PATH_AUTO = 0,   /* tensor path when count >= the tuned threshold  */
+  LWE_PATH_SKINNY = 1, /* per-item CUDA-core kernels ("plain" path)      */
+  LWE_PATH_TENSOR = 2  /* stacked S' as one exact two-limb bf16 tcgen05
+                          GEMM (tensor cores, fp32 accumulation)          */
+};
+enum {
+  LWE_OPT_PATH = 0,          /* one of LWE_PATH_*                             */
+  LWE_OPT_TENSOR_MIN = 1,    /* AUTO threshold (items per call), default 64   */
+  LWE_OPT_TIMING = 2,        /* 1: time every launch with CUDA events          */
+  LWE_OPT_GEMM_BN = 3        /* GEMM output-column tile: 64 or 128 (default)  */
+};
+int lwe_ctx_set_option(lwe_ctx *ctx, int option, int64_t value);
+
+/* ---- KEM (Alg. 1, 4, 5) ------------------------------------------------ */
+
+/* KeyGen, Alg. 1, for `count` independent key pairs.
+ *   seeds  [count][32]         master seeds.  Derived: seedA =
+ *                              H(0x41||ms)[0:16], seedSE = H(0x53||ms)[0:16],
+ *                              z = H(0x5A||ms) with H = SHA3-256.
+ *   pk     [count][pk_bytes]   output.
+ *   sk     [count][sk_bytes]   output.
+ *   A_out  [count][n][n] uint16, nullable: when given, A is written there
+ *          (stored mode); when NULL it is regenerated inside the product and
+ *          never stored (Sec. 3.5, Sec. 4.3: on-demand generation of A).
+ * count == 0 is a no-op.  count > max_batch returns LWE_ECAPACITY. */
+int lwe_keygen(lwe_ctx *ctx, const uint8_t *seeds, uint32_t count,
+               uint8_t *pk, uint8_t *sk, uint16_t *A_out, void *stream);
+
+/* Encaps, Alg. 4 (with Encrypt of Alg. 2), `count` encapsulations against
+ * ONE public key.
+ *   pk     [pk_bytes]           public key.
+ *   A      [n][n] uint16, nullable: the expansion of pk's seedA (stored
+ *          mode); NULL regenerates A on the fly.
+ *   coins  [count][32]          randomness: mu = H(0x4D||coins)[0:8B bytes].
+ *   ct     [count][ct_bytes]    output ciphertexts.
+ *   K      [count][32]          output shared keys. */
+int lwe_encaps(lwe_ctx *ctx, const uint8_t *pk, const uint16_t *A,
+               const uint8_t *coins, uint32_t count, uint8_t *ct, uint8_t *K,
+               void *stream);
+
+/* Decaps, Alg. 5 (with Decrypt of Alg. 3), `count` decapsulations with ONE
+ * secret key.  Constant time in the validity of each ciphertext: the
+ * re-encryption is compared with a branch-free OR of differences and the
+ * key material is selected by masking (implicit rejection, Sec. 2.1).
+ *   sk  [sk_bytes];  A as in lwe_encaps (pk is taken from inside sk);
+ *   ct  [count][ct_bytes];  K [count][32] output. */
+int lwe_decaps(lwe_ctx *ctx, const uint8_t *sk, const uint16_t *A,
+               const uint8_t *ct, uint32_t count, uint8_t *K, void *stream);
+
+/* ---- standalone hot-path kernels --------------------------------------- */
+
+/* sample(seedA) of Alg. 1: A[i][j..j+7] = the eight little-endian 16-bit
+ * words of AES-128_{seedA}(BE64(0) || BE64(i*n/8 + j/8)), each masked to
+ * logq bits.  seedA [16] device; A_out [n][n] uint16 device.
+ * Written with coalesced 16-byte stores.  Needs no context. */
+int lwe_expand_A(const uint8_t *seedA, uint32_t n, uint32_t logq,
+                 uint16_t *A_out, void *stream);
+
+/* The mod-q products of Alg. 1-2 on their own (q = 2^logq):
+ *   side LWE_SIDE_AS:  out[n][k]  = A S  + E,  S given as S^T [k][n] int8,
+ *                      E [n][k] int8 (nullable); k must be 8.
+ *   side LWE_SIDE_SA:  out[k][n]  = S A  + E,  S [k][n] int8,
+ *                      E [k][n] int8 (nullable); k a multiple of 8
+ *                      (k = 8 * stacked encryptions).
+ * A [n][n] uint16, or NULL to regenerate it from seedA [16] (device) tile
+ * by tile inside the product, never storing it.  ctx: nullable; when given
+ * (and its n equals n and its max_batch covers k/8), SA may take the
+ * tensor-core path and its workspace; otherwise the CUDA-core kernels run. */
+enum { LWE_SIDE_AS = 0, LWE_SIDE_SA = 1 };
+int lwe_matmul_modq(lwe_ctx *ctx, int side, const uint16_t *A,
+                    const uint8_t *seedA, const int8_t *S, uint32_t n,
+                    uint32_t k, uint32_t logq, const int8_t *E,
+                    uint16_t *out, void *stream);
+
+/* ---- diagnostics ------------------------------------------------------- */
+const char *lwe_strerror(int code);
+/* The last CUDA error string seen by this thread's calls ("" if none). */
+const char *lwe_last_cuda_error(void);
+/* Synchronises the device, returns LWE_OK or the device error word set by
+ * a bounded wait (LWE_ETIMEOUT), and clears it. */
+int lwe_ctx_device_error(lwe_ctx *ctx);
+/* Number of kernels this context has launched so far. */
+uint64_t lwe_ctx_launches(const lwe_ctx *ctx);
+/* Per-kernel event timing (needs LWE_OPT_TIMING = 1; synchronises). */
+int lwe_ctx_kernel_stats(lwe_ctx *ctx, int kernel_id, uint64_t *launches,
+                         double *total_ms);
+int lwe_ctx_reset_stats(lwe_ctx *ctx);
+/* Name of kernel id 0..lwe_num_kernels()-1, NULL out of range. */
+const char *lwe_kernel_name(int kernel_id);
+int lwe_num_kernels(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LWE_H */

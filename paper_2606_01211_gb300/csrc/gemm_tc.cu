@@ -1,0 +1,434 @@
+// gemm_tc.cu -- exact mod-2^D product S' [A | B] on the sm_103a tensor cores.
+//
+// Batching many encryptions against one public key stacks their S' (Alg. 2)
+// into one tall matrix, so that B' = S' A + E' and V = S' B + E'' become one
+// dense contraction with K = n.  sm_103a has no integer tcgen05 MMA, so the
+// product is made exact on the bf16 path:
+//
+//   A[i][c] = lo + 256 hi (mod 2^16),  lo, hi in [-128, 127] (bf16-exact)
+//   S'[r][i] in [-c, c]                                       (bf16-exact)
+//   P_lo = S' lo,  P_hi = S' hi accumulate in fp32; every partial sum is an
+//   integer of magnitude <= n c 128 < 2^24, so fp32 holds it exactly.
+//   out = (P_lo + 256 P_hi + E) mod 2^D
+//
+// Kernel shape: persistent, one 128 x BN output tile at a time per CTA,
+// warp-specialised: warp 0 issues TMA loads of S' and limb tiles (128B
+// swizzle) into a 4-stage shared-memory ring, warp 1 issues tcgen05.mma
+// (M = 128, N = 2 BN: the lo and hi limb tiles side by side, K = 16) into one
+// of two TMEM accumulators, warps 2-5 drain the other accumulator with
+// tcgen05.ld, fold the limbs, add the noise (and the encoded message for the
+// C columns) and store -- or compare against a received ciphertext (Decaps).
+// Every mbarrier wait is bounded; a wait that runs out raises the context's
+// device error word and the CTA leaves cleanly.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include "common.cuh"
+#include "gemm_tc.h"
+
+namespace {
+
+constexpr int BM = 128;
+constexpr int BK = 64;  // bf16 elements = 128 bytes = one swizzle atom row
+constexpr int STAGES = 4;
+constexpr int NTHREADS = 192;
+constexpr uint64_t kTimeoutNs = 1000000000ull;  // 1 s per wait
+
+template <int BN>
+struct Cfg {
+  static constexpr int A_BYTES = BM * BK * 2;          // 16 KB
+  static constexpr int B_BYTES = 2 * BN * BK * 2;      // lo + hi tiles
+  static constexpr int STAGE_TX = A_BYTES + B_BYTES;
+  static constexpr int TMEM_COLS = 2 * (2 * BN);       // two accumulators
+  static constexpr int BAR_OFF = STAGES * (A_BYTES + B_BYTES);
+  static constexpr int SMEM = BAR_OFF + 256 + 1024;    // + barriers + align
+  // instruction descriptor, kind::f16: D f32, A/B bf16, K-major, N = 2 BN,
+  // M = 128
+  static constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) |
+                                    ((uint32_t)(2 * BN / 8) << 17) |
+                                    ((uint32_t)(BM / 16) << 24);
+};
+
+LWE_DEV uint32_t smem_u32(const void *p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+LWE_DEV uint64_t gtime() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+LWE_DEV void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+LWE_DEV void mbar_arrive_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+               : "memory");
+}
+
+LWE_DEV void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+LWE_DEV bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait: false when another role gave up or the limit ran out.
+LWE_DEV bool wait_bar(uint32_t bar, uint32_t parity, volatile uint32_t *abort_flag,
+                      uint32_t *dev_err) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = gtime();
+  while (true) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (*abort_flag) return false;
+    if (gtime() - t0 > kTimeoutNs) {
+      *abort_flag = 1;
+      atomicOr(dev_err, LWE_DEVERR_TIMEOUT);
+      return false;
+    }
+  }
+}
+
+LWE_DEV void tma_load_2d(uint32_t dst, const CUtensorMap *map, int c0, int c1, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(bar)
+      : "memory");
+}
+
+LWE_DEV void tma_load_3d(uint32_t dst, const CUtensorMap *map, int c0, int c1, int c2,
+                         uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(bar)
+      : "memory");
+}
+
+LWE_DEV void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+LWE_DEV void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// Shared-memory matrix descriptor (tcgen05 format): K-major, 128-byte
+// swizzle, 8-row core groups 1024 bytes apart (stride byte offset), version
+// bits 46-48 = 0b001, swizzle mode 2 (128B) in bits 61-63.
+LWE_DEV uint64_t sdesc(uint32_t saddr) {
+  return (uint64_t)((saddr & 0x3FFFF) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
+         ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
+
+LWE_DEV void mma_bf16(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                      uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(dtmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+LWE_DEV void mma_commit(uint32_t bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+      : "memory");
+}
+
+LWE_DEV void tmem_ld16(uint32_t taddr, uint32_t r[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+}
+
+LWE_DEV void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+LWE_DEV uint32_t fold(uint32_t lo_bits, uint32_t hi_bits) {
+  const int lo = __float2int_rn(__uint_as_float(lo_bits));
+  const int hi = __float2int_rn(__uint_as_float(hi_bits));
+  return (uint32_t)lo + ((uint32_t)hi << 8);
+}
+
+template <int BN>
+__global__ void __launch_bounds__(NTHREADS, 1)
+    k_gemm_sa(const __grid_constant__ CUtensorMap tmS, const __grid_constant__ CUtensorMap tmL,
+              const GemmSaArgs a) {
+  using C = Cfg<BN>;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
+                                              ~(uintptr_t)1023);
+  uint64_t *bars = reinterpret_cast<uint64_t *>(smem + C::BAR_OFF);
+  // bars: full[STAGES], empty[STAGES], tfull[2], tempty[2], done
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * STAGES + 5);
+  volatile uint32_t *abort_flag = tmem_slot + 1;
+
+  const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t num_m = (a.rows + BM - 1) / BM;
+  const uint32_t num_n = (a.ncols + BN - 1) / BN;
+  const uint32_t num_tiles = num_m * num_n;
+  const uint32_t KB = (a.n + BK - 1) / BK;
+
+  auto bar = [&](int i) { return smem_u32(bars + i); };
+  auto full = [&](uint32_t s) { return bar(s); };
+  auto empty = [&](uint32_t s) { return bar(STAGES + s); };
+  auto tfull = [&](uint32_t x) { return bar(2 * STAGES + x); };
+  auto tempty = [&](uint32_t x) { return bar(2 * STAGES + 2 + x); };
+  const uint32_t done_bar = bar(2 * STAGES + 4);
+  auto sA = [&](uint32_t s) { return smem_u32(smem + s * C::A_BYTES); };
+  auto sB = [&](uint32_t s) { return smem_u32(smem + STAGES * C::A_BYTES + s * C::B_BYTES); };
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; s++) {
+      mbar_init(full(s), 1);
+      mbar_init(empty(s), 1);
+    }
+    for (int x = 0; x < 2; x++) {
+      mbar_init(tfull(x), 1);
+      mbar_init(tempty(x), 4 * 32);
+    }
+    mbar_init(done_bar, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmS)) : "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmL)) : "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_slot)),
+                 "r"((uint32_t)C::TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+
+  if (warp == 0 && lane == 0) {
+    // ---------------- TMA producer ----------------
+    uint32_t stage = 0, phase = 0;
+    uint32_t issued = 0;  // bit s: stage s has a load in flight or done
+    uint32_t last_phase = 0;  // bit s: phase of stage s's last load
+    bool ok = true;
+    for (uint32_t tile = blockIdx.x; ok && tile < num_tiles; tile += gridDim.x) {
+      const int m0 = (int)((tile / num_n) * BM);
+      const int n0 = (int)((tile % num_n) * BN);
+      for (uint32_t kb = 0; kb < KB; kb++) {
+        if (!wait_bar(empty(stage), phase ^ 1, abort_flag, a.dev_err)) {
+          ok = false;
+          break;
+        }
+        mbar_arrive_expect_tx(full(stage), C::STAGE_TX);
+        tma_load_2d(sA(stage), &tmS, (int)(kb * BK), m0, full(stage));
+        tma_load_3d(sB(stage), &tmL, (int)(kb * BK), n0, 0, full(stage));
+        issued |= 1u << stage;
+        last_phase = (last_phase & ~(1u << stage)) | (phase << stage);
+        if (++stage == STAGES) {
+          stage = 0;
+          phase ^= 1;
+        }
+      }
+    }
+    if (!ok) {
+      // let every copy already issued land before the CTA leaves
+      for (uint32_t s = 0; s < STAGES; s++) {
+        if (!(issued & (1u << s))) continue;
+        const uint32_t ph = (last_phase >> s) & 1u;
+        const uint64_t t0 = gtime();
+        while (!mbar_try_wait(full(s), ph) && gtime() - t0 < kTimeoutNs) {
+        }
+      }
+    }
+  } else if (warp == 1 && lane == 0) {
+    // ---------------- MMA issuer ----------------
+    uint32_t stage = 0, phase = 0, it = 0;
+    bool ok = true;
+    for (uint32_t tile = blockIdx.x; ok && tile < num_tiles; tile += gridDim.x, ++it) {
+      const uint32_t acc = it & 1, use = it >> 1;
+      if (!wait_bar(tempty(acc), (use & 1) ^ 1, abort_flag, a.dev_err)) {
+        ok = false;
+        break;
+      }
+      tc_fence_after();
+      const uint32_t d = tmem_base + acc * (2 * BN);
+      for (uint32_t kb = 0; kb < KB; kb++) {
+        if (!wait_bar(full(stage), phase, abort_flag, a.dev_err)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const uint64_t ad = sdesc(sA(stage)), bd = sdesc(sB(stage));
+#pragma unroll
+        for (uint32_t kk = 0; kk < BK / 16; kk++)
+          mma_bf16(d, ad + 2 * kk, bd + 2 * kk, C::IDESC, (kb | kk) != 0);
+        mma_commit(empty(stage));
+        if (++stage == STAGES) {
+          stage = 0;
+          phase ^= 1;
+        }
+      }
+      if (ok) mma_commit(tfull(acc));
+    }
+    // all issued MMAs complete before TMEM is released
+    mma_commit(done_bar);
+    const uint64_t t0 = gtime();
+    while (!mbar_try_wait(done_bar, 0) && gtime() - t0 < kTimeoutNs) {
+    }
+  } else if (warp >= 2) {
+    // ---------------- epilogue ----------------
+    const uint32_t q = warp & 3;  // TMEM lane quarter of this warp
+    const uint32_t D = a.logq, mask = (1u << D) - 1u;
+    const uint32_t mm = mask | (mask << 16);
+    uint32_t it = 0;
+    for (uint32_t tile = blockIdx.x; tile < num_tiles; tile += gridDim.x, ++it) {
+      const uint32_t acc = it & 1, use = it >> 1;
+      if (!wait_bar(tfull(acc), use & 1, abort_flag, a.dev_err)) break;
+      tc_fence_after();
+      const uint32_t m0 = (tile / num_n) * BM, n0 = (tile % num_n) * BN;
+      const uint32_t row = m0 + 32 * q + lane;
+      const bool rv = row < a.rows;
+      const uint32_t e = row >> 3, kk = row & 7;
+      uint8_t *obase = a.out + (size_t)e * a.out_stride;
+      const uint32_t tl = tmem_base + ((32 * q) << 16) + acc * (2 * BN);
+      uint32_t diff = 0;
+#pragma unroll 1
+      for (uint32_t cc = 0; cc < BN / 16; cc++) {
+        const uint32_t c = n0 + 16 * cc;
+        uint32_t lo[16], hi[16];
+        tmem_ld16(tl + 16 * cc, lo);
+        tmem_ld16(tl + BN + 16 * cc, hi);
+        tmem_wait_ld();
+        if (!rv || c >= a.ncols) continue;
+        uint32_t v[16];
+#pragma unroll
+        for (int t = 0; t < 16; t++) v[t] = fold(lo[t], hi[t]);
+        if (c < a.n) {  // B' columns: 16 at once (n is a multiple of 16)
+          if (a.E) {
+            const uint4 ev = *reinterpret_cast<const uint4 *>(a.E + (size_t)row * a.n + c);
+            const uint32_t ew[4] = {ev.x, ev.y, ev.z, ev.w};
+#pragma unroll
+            for (int t = 0; t < 16; t++) v[t] += (uint32_t)sext8(ew[t >> 2], t & 3);
+          }
+          uint32_t w[8];
+#pragma unroll
+          for (int t = 0; t < 8; t++) w[t] = (v[2 * t] | (v[2 * t + 1] << 16)) & mm;
+          uint4 *o = reinterpret_cast<uint4 *>(obase + 2 * ((size_t)kk * a.n + c));
+          if (a.cmp) {
+            const uint4 o0 = o[0], o1 = o[1];
+            diff |= (o0.x ^ w[0]) | (o0.y ^ w[1]) | (o0.z ^ w[2]) | (o0.w ^ w[3]) |
+                    (o1.x ^ w[4]) | (o1.y ^ w[5]) | (o1.z ^ w[6]) | (o1.w ^ w[7]);
+          } else {
+            o[0] = make_uint4(w[0], w[1], w[2], w[3]);
+            o[1] = make_uint4(w[4], w[5], w[6], w[7]);
+          }
+        } else {  // V columns n..n+7: C = V + E'' + Enc(mu)
+          const uint32_t Bb = a.B;
+          const uint8_t *mu = a.mu + 32 * (size_t)e + kk * Bb;
+          uint32_t bits = 0;
+          for (uint32_t t = 0; t < Bb; t++) bits |= (uint32_t)mu[t] << (8 * t);
+          const int8_t *epp = a.Epp + 64 * (size_t)e + 8 * kk;
+          uint16_t *co = reinterpret_cast<uint16_t *>(obase + 16 * (size_t)a.n) + 8 * kk;
+#pragma unroll
+          for (int t = 0; t < 8; t++) {
+            const uint32_t sym = (bits >> (t * Bb)) & ((1u << Bb) - 1u);
+            const uint32_t cv = (v[t] + (uint32_t)(int)epp[t] + (sym << (D - Bb))) & mask;
+            if (a.cmp)
+              diff |= cv ^ (uint32_t)co[t];
+            else
+              co[t] = (uint16_t)cv;
+          }
+        }
+      }
+      tc_fence_before();
+      mbar_arrive(tempty(acc));
+      if (a.cmp) {
+        diff |= __shfl_xor_sync(0xffffffffu, diff, 1);
+        diff |= __shfl_xor_sync(0xffffffffu, diff, 2);
+        diff |= __shfl_xor_sync(0xffffffffu, diff, 4);
+        if (rv && kk == 0 && diff) atomicOr(a.flags + e, 1u);
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base),
+                 "r"((uint32_t)C::TMEM_COLS)
+                 : "memory");
+  }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+
+bool make_map(CUtensorMap *m, const void *base, int rank, const cuuint64_t *dims,
+              const cuuint64_t *strides, const cuuint32_t *box) {
+  cuuint32_t es[3] = {1, 1, 1};
+  CUresult r = g_encode(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, rank, const_cast<void *>(base), dims,
+                        strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                        CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+template <int BN>
+int launch_bn(const GemmSaArgs &a, int num_sms, cudaStream_t st) {
+  using C = Cfg<BN>;
+  CUtensorMap tmS, tmL;
+  const cuuint64_t dS[2] = {a.n, a.rows};
+  const cuuint64_t sS[1] = {2ull * a.n};
+  const cuuint32_t bS[2] = {BK, BM};
+  const cuuint64_t dL[3] = {a.n, a.ncols, 2};
+  const cuuint64_t sL[2] = {2ull * a.n, 2ull * a.n * a.ncols};
+  const cuuint32_t bL[3] = {BK, BN, 2};
+  if (!make_map(&tmS, a.S, 2, dS, sS, bS)) return LWE_ECUDA;
+  if (!make_map(&tmL, a.limbs, 3, dL, sL, bL)) return LWE_ECUDA;
+  const uint32_t tiles = ((a.rows + BM - 1) / BM) * ((a.ncols + BN - 1) / BN);
+  const int grid = (int)(tiles < (uint32_t)num_sms ? tiles : (uint32_t)num_sms);
+  k_gemm_sa<BN><<<grid, NTHREADS, C::SMEM, st>>>(tmS, tmL, a);
+  return LWE_OK;
+}
+
+}  // namespace
+
+cudaError_t lwe_gemm_setup() {
+  if (!g_encode) {
+    cudaDriverEntryPointQueryResult q;
+    void *fn = nullptr;
+    cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000,
+                                                     cudaEnableDefault, &q);
+    if (e != cudaSuccess) return e;
+    if (q != cudaDriverEntryPointSuccess || !fn) return cudaErrorNotSupported;
+    g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  }
+  cudaError_t e = cudaFuncSetAttribute(k_gemm_sa<128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       Cfg<128>::SMEM);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_gemm_sa<64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              Cfg<64>::SMEM);
+}
+
+// The fp32 accumulator is exact while n * c * 128 < 2^24.
+bool lwe_gemm_supported(uint32_t n, uint32_t logq, uint32_t clip) {
+  (void)logq;
+  return n >= 64 && (uint64_t)n * clip * 128u < (1u << 24);
+}
+
+int launch_gemm_sa(const GemmSaArgs &a, int num_sms, cudaStream_t st) {
+  if (!g_encode) return LWE_ECUDA;
+  if (a.rows == 0) return LWE_OK;
+  return a.bn == 64 ? launch_bn<64>(a, num_sms, st) : launch_bn<128>(a, num_sms, st);
+}

@@ -1,0 +1,42 @@
+// gemm_tc.h -- the batched Encrypt product on the tcgen05 tensor cores.
+// Internal to liblwe.so.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+// Operand B of the GEMM: the columns of [A | B] (A: n x n from the seed,
+// B: n x 8 of the public key) split into two signed 8-bit limbs,
+// x = lo + 256 hi (mod 2^16), stored as bf16, K-major: limbs[l][c][i].
+struct GemmLimbArgs {
+  const uint16_t *A;      // stored A (n x n) or NULL
+  const uint8_t *seedA;   // fused: 16-byte seed (device)
+  const uint8_t *B;       // n x 8 uint16 (public key matrix) or NULL
+  uint32_t n, logq;
+  uint16_t *limbs;        // bf16 bits, [2][ncols][n], ncols = n (+8 with B)
+};
+
+struct GemmSaArgs {
+  const uint16_t *S;      // bf16 bits, [rows][n] (stacked S', K-major)
+  const uint16_t *limbs;  // bf16 bits, [2][ncols][n]
+  const int8_t *E;        // [rows][n] int8 (E'), nullable
+  const int8_t *Epp;      // [rows/8][8][8] int8 (E''), for columns >= n
+  const uint8_t *mu;      // 32-byte message slot per item (rows/8 items)
+  uint8_t *out;           // item e at out + e * out_stride: rows k of n
+                          // uint16 (B'), then C (8 x 8 uint16) at +16 n
+  uint64_t out_stride;
+  uint32_t *flags;        // compare mode: atomicOr(flags[e], 1) on mismatch
+  uint32_t *dev_err;      // bounded waits that run out set bit 0
+  uint32_t n;             // K and the A column count
+  uint32_t ncols;         // n or n + 8
+  uint32_t rows;          // 8 * items
+  uint32_t logq, B;
+  int cmp;                // 0: write out; 1: compare with out
+  int bn;                 // output columns per tile: 64 or 128
+};
+
+cudaError_t lwe_gemm_setup();
+bool lwe_gemm_supported(uint32_t n, uint32_t logq, uint32_t clip);
+int launch_gemm_sa(const GemmSaArgs &a, int num_sms, cudaStream_t st);
+void launch_gemm_limbs(const GemmLimbArgs &a, int num_sms, cudaStream_t st);
+void launch_s_to_bf16(const int8_t *S, uint64_t count, uint16_t *out, int num_sms,
+                      cudaStream_t st);

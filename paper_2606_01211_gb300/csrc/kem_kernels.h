@@ -1,0 +1,139 @@
+// kem_kernels.h -- argument blocks and launch wrappers of the KEM kernels.
+// Internal to liblwe.so; the public boundary is include/lwe.h.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+// Long inputs (pk, c) are hashed as SHA3-256 of the concatenated SHA3-256
+// digests of their 1024-byte chunks (a fixed-shape two-level tree).
+#define LWE_TREE_CHUNK 1024
+
+enum { NOISE_I8 = 0, NOISE_BF16 = 1 };
+
+struct NoiseOut {
+  void *base;            // item e writes at base + e * item_stride (bytes)
+  uint64_t item_stride;  // bytes
+  uint32_t nsamples;     // samples per item, sample k from word k%8 of block k/8
+  uint32_t domain;       // counter-block domain
+  uint32_t fmt;          // NOISE_I8 or NOISE_BF16
+  uint32_t pad;
+};
+
+struct NoiseArgs {
+  const uint8_t *keys;  // item e key at keys + e * key_stride (16 bytes)
+  uint32_t key_stride;
+  uint32_t count;
+  uint32_t nout;
+  uint32_t pad;
+  NoiseOut out[3];
+  uint16_t T[16];  // CDF table, entries >= clip set to 0x7FFF
+};
+
+struct MulAsArgs {
+  const uint16_t *A;     // stored mode: A of item e at A + e * a_stride
+  uint64_t a_stride;     // elements
+  const uint8_t *seeds;  // fused mode: seedA of item e at seeds + e*seed_stride
+  uint32_t seed_stride;
+  uint32_t n;
+  uint32_t logq;
+  uint32_t pad;
+  const int8_t *St;      // S^T (8 x n) of item e at St + e * st_stride
+  uint64_t st_stride;
+  const int8_t *E;       // nullable, n x 8 of item e at E + e * e_stride
+  uint64_t e_stride;
+  uint8_t *out;          // row i (8 uint16) at out + e*out_stride + 16 i
+  uint64_t out_stride;
+  uint8_t *out2;         // nullable second copy
+  uint64_t out2_stride;
+};
+
+struct DecryptArgs {
+  const uint8_t *ct;     // item e at ct + e * ct_bytes
+  uint64_t ct_bytes;
+  const int8_t *St;      // one secret S^T (8 x n)
+  uint8_t *mu;           // 32-byte slot per item
+  uint32_t n, logq, B, pad;
+};
+
+struct MulSaArgs {
+  const uint16_t *A;     // stored A (n x n) or NULL
+  const uint8_t *seedA;  // fused: 16-byte seed (device)
+  uint32_t n;
+  uint32_t logq;
+  const int8_t *S;       // item e: S (8 x n) at S + e * s_stride
+  uint64_t s_stride;
+  const int8_t *E;       // nullable, item e: 8 x n at E + e * e_stride
+  uint64_t e_stride;
+  uint8_t *out;          // item e rows at out + e*out_stride + 2 k n (uint16)
+  uint64_t out_stride;
+  uint32_t *flags;       // compare mode: atomicOr(flags[e], 1) on mismatch
+};
+
+struct VEncArgs {
+  const uint8_t *pk;     // seedA || B (n x 8 uint16)
+  const int8_t *S;       // item e: S' (8 x n) at S + e * s_stride
+  uint64_t s_stride;
+  const int8_t *Epp;     // item e: E'' (8 x 8) at Epp + e * epp_stride
+  uint64_t epp_stride;
+  const uint8_t *mu;     // 32-byte slot per item
+  uint8_t *ct;           // item e at ct + e * ct_bytes; C at +16n
+  uint64_t ct_bytes;
+  uint32_t *flags;
+  uint32_t n, logq, B, pad;
+};
+
+struct KeygenSeedArgs {
+  const uint8_t *ms;     // count x 32
+  uint8_t *pk;
+  uint8_t *sk;
+  uint8_t *ws_seeds;     // count x 32: seedA || seedSE
+  uint64_t pk_bytes, sk_bytes;
+  uint64_t sk_z_off, sk_pk_off;
+  uint32_t count, pad;
+};
+
+struct DeriveArgs {
+  const uint8_t *coins;  // Encaps: count x 32; Decaps: NULL (mu given)
+  const uint8_t *pkh;    // 32 bytes
+  uint8_t *mu;           // 32-byte slot per item
+  uint8_t *kprime;       // 32 per item
+  uint8_t *seeds;        // 32-byte slot per item, seedSE' in the first 16
+  uint32_t count, mu_bytes;
+};
+
+struct TreeLeafArgs {
+  const uint8_t *msgs;   // item e at msgs + e * stride
+  uint64_t stride;
+  uint32_t len;          // bytes per item
+  uint32_t count;
+  uint8_t *leaves;       // [count][m][32]
+};
+
+enum { TREE_DIGEST = 0, TREE_ENC_KEY = 1, TREE_DEC_KEY = 2 };
+
+struct TreeRootArgs {
+  const uint8_t *leaves;
+  uint32_t m, count;
+  int mode, pad;
+  uint8_t *out;          // DIGEST: out + e*out_stride; keys: out + 32 e
+  uint64_t out_stride;
+  uint8_t *out2;
+  uint64_t out2_stride;
+  const uint8_t *kprime; // 32 per item
+  const uint8_t *z;      // Decaps: 32 bytes
+  const uint32_t *flags; // Decaps: mismatch flag per item
+};
+
+cudaError_t lwe_upload_aes_table(const uint32_t T0[256]);
+cudaError_t lwe_kernel_smem_setup();
+void launch_expand_A(const uint8_t *seeds, uint32_t seed_stride, uint32_t count, uint32_t n,
+                     uint32_t logq, uint16_t *A, uint64_t a_stride, int num_sms, cudaStream_t st);
+void launch_noise(const NoiseArgs &a, int num_sms, cudaStream_t st);
+void launch_mul_as(const MulAsArgs &a, uint32_t count, bool fused, cudaStream_t st);
+void launch_decrypt(const DecryptArgs &a, uint32_t count, cudaStream_t st);
+void launch_mul_sa(const MulSaArgs &a, uint32_t items, bool fused, bool cmp, cudaStream_t st);
+void launch_v_encode(const VEncArgs &a, uint32_t count, bool cmp, cudaStream_t st);
+void launch_keygen_seeds(const KeygenSeedArgs &a, cudaStream_t st);
+void launch_derive(const DeriveArgs &a, cudaStream_t st);
+void launch_tree_leaves(const TreeLeafArgs &a, cudaStream_t st);
+void launch_tree_root(const TreeRootArgs &a, cudaStream_t st);

@@ -1,0 +1,758 @@
+// lwe_api.cu -- host runtime behind the C ABI of include/lwe.h.
+//
+// Owns the parameter presets, the noise table, the AES table upload, the
+// contexts and their device workspaces, and the order of kernel launches
+// that makes up KeyGen, Encaps and Decaps (Alg. 1, 4, 5 of the paper).
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/lwe.h"
+#include "common.cuh"
+#include "gemm_tc.h"
+#include "kem_kernels.h"
+
+namespace {
+
+thread_local std::string g_last_cuda_error;
+
+int cuda_fail(cudaError_t e) {
+  g_last_cuda_error = cudaGetErrorString(e);
+  return LWE_ECUDA;
+}
+
+#define CUDA_TRY(x)                                 \
+  do {                                              \
+    cudaError_t _e = (x);                           \
+    if (_e != cudaSuccess) return cuda_fail(_e);    \
+  } while (0)
+
+bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
+
+// ---- AES round table T0, from the S-box of FIPS-197 ---------------------
+// S(x) = affine(x^-1) with the inverse taken through log / antilog tables
+// of the generator 3 of GF(2^8)*; T0[x] = 2S | S<<8 | S<<16 | 3S<<24.
+uint8_t gmul2(uint8_t a) { return (uint8_t)((a << 1) ^ ((a & 0x80) ? 0x1b : 0)); }
+
+void build_aes_T0(uint32_t T0[256]) {
+  uint8_t alog[256], logt[256];
+  uint8_t x = 1;
+  for (int i = 0; i < 255; i++) {
+    alog[i] = x;
+    logt[x] = (uint8_t)i;
+    x = (uint8_t)(x ^ gmul2(x));  // multiply by 3
+  }
+  for (int v = 0; v < 256; v++) {
+    uint8_t inv = v == 0 ? 0 : alog[(255 - logt[v]) % 255];
+    uint8_t s = inv;
+    for (int r = 1; r <= 4; r++) s ^= (uint8_t)((inv << r) | (inv >> (8 - r)));
+    s ^= 0x63;
+    uint8_t s2 = gmul2(s), s3 = (uint8_t)(s2 ^ s);
+    T0[v] = (uint32_t)s2 | ((uint32_t)s << 8) | ((uint32_t)s << 16) | ((uint32_t)s3 << 24);
+  }
+}
+
+// ---- per-device one-time set-up ------------------------------------------
+std::mutex g_dev_mu;
+bool g_dev_ready[128];
+
+int device_setup(int device) {
+  if (device < 0 || device >= 128) return LWE_EINVAL;
+  std::lock_guard<std::mutex> lk(g_dev_mu);
+  if (g_dev_ready[device]) return LWE_OK;
+  cudaDeviceProp prop;
+  CUDA_TRY(cudaGetDeviceProperties(&prop, device));
+  if (prop.major != 10 || prop.minor != 3) return LWE_EUNSUPPORTED;
+  int prev = 0;
+  CUDA_TRY(cudaGetDevice(&prev));
+  CUDA_TRY(cudaSetDevice(device));
+  uint32_t T0[256];
+  build_aes_T0(T0);
+  cudaError_t e = lwe_upload_aes_table(T0);
+  if (e == cudaSuccess) e = lwe_kernel_smem_setup();
+  if (e == cudaSuccess) e = lwe_gemm_setup();
+  cudaSetDevice(prev);
+  if (e != cudaSuccess) return cuda_fail(e);
+  g_dev_ready[device] = true;
+  return LWE_OK;
+}
+
+int current_device_setup(int *dev_out, int *sms_out) {
+  int dev = 0;
+  CUDA_TRY(cudaGetDevice(&dev));
+  int rc = device_setup(dev);
+  if (rc != LWE_OK) return rc;
+  if (dev_out) *dev_out = dev;
+  if (sms_out) CUDA_TRY(cudaDeviceGetAttribute(sms_out, cudaDevAttrMultiProcessorCount, dev));
+  return LWE_OK;
+}
+
+// ---- noise table (independent restatement of the rounded Gaussian) -------
+double norm_cdf(double x) { return 0.5 * std::erfc(-x / std::sqrt(2.0)); }
+
+int cdf_table(double sigma, uint32_t clip, uint16_t T[16]) {
+  if (!(sigma > 0.0) || clip < 1 || clip > 15) return LWE_EINVAL;
+  double mass[16];
+  double z = 0.0;
+  for (uint32_t k = 0; k <= clip; k++) {
+    mass[k] = norm_cdf((k + 0.5) / sigma) - norm_cdf((k - 0.5) / sigma);
+    z += k ? 2.0 * mass[k] : mass[k];
+  }
+  double acc = 0.0;
+  for (uint32_t k = 0; k < 16; k++) T[k] = 0x7fff;
+  for (uint32_t k = 0; k < clip; k++) {
+    acc += (k ? 2.0 * mass[k] : mass[k]) / z;
+    const double v = std::floor(acc * 32768.0 + 0.5) - 1.0;
+    if (v < 0.0 || v >= 32767.0) return LWE_EINVAL;
+    T[k] = (uint16_t)v;
+    if (k > 0 && T[k] <= T[k - 1]) return LWE_EINVAL;
+  }
+  return LWE_OK;
+}
+
+int params_check(const lwe_params *p) {
+  if (!p) return LWE_EINVAL;
+  if (p->n < 16 || p->n > 65536 || (p->n % 16) != 0) return LWE_EINVAL;
+  if (p->nbar != 8 || p->mbar != 8) return LWE_EINVAL;
+  if (p->logq < 2 || p->logq > 16) return LWE_EINVAL;
+  if (p->B < 1 || p->B > 4 || p->B >= p->logq) return LWE_EINVAL;
+  uint16_t T[16];
+  return cdf_table(p->sigma, p->clip, T);
+}
+
+size_t pk_bytes(const lwe_params &p) { return 16 + 16 * (size_t)p.n; }
+size_t sk_bytes(const lwe_params &p) { return 8 * (size_t)p.n + 64 + pk_bytes(p); }
+size_t ct_bytes(const lwe_params &p) { return 16 * (size_t)p.n + 128; }
+uint32_t mu_bytes(const lwe_params &p) { return 8 * p.B; }
+
+const char *kKernelNames[KID_COUNT] = {
+    "k_expand_A", "k_noise",        "k_keygen_seeds", "k_mul_as",     "k_decrypt",
+    "k_mul_sa",   "k_mul_sa_fused", "k_v_encode",     "k_tree_leaves", "k_tree_root",
+    "k_derive",   "k_limbs",        "k_gemm_tc"};
+
+}  // namespace
+
+// ---- context ---------------------------------------------------------------
+struct TimedLaunch {
+  int kid;
+  cudaEvent_t a, b;
+};
+
+struct lwe_ctx {
+  lwe_params p;
+  uint16_t T[16];
+  int device = 0;
+  int num_sms = 0;
+  uint32_t max_batch = 0;
+  int path = LWE_PATH_AUTO;
+  int tensor_min = 64;
+  int gemm_bn = 128;
+  bool timing = false;
+  uint64_t launches = 0;
+  std::vector<TimedLaunch> pending;
+  std::vector<cudaEvent_t> free_events;
+  uint64_t stat_launches[KID_COUNT] = {};
+  double stat_ms[KID_COUNT] = {};
+  // workspace
+  uint8_t *ws = nullptr;
+  size_t ws_bytes = 0;
+  uint8_t *seeds = nullptr, *mu = nullptr, *kp = nullptr, *pkh = nullptr, *leaves = nullptr;
+  uint32_t *flags = nullptr, *dev_err = nullptr;
+  int8_t *sp8 = nullptr, *ep8 = nullptr, *epp = nullptr;
+  uint16_t *spbf = nullptr;  // bf16 bits
+  uint16_t *limbs = nullptr; // bf16 bits, [2][n + 8][n]
+  bool has_tensor = false;
+  uint32_t tree_m = 0;  // leaves per item
+};
+
+namespace {
+
+cudaEvent_t take_event(lwe_ctx *c) {
+  if (!c->free_events.empty()) {
+    cudaEvent_t e = c->free_events.back();
+    c->free_events.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+  return e;
+}
+
+struct LaunchScope {
+  lwe_ctx *c;
+  int kid;
+  cudaStream_t st;
+  cudaEvent_t a = nullptr, b = nullptr;
+  LaunchScope(lwe_ctx *c_, int kid_, cudaStream_t st_) : c(c_), kid(kid_), st(st_) {
+    if (c && c->timing) {
+      a = take_event(c);
+      b = take_event(c);
+      if (a && b) cudaEventRecord(a, st);
+    }
+  }
+  ~LaunchScope() {
+    if (!c) return;
+    c->launches++;
+    if (a && b) {
+      cudaEventRecord(b, st);
+      c->pending.push_back({kid, a, b});
+    }
+  }
+};
+
+#define LAUNCH(ctx, kid, stream, call) \
+  do {                                 \
+    LaunchScope _ls(ctx, kid, stream); \
+    call;                              \
+  } while (0)
+
+int check_launch() {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e);
+  return LWE_OK;
+}
+
+void harvest(lwe_ctx *c) {
+  for (auto &t : c->pending) {
+    cudaEventSynchronize(t.b);
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, t.a, t.b) == cudaSuccess) {
+      c->stat_launches[t.kid]++;
+      c->stat_ms[t.kid] += ms;
+    }
+    c->free_events.push_back(t.a);
+    c->free_events.push_back(t.b);
+  }
+  c->pending.clear();
+}
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+NoiseArgs noise_args(const lwe_ctx *c, const uint8_t *keys, uint32_t count) {
+  NoiseArgs a;
+  memset(&a, 0, sizeof a);
+  a.keys = keys;
+  a.key_stride = 32;
+  a.count = count;
+  for (int i = 0; i < 16; i++) a.T[i] = c->T[i];
+  return a;
+}
+
+// Encrypt (Alg. 2) for `count` items whose seedSE' and mu are in the
+// workspace; writes ct, or (cmp) compares against ct and sets flags.
+int run_encrypt(lwe_ctx *c, const uint8_t *pk, const uint16_t *A, uint32_t count, uint8_t *ct,
+                bool cmp, cudaStream_t st) {
+  const uint32_t n = c->p.n;
+  bool tensor = false;
+  if (c->path == LWE_PATH_TENSOR)
+    tensor = true;
+  else if (c->path == LWE_PATH_AUTO)
+    tensor = (int)count >= c->tensor_min;
+  tensor = tensor && c->has_tensor;
+
+  NoiseArgs na = noise_args(c, c->seeds, count);
+  na.nout = 3;
+  if (tensor)
+    na.out[0] = {c->spbf, 16ull * n, 8 * n, 3, NOISE_BF16, 0};
+  else
+    na.out[0] = {c->sp8, 8ull * n, 8 * n, 3, NOISE_I8, 0};
+  na.out[1] = {c->ep8, 8ull * n, 8 * n, 4, NOISE_I8, 0};
+  na.out[2] = {c->epp, 64, 64, 5, NOISE_I8, 0};
+  LAUNCH(c, KID_NOISE, st, launch_noise(na, c->num_sms, st));
+
+  if (tensor) {
+    GemmLimbArgs la;
+    la.A = A;
+    la.seedA = pk;
+    la.B = pk + 16;
+    la.n = n;
+    la.logq = c->p.logq;
+    la.limbs = c->limbs;
+    LAUNCH(c, KID_LIMBS, st, launch_gemm_limbs(la, c->num_sms, st));
+    GemmSaArgs ga;
+    memset(&ga, 0, sizeof ga);
+    ga.S = c->spbf;
+    ga.limbs = c->limbs;
+    ga.E = c->ep8;
+    ga.Epp = c->epp;
+    ga.mu = c->mu;
+    ga.out = ct;
+    ga.out_stride = ct_bytes(c->p);
+    ga.flags = c->flags;
+    ga.dev_err = c->dev_err;
+    ga.n = n;
+    ga.ncols = n + 8;
+    ga.rows = 8 * count;
+    ga.logq = c->p.logq;
+    ga.B = c->p.B;
+    ga.cmp = cmp ? 1 : 0;
+    ga.bn = c->gemm_bn;
+    int rc = LWE_OK;
+    LAUNCH(c, KID_GEMM, st, rc = launch_gemm_sa(ga, c->num_sms, st));
+    if (rc != LWE_OK) return rc;
+    return check_launch();
+  }
+
+  MulSaArgs sa;
+  memset(&sa, 0, sizeof sa);
+  sa.A = A;
+  sa.seedA = pk;
+  sa.n = n;
+  sa.logq = c->p.logq;
+  sa.S = c->sp8;
+  sa.s_stride = 8ull * n;
+  sa.E = c->ep8;
+  sa.e_stride = 8ull * n;
+  sa.out = ct;
+  sa.out_stride = ct_bytes(c->p);
+  sa.flags = c->flags;
+  LAUNCH(c, A ? KID_MUL_SA : KID_MUL_SA_FUSED, st, launch_mul_sa(sa, count, A == nullptr, cmp, st));
+
+  VEncArgs va;
+  memset(&va, 0, sizeof va);
+  va.pk = pk;
+  va.S = c->sp8;
+  va.s_stride = 8ull * n;
+  va.Epp = c->epp;
+  va.epp_stride = 64;
+  va.mu = c->mu;
+  va.ct = ct;
+  va.ct_bytes = ct_bytes(c->p);
+  va.flags = c->flags;
+  va.n = n;
+  va.logq = c->p.logq;
+  va.B = c->p.B;
+  LAUNCH(c, KID_V_ENCODE, st, launch_v_encode(va, count, cmp, st));
+  return check_launch();
+}
+
+int hash_tree(lwe_ctx *c, const uint8_t *msgs, uint64_t stride, uint32_t len, uint32_t count,
+              int mode, uint8_t *out, uint64_t out_stride, uint8_t *out2, uint64_t out2_stride,
+              const uint8_t *z, cudaStream_t st) {
+  TreeLeafArgs la{msgs, stride, len, count, c->leaves};
+  LAUNCH(c, KID_TREE_LEAVES, st, launch_tree_leaves(la, st));
+  TreeRootArgs ra;
+  memset(&ra, 0, sizeof ra);
+  ra.leaves = c->leaves;
+  ra.m = (len + LWE_TREE_CHUNK - 1) / LWE_TREE_CHUNK;
+  ra.count = count;
+  ra.mode = mode;
+  ra.out = out;
+  ra.out_stride = out_stride;
+  ra.out2 = out2;
+  ra.out2_stride = out2_stride;
+  ra.kprime = c->kp;
+  ra.z = z;
+  ra.flags = c->flags;
+  LAUNCH(c, KID_TREE_ROOT, st, launch_tree_root(ra, st));
+  return check_launch();
+}
+
+int set_device_of(lwe_ctx *c) {
+  int cur = -1;
+  CUDA_TRY(cudaGetDevice(&cur));
+  if (cur != c->device) CUDA_TRY(cudaSetDevice(c->device));
+  return LWE_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int lwe_params_preset(int id, lwe_params *out) {
+  if (!out) return LWE_EINVAL;
+  static const struct {
+    uint32_t n, logq, B, clip;
+    double sigma;
+  } P[] = {{640, 15, 2, 12, 2.8},  {976, 16, 3, 10, 2.3},   {1344, 16, 4, 6, 1.4},
+           {4096, 16, 2, 12, 2.8}, {16384, 16, 1, 12, 2.8}, {32768, 16, 1, 12, 2.8}};
+  if (id < 0 || id >= (int)(sizeof P / sizeof P[0])) return LWE_EINVAL;
+  out->n = P[id].n;
+  out->nbar = 8;
+  out->mbar = 8;
+  out->logq = P[id].logq;
+  out->B = P[id].B;
+  out->clip = P[id].clip;
+  out->sigma = P[id].sigma;
+  return LWE_OK;
+}
+
+int lwe_params_check(const lwe_params *p) { return params_check(p); }
+
+int lwe_cdf_table(const lwe_params *p, uint16_t T[16]) {
+  if (!p || !T) return LWE_EINVAL;
+  return cdf_table(p->sigma, p->clip, T);
+}
+
+size_t lwe_pk_bytes(const lwe_params *p) { return p ? pk_bytes(*p) : 0; }
+size_t lwe_sk_bytes(const lwe_params *p) { return p ? sk_bytes(*p) : 0; }
+size_t lwe_ct_bytes(const lwe_params *p) { return p ? ct_bytes(*p) : 0; }
+
+int lwe_ctx_create(const lwe_params *p, uint32_t max_batch, int device, lwe_ctx **out) {
+  if (!out) return LWE_EINVAL;
+  *out = nullptr;
+  if (params_check(p) != LWE_OK || max_batch < 1) return LWE_EINVAL;
+  int ndev = 0;
+  CUDA_TRY(cudaGetDeviceCount(&ndev));
+  if (device < 0 || device >= ndev) return LWE_EINVAL;
+  int rc = device_setup(device);
+  if (rc != LWE_OK) return rc;
+  int prev = 0;
+  CUDA_TRY(cudaGetDevice(&prev));
+  CUDA_TRY(cudaSetDevice(device));
+
+  lwe_ctx *c = new lwe_ctx();
+  c->p = *p;
+  cdf_table(p->sigma, p->clip, c->T);
+  c->device = device;
+  c->max_batch = max_batch;
+  cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
+
+  const size_t n = p->n;
+  const size_t Bm = max_batch;
+  c->tree_m = (uint32_t)((std::max(ct_bytes(*p), pk_bytes(*p)) + LWE_TREE_CHUNK - 1) / LWE_TREE_CHUNK);
+  c->has_tensor = lwe_gemm_supported(p->n, p->logq, p->clip);
+  size_t off = 0;
+  auto carve = [&](size_t bytes) {
+    size_t o = off;
+    off = align_up(off + bytes, 256);
+    return o;
+  };
+  const size_t o_seeds = carve(32 * Bm), o_mu = carve(32 * Bm), o_kp = carve(32 * Bm);
+  const size_t o_flags = carve(4 * Bm), o_err = carve(16), o_pkh = carve(32);
+  const size_t o_leaves = carve(32 * (size_t)c->tree_m * Bm);
+  const size_t o_sp8 = carve(8 * n * Bm), o_ep8 = carve(8 * n * Bm), o_epp = carve(64 * Bm);
+  size_t o_spbf = 0, o_limbs = 0;
+  if (c->has_tensor) {
+    o_spbf = carve(16 * n * Bm);
+    o_limbs = carve(2 * 2 * (n + 8) * n);
+  }
+  c->ws_bytes = off;
+  cudaError_t e = cudaMalloc(&c->ws, c->ws_bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    delete c;
+    cudaSetDevice(prev);
+    return LWE_ENOMEM;
+  }
+  c->seeds = c->ws + o_seeds;
+  c->mu = c->ws + o_mu;
+  c->kp = c->ws + o_kp;
+  c->flags = reinterpret_cast<uint32_t *>(c->ws + o_flags);
+  c->dev_err = reinterpret_cast<uint32_t *>(c->ws + o_err);
+  c->pkh = c->ws + o_pkh;
+  c->leaves = c->ws + o_leaves;
+  c->sp8 = reinterpret_cast<int8_t *>(c->ws + o_sp8);
+  c->ep8 = reinterpret_cast<int8_t *>(c->ws + o_ep8);
+  c->epp = reinterpret_cast<int8_t *>(c->ws + o_epp);
+  if (c->has_tensor) {
+    c->spbf = reinterpret_cast<uint16_t *>(c->ws + o_spbf);
+    c->limbs = reinterpret_cast<uint16_t *>(c->ws + o_limbs);
+  }
+  e = cudaMemset(c->ws, 0, c->ws_bytes);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  cudaSetDevice(prev);
+  if (e != cudaSuccess) {
+    cudaFree(c->ws);
+    delete c;
+    return cuda_fail(e);
+  }
+  *out = c;
+  return LWE_OK;
+}
+
+int lwe_ctx_destroy(lwe_ctx *c) {
+  if (!c) return LWE_OK;
+  int prev = 0;
+  cudaGetDevice(&prev);
+  cudaSetDevice(c->device);
+  cudaDeviceSynchronize();
+  for (auto &t : c->pending) {
+    cudaEventDestroy(t.a);
+    cudaEventDestroy(t.b);
+  }
+  for (auto e : c->free_events) cudaEventDestroy(e);
+  cudaFree(c->ws);
+  cudaSetDevice(prev);
+  delete c;
+  return LWE_OK;
+}
+
+int lwe_ctx_set_option(lwe_ctx *c, int option, int64_t value) {
+  if (!c) return LWE_EINVAL;
+  switch (option) {
+    case LWE_OPT_PATH:
+      if (value < LWE_PATH_AUTO || value > LWE_PATH_TENSOR) return LWE_EINVAL;
+      if (value == LWE_PATH_TENSOR && !c->has_tensor) return LWE_EUNSUPPORTED;
+      c->path = (int)value;
+      return LWE_OK;
+    case LWE_OPT_TENSOR_MIN:
+      if (value < 1) return LWE_EINVAL;
+      c->tensor_min = (int)value;
+      return LWE_OK;
+    case LWE_OPT_TIMING:
+      c->timing = value != 0;
+      return LWE_OK;
+    case LWE_OPT_GEMM_BN:
+      if (value != 64 && value != 128) return LWE_EINVAL;
+      c->gemm_bn = (int)value;
+      return LWE_OK;
+    default:
+      return LWE_EINVAL;
+  }
+}
+
+int lwe_keygen(lwe_ctx *c, const uint8_t *seeds, uint32_t count, uint8_t *pk, uint8_t *sk,
+               uint16_t *A_out, void *stream) {
+  if (!c) return LWE_EINVAL;
+  if (count == 0) return LWE_OK;
+  if (count > c->max_batch) return LWE_ECAPACITY;
+  if (!seeds || !pk || !sk || !aligned16(seeds) || !aligned16(pk) || !aligned16(sk) ||
+      (A_out && !aligned16(A_out)))
+    return LWE_EINVAL;
+  int rc = set_device_of(c);
+  if (rc) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  const lwe_params &p = c->p;
+  const uint32_t n = p.n;
+  const size_t pkb = pk_bytes(p), skb = sk_bytes(p);
+
+  KeygenSeedArgs ka{seeds, pk, sk, c->seeds, pkb, skb, 8ull * n, 8ull * n + 64, count, 0};
+  LAUNCH(c, KID_KEYGEN_SEEDS, st, launch_keygen_seeds(ka, st));
+
+  NoiseArgs na = noise_args(c, c->seeds + 16, count);
+  na.nout = 2;
+  na.out[0] = {sk, skb, 8 * n, 1, NOISE_I8, 0};           // S^T, row-major 8 x n
+  na.out[1] = {c->ep8, 8ull * n, 8 * n, 2, NOISE_I8, 0};  // E, n x 8
+  LAUNCH(c, KID_NOISE, st, launch_noise(na, c->num_sms, st));
+
+  if (A_out)
+    LAUNCH(c, KID_EXPAND_A, st,
+           launch_expand_A(c->seeds, 32, count, n, p.logq, A_out, (uint64_t)n * n, c->num_sms, st));
+
+  MulAsArgs ma;
+  memset(&ma, 0, sizeof ma);
+  ma.A = A_out;
+  ma.a_stride = (uint64_t)n * n;
+  ma.seeds = c->seeds;
+  ma.seed_stride = 32;
+  ma.n = n;
+  ma.logq = p.logq;
+  ma.St = reinterpret_cast<const int8_t *>(sk);
+  ma.st_stride = skb;
+  ma.E = c->ep8;
+  ma.e_stride = 8ull * n;
+  ma.out = pk + 16;
+  ma.out_stride = pkb;
+  ma.out2 = sk + 8 * (size_t)n + 64 + 16;
+  ma.out2_stride = skb;
+  LAUNCH(c, KID_MUL_AS, st, launch_mul_as(ma, count, A_out == nullptr, st));
+
+  // H(pk) into sk
+  return hash_tree(c, pk, pkb, (uint32_t)pkb, count, TREE_DIGEST, sk + 8 * (size_t)n + 32, skb,
+                   nullptr, 0, nullptr, st);
+}
+
+int lwe_encaps(lwe_ctx *c, const uint8_t *pk, const uint16_t *A, const uint8_t *coins,
+               uint32_t count, uint8_t *ct, uint8_t *K, void *stream) {
+  if (!c) return LWE_EINVAL;
+  if (count == 0) return LWE_OK;
+  if (count > c->max_batch) return LWE_ECAPACITY;
+  if (!pk || !coins || !ct || !K || !aligned16(pk) || !aligned16(coins) || !aligned16(ct) ||
+      !aligned16(K) || (A && !aligned16(A)))
+    return LWE_EINVAL;
+  int rc = set_device_of(c);
+  if (rc) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  const lwe_params &p = c->p;
+  const size_t pkb = pk_bytes(p), ctb = ct_bytes(p);
+
+  rc = hash_tree(c, pk, pkb, (uint32_t)pkb, 1, TREE_DIGEST, c->pkh, 32, nullptr, 0, nullptr, st);
+  if (rc) return rc;
+  DeriveArgs da{coins, c->pkh, c->mu, c->kp, c->seeds, count, mu_bytes(p)};
+  LAUNCH(c, KID_DERIVE, st, launch_derive(da, st));
+  rc = run_encrypt(c, pk, A, count, ct, false, st);
+  if (rc) return rc;
+  return hash_tree(c, ct, ctb, (uint32_t)ctb, count, TREE_ENC_KEY, K, 32, nullptr, 0, nullptr, st);
+}
+
+int lwe_decaps(lwe_ctx *c, const uint8_t *sk, const uint16_t *A, const uint8_t *ct,
+               uint32_t count, uint8_t *K, void *stream) {
+  if (!c) return LWE_EINVAL;
+  if (count == 0) return LWE_OK;
+  if (count > c->max_batch) return LWE_ECAPACITY;
+  if (!sk || !ct || !K || !aligned16(sk) || !aligned16(ct) || !aligned16(K) ||
+      (A && !aligned16(A)))
+    return LWE_EINVAL;
+  int rc = set_device_of(c);
+  if (rc) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  const lwe_params &p = c->p;
+  const uint32_t n = p.n;
+  const size_t ctb = ct_bytes(p);
+  const uint8_t *z = sk + 8 * (size_t)n;
+  const uint8_t *pkh = z + 32;
+  const uint8_t *pk = pkh + 32;
+
+  CUDA_TRY(cudaMemsetAsync(c->flags, 0, 4 * (size_t)count, st));
+  DecryptArgs dca{ct, ctb, reinterpret_cast<const int8_t *>(sk), c->mu, n, p.logq, p.B, 0};
+  LAUNCH(c, KID_DECRYPT, st, launch_decrypt(dca, count, st));
+  DeriveArgs da{nullptr, pkh, c->mu, c->kp, c->seeds, count, mu_bytes(p)};
+  LAUNCH(c, KID_DERIVE, st, launch_derive(da, st));
+  rc = run_encrypt(c, pk, A, count, const_cast<uint8_t *>(ct), true, st);
+  if (rc) return rc;
+  return hash_tree(c, ct, ctb, (uint32_t)ctb, count, TREE_DEC_KEY, K, 32, nullptr, 0, z, st);
+}
+
+int lwe_expand_A(const uint8_t *seedA, uint32_t n, uint32_t logq, uint16_t *A_out,
+                 void *stream) {
+  if (!seedA || !A_out || !aligned16(A_out) || n < 16 || n > 65536 || (n % 16) || logq < 1 ||
+      logq > 16)
+    return LWE_EINVAL;
+  int sms = 0;
+  int rc = current_device_setup(nullptr, &sms);
+  if (rc) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  launch_expand_A(seedA, 16, 1, n, logq, A_out, 0, sms, st);
+  return check_launch();
+}
+
+int lwe_matmul_modq(lwe_ctx *c, int side, const uint16_t *A, const uint8_t *seedA,
+                    const int8_t *S, uint32_t n, uint32_t k, uint32_t logq, const int8_t *E,
+                    uint16_t *out, void *stream) {
+  if (!S || !out || (!A && !seedA) || n < 16 || n > 65536 || (n % 16) || logq < 1 || logq > 16)
+    return LWE_EINVAL;
+  if (!aligned16(S) || !aligned16(out) || (A && !aligned16(A)) || (E && !aligned16(E)))
+    return LWE_EINVAL;
+  int sms = 0;
+  int rc = current_device_setup(nullptr, &sms);
+  if (rc) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (side == LWE_SIDE_AS) {
+    if (k != 8) return LWE_EINVAL;
+    MulAsArgs ma;
+    memset(&ma, 0, sizeof ma);
+    ma.A = A;
+    ma.seeds = seedA;
+    ma.seed_stride = 16;
+    ma.n = n;
+    ma.logq = logq;
+    ma.St = S;
+    ma.E = E;
+    ma.out = reinterpret_cast<uint8_t *>(out);
+    LAUNCH(c, KID_MUL_AS, st, launch_mul_as(ma, 1, A == nullptr, st));
+    return check_launch();
+  }
+  if (side != LWE_SIDE_SA || k == 0 || (k % 8)) return LWE_EINVAL;
+  const uint32_t items = k / 8;
+  if (c && c->has_tensor && c->p.n == n && c->p.logq == logq && items <= c->max_batch &&
+      (c->path == LWE_PATH_TENSOR ||
+       (c->path == LWE_PATH_AUTO && (int)items >= c->tensor_min))) {
+    rc = set_device_of(c);
+    if (rc) return rc;
+    // S and E go through the GEMM as given: convert S to bf16 in the workspace
+    GemmLimbArgs la;
+    la.A = A;
+    la.seedA = seedA;
+    la.B = nullptr;
+    la.n = n;
+    la.logq = logq;
+    la.limbs = c->limbs;
+    LAUNCH(c, KID_LIMBS, st, launch_gemm_limbs(la, c->num_sms, st));
+    LAUNCH(c, KID_LIMBS, st, launch_s_to_bf16(S, (uint64_t)k * n, c->spbf, c->num_sms, st));
+    GemmSaArgs ga;
+    memset(&ga, 0, sizeof ga);
+    ga.S = c->spbf;
+    ga.limbs = c->limbs;
+    ga.E = E;
+    ga.out = reinterpret_cast<uint8_t *>(out);
+    ga.out_stride = 16ull * n;
+    ga.dev_err = c->dev_err;
+    ga.n = n;
+    ga.ncols = n;
+    ga.rows = k;
+    ga.logq = logq;
+    ga.B = 0;
+    ga.cmp = 0;
+    ga.bn = c->gemm_bn;
+    LAUNCH(c, KID_GEMM, st, rc = launch_gemm_sa(ga, c->num_sms, st));
+    if (rc) return rc;
+    return check_launch();
+  }
+  MulSaArgs sa;
+  memset(&sa, 0, sizeof sa);
+  sa.A = A;
+  sa.seedA = seedA;
+  sa.n = n;
+  sa.logq = logq;
+  sa.S = S;
+  sa.s_stride = 8ull * n;
+  sa.E = E;
+  sa.e_stride = 8ull * n;
+  sa.out = reinterpret_cast<uint8_t *>(out);
+  sa.out_stride = 16ull * n;
+  LAUNCH(c, A ? KID_MUL_SA : KID_MUL_SA_FUSED, st, launch_mul_sa(sa, items, A == nullptr, false, st));
+  return check_launch();
+}
+
+const char *lwe_strerror(int code) {
+  switch (code) {
+    case LWE_OK: return "ok";
+    case LWE_EINVAL: return "invalid argument";
+    case LWE_ENOMEM: return "out of device memory";
+    case LWE_ECUDA: return "CUDA error";
+    case LWE_ETIMEOUT: return "device wait timed out";
+    case LWE_EUNSUPPORTED: return "unsupported device or configuration";
+    case LWE_ECAPACITY: return "count exceeds the context's max_batch";
+    default: return "unknown error";
+  }
+}
+
+const char *lwe_last_cuda_error(void) { return g_last_cuda_error.c_str(); }
+
+int lwe_ctx_device_error(lwe_ctx *c) {
+  if (!c) return LWE_EINVAL;
+  int rc = set_device_of(c);
+  if (rc) return rc;
+  CUDA_TRY(cudaDeviceSynchronize());
+  uint32_t v = 0;
+  CUDA_TRY(cudaMemcpy(&v, c->dev_err, 4, cudaMemcpyDeviceToHost));
+  if (v) {
+    CUDA_TRY(cudaMemset(c->dev_err, 0, 4));
+    return LWE_ETIMEOUT;
+  }
+  return LWE_OK;
+}
+
+uint64_t lwe_ctx_launches(const lwe_ctx *c) { return c ? c->launches : 0; }
+
+int lwe_ctx_kernel_stats(lwe_ctx *c, int kid, uint64_t *launches, double *total_ms) {
+  if (!c || kid < 0 || kid >= KID_COUNT) return LWE_EINVAL;
+  harvest(c);
+  if (launches) *launches = c->stat_launches[kid];
+  if (total_ms) *total_ms = c->stat_ms[kid];
+  return LWE_OK;
+}
+
+int lwe_ctx_reset_stats(lwe_ctx *c) {
+  if (!c) return LWE_EINVAL;
+  harvest(c);
+  for (int i = 0; i < KID_COUNT; i++) {
+    c->stat_launches[i] = 0;
+    c->stat_ms[i] = 0.0;
+  }
+  return LWE_OK;
+}
+
+const char *lwe_kernel_name(int kid) {
+  if (kid < 0 || kid >= KID_COUNT) return nullptr;
+  return kKernelNames[kid];
+}
+
+int lwe_num_kernels(void) { return KID_COUNT; }
+
+}  // extern "C"

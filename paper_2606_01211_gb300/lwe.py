@@ -1,0 +1,288 @@
+"""Python binding of liblwe.so (include/lwe.h): argument marshalling only.
+
+Every function takes torch CUDA tensors (uint8 / int8 / int16 storage),
+checks their sizes, and passes their device pointers and the current CUDA
+stream to the C ABI.  All arithmetic of the KEM runs in the library's CUDA
+kernels; nothing here computes any step of it, and there is no CPU fallback:
+if liblwe.so is missing or fails to load, import raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+
+import torch
+
+from .build_lib import LIB
+
+# status codes (include/lwe.h)
+LWE_OK = 0
+LWE_EINVAL = -1
+LWE_ENOMEM = -2
+LWE_ECUDA = -3
+LWE_ETIMEOUT = -4
+LWE_EUNSUPPORTED = -5
+LWE_ECAPACITY = -6
+
+PATH_AUTO, PATH_SKINNY, PATH_TENSOR = 0, 1, 2
+OPT_PATH, OPT_TENSOR_MIN, OPT_TIMING, OPT_GEMM_BN = 0, 1, 2, 3
+SIDE_AS, SIDE_SA = 0, 1
+PRESET_IDS = {"P640": 0, "P976": 1, "P1344": 2, "P4096": 3, "P16384": 4, "P32768": 5}
+
+
+class LweError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        msg = "%s failed: %s (%d)" % (what, _lib.lwe_strerror(code).decode(), code)
+        if code == LWE_ECUDA:
+            msg += ": " + _lib.lwe_last_cuda_error().decode()
+        super().__init__(msg)
+        self.code = code
+
+
+class _Params(C.Structure):
+    _fields_ = [("n", C.c_uint32), ("nbar", C.c_uint32), ("mbar", C.c_uint32),
+                ("logq", C.c_uint32), ("B", C.c_uint32), ("clip", C.c_uint32),
+                ("sigma", C.c_double)]
+
+
+def _load():
+    if not os.path.exists(LIB):
+        raise ImportError("liblwe.so is not built (run __graft_entry__.build() or "
+                          "python -m paper_2606_01211_gb300.build_lib)")
+    lib = C.CDLL(LIB)
+    vp, u32, i32, sz = C.c_void_p, C.c_uint32, C.c_int, C.c_size_t
+    P = C.POINTER(_Params)
+    sig = {
+        "lwe_params_preset": (i32, [i32, P]),
+        "lwe_params_check": (i32, [P]),
+        "lwe_cdf_table": (i32, [P, vp]),
+        "lwe_pk_bytes": (sz, [P]),
+        "lwe_sk_bytes": (sz, [P]),
+        "lwe_ct_bytes": (sz, [P]),
+        "lwe_ctx_create": (i32, [P, u32, i32, C.POINTER(vp)]),
+        "lwe_ctx_destroy": (i32, [vp]),
+        "lwe_ctx_set_option": (i32, [vp, i32, C.c_int64]),
+        "lwe_keygen": (i32, [vp, vp, u32, vp, vp, vp, vp]),
+        "lwe_encaps": (i32, [vp, vp, vp, vp, u32, vp, vp, vp]),
+        "lwe_decaps": (i32, [vp, vp, vp, vp, u32, vp, vp]),
+        "lwe_expand_A": (i32, [vp, u32, u32, vp, vp]),
+        "lwe_matmul_modq": (i32, [vp, i32, vp, vp, vp, u32, u32, u32, vp, vp, vp]),
+        "lwe_strerror": (C.c_char_p, [i32]),
+        "lwe_last_cuda_error": (C.c_char_p, []),
+        "lwe_ctx_device_error": (i32, [vp]),
+        "lwe_ctx_launches": (C.c_uint64, [vp]),
+        "lwe_ctx_kernel_stats": (i32, [vp, i32, C.POINTER(C.c_uint64), C.POINTER(C.c_double)]),
+        "lwe_ctx_reset_stats": (i32, [vp]),
+        "lwe_kernel_name": (C.c_char_p, [i32]),
+        "lwe_num_kernels": (i32, []),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    return lib
+
+
+_lib = _load()
+
+
+def lib():
+    return _lib
+
+
+def _check(rc: int, what: str):
+    if rc != LWE_OK:
+        raise LweError(rc, what)
+
+
+@dataclass(frozen=True)
+class Params:
+    n: int
+    logq: int
+    B: int
+    clip: int
+    sigma: float
+    nbar: int = 8
+    mbar: int = 8
+
+    def c(self) -> _Params:
+        return _Params(self.n, self.nbar, self.mbar, self.logq, self.B, self.clip, self.sigma)
+
+    @staticmethod
+    def preset(name: str) -> "Params":
+        p = _Params()
+        _check(_lib.lwe_params_preset(PRESET_IDS[name], C.byref(p)), "lwe_params_preset")
+        return Params(n=p.n, logq=p.logq, B=p.B, clip=p.clip, sigma=p.sigma)
+
+    def valid(self) -> bool:
+        cp = self.c()
+        return _lib.lwe_params_check(C.byref(cp)) == LWE_OK
+
+    @property
+    def pk_bytes(self) -> int:
+        cp = self.c()
+        return int(_lib.lwe_pk_bytes(C.byref(cp)))
+
+    @property
+    def sk_bytes(self) -> int:
+        cp = self.c()
+        return int(_lib.lwe_sk_bytes(C.byref(cp)))
+
+    @property
+    def ct_bytes(self) -> int:
+        cp = self.c()
+        return int(_lib.lwe_ct_bytes(C.byref(cp)))
+
+    def cdf_table(self):
+        import numpy as np
+        T = np.zeros(16, np.uint16)
+        cp = self.c()
+        _check(_lib.lwe_cdf_table(C.byref(cp), T.ctypes.data), "lwe_cdf_table")
+        return T[: self.clip].copy()
+
+
+def _ptr(t: torch.Tensor | None, dtype=None, nbytes: int | None = None, what: str = "") -> int | None:
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("%s must be a CUDA tensor" % what)
+    if not t.is_contiguous():
+        raise ValueError("%s must be contiguous" % what)
+    if dtype is not None and t.dtype != dtype:
+        raise ValueError("%s must have dtype %s, got %s" % (what, dtype, t.dtype))
+    if nbytes is not None and t.numel() * t.element_size() < nbytes:
+        raise ValueError("%s holds %d bytes, needs %d" % (what, t.numel() * t.element_size(), nbytes))
+    return t.data_ptr()
+
+
+def _stream(stream) -> int | None:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return stream.cuda_stream
+
+
+class Ctx:
+    """An lwe_ctx: parameters, device workspaces for max_batch items."""
+
+    def __init__(self, params: Params, max_batch: int = 1, device: int | None = None):
+        if device is None:
+            device = torch.cuda.current_device()
+        self.params = params
+        self.max_batch = max_batch
+        self.device = device
+        h = C.c_void_p()
+        cp = params.c()
+        _check(_lib.lwe_ctx_create(C.byref(cp), max_batch, device, C.byref(h)), "lwe_ctx_create")
+        self._h = h
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if self._h:
+            _lib.lwe_ctx_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_option(self, option: int, value: int):
+        _check(_lib.lwe_ctx_set_option(self._h, option, int(value)), "lwe_ctx_set_option")
+
+    def set_path(self, path: int):
+        self.set_option(OPT_PATH, path)
+
+    def device_error(self) -> int:
+        return int(_lib.lwe_ctx_device_error(self._h))
+
+    def launches(self) -> int:
+        return int(_lib.lwe_ctx_launches(self._h))
+
+    def kernel_stats(self) -> dict:
+        out = {}
+        for k in range(_lib.lwe_num_kernels()):
+            n = C.c_uint64()
+            ms = C.c_double()
+            _check(_lib.lwe_ctx_kernel_stats(self._h, k, C.byref(n), C.byref(ms)), "kernel_stats")
+            if n.value:
+                out[_lib.lwe_kernel_name(k).decode()] = (int(n.value), float(ms.value))
+        return out
+
+    def reset_stats(self):
+        _check(_lib.lwe_ctx_reset_stats(self._h), "lwe_ctx_reset_stats")
+
+    # ---- buffers -------------------------------------------------------
+    def empty_pk(self, count: int = 1) -> torch.Tensor:
+        return torch.empty((count, self.params.pk_bytes), dtype=torch.uint8, device="cuda")
+
+    def empty_sk(self, count: int = 1) -> torch.Tensor:
+        return torch.empty((count, self.params.sk_bytes), dtype=torch.uint8, device="cuda")
+
+    def empty_ct(self, count: int = 1) -> torch.Tensor:
+        return torch.empty((count, self.params.ct_bytes), dtype=torch.uint8, device="cuda")
+
+    # ---- KEM -----------------------------------------------------------
+    def keygen(self, seeds: torch.Tensor, pk: torch.Tensor, sk: torch.Tensor,
+               A_out: torch.Tensor | None = None, stream=None):
+        count = seeds.shape[0] if seeds.dim() > 1 else seeds.numel() // 32
+        p = self.params
+        rc = _lib.lwe_keygen(
+            self._h, _ptr(seeds, torch.uint8, 32 * count, "seeds"), count,
+            _ptr(pk, torch.uint8, count * p.pk_bytes, "pk"),
+            _ptr(sk, torch.uint8, count * p.sk_bytes, "sk"),
+            _ptr(A_out, torch.int16, count * p.n * p.n * 2, "A_out"), _stream(stream))
+        _check(rc, "lwe_keygen")
+
+    def encaps(self, pk: torch.Tensor, coins: torch.Tensor, ct: torch.Tensor, K: torch.Tensor,
+               A: torch.Tensor | None = None, stream=None):
+        count = coins.shape[0] if coins.dim() > 1 else coins.numel() // 32
+        p = self.params
+        rc = _lib.lwe_encaps(
+            self._h, _ptr(pk, torch.uint8, p.pk_bytes, "pk"),
+            _ptr(A, torch.int16, p.n * p.n * 2, "A"),
+            _ptr(coins, torch.uint8, 32 * count, "coins"), count,
+            _ptr(ct, torch.uint8, count * p.ct_bytes, "ct"),
+            _ptr(K, torch.uint8, 32 * count, "K"), _stream(stream))
+        _check(rc, "lwe_encaps")
+
+    def decaps(self, sk: torch.Tensor, ct: torch.Tensor, K: torch.Tensor,
+               A: torch.Tensor | None = None, stream=None, count: int | None = None):
+        p = self.params
+        if count is None:
+            count = ct.shape[0] if ct.dim() > 1 else ct.numel() // p.ct_bytes
+        rc = _lib.lwe_decaps(
+            self._h, _ptr(sk, torch.uint8, p.sk_bytes, "sk"),
+            _ptr(A, torch.int16, p.n * p.n * 2, "A"),
+            _ptr(ct, torch.uint8, count * p.ct_bytes, "ct"), count,
+            _ptr(K, torch.uint8, 32 * count, "K"), _stream(stream))
+        _check(rc, "lwe_decaps")
+
+
+def expand_A(seedA: torch.Tensor, n: int, logq: int, A_out: torch.Tensor, stream=None):
+    """A (n x n, int16 storage of uint16 values) from a 16-byte device seed."""
+    rc = _lib.lwe_expand_A(_ptr(seedA, torch.uint8, 16, "seedA"), n, logq,
+                           _ptr(A_out, torch.int16, n * n * 2, "A_out"), _stream(stream))
+    _check(rc, "lwe_expand_A")
+
+
+def matmul_modq(side: int, S: torch.Tensor, out: torch.Tensor, n: int, logq: int,
+                A: torch.Tensor | None = None, seedA: torch.Tensor | None = None,
+                E: torch.Tensor | None = None, ctx: Ctx | None = None, stream=None):
+    """side AS: out[n][8] = A S + E (S given as S^T, 8 x n);
+    side SA: out[k][n] = S A + E (S k x n)."""
+    k = S.shape[0]
+    rc = _lib.lwe_matmul_modq(
+        ctx.handle if ctx is not None else None, side,
+        _ptr(A, torch.int16, n * n * 2, "A"), _ptr(seedA, torch.uint8, 16, "seedA"),
+        _ptr(S, torch.int8, k * n, "S"), n, k, logq, _ptr(E, torch.int8, k * n, "E"),
+        _ptr(out, torch.int16, k * n * 2, "out"), _stream(stream))
+    _check(rc, "lwe_matmul_modq")
+
+
+def kernel_names():
+    return [_lib.lwe_kernel_name(i).decode() for i in range(_lib.lwe_num_kernels())]

@@ -1,0 +1,130 @@
+"""GPU parity of the batched tensor-core path (stacked S' times [A | B] as an
+exact two-limb bf16 tcgen05 GEMM) against the CPU oracle.
+
+Sizes span several 128-row tiles and 64/128-column tiles with ragged M, N
+and K tails; the worst-case limb magnitudes check that the fp32 accumulation
+stays exact.  All comparisons are bit-exact."""
+import numpy as np
+import pytest
+import torch
+
+from gpu_util import (O, PRESETS, as_u16, cfg_key, coins, dev, host, lwe, master_seeds,
+                      oracle_keys, params)
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _device():
+    assert torch.cuda.is_available()
+    torch.cuda.set_device(0)
+
+
+def _sa_ctx(n, logq, items, bn=128, clip=12):
+    p = lwe.Params(n=n, logq=logq, B=2, clip=clip, sigma=2.8 if clip == 12 else 2.3)
+    ctx = lwe.Ctx(p, max_batch=items)
+    ctx.set_path(lwe.PATH_TENSOR)
+    ctx.set_option(lwe.OPT_GEMM_BN, bn)
+    return ctx
+
+
+@pytest.mark.parametrize("n,logq,items", [(64, 16, 1), (80, 15, 17), (208, 16, 16),
+                                          (976, 16, 37), (1344, 16, 20)])
+@pytest.mark.parametrize("stored", [True, False])
+@pytest.mark.parametrize("bn", [128, 64])
+def test_matmul_modq_SA_tensor_matches_oracle(n, logq, items, stored, bn):
+    k = 8 * items
+    r = np.random.default_rng(n * items + bn)
+    seed = r.integers(0, 256, 16, dtype=np.uint8)
+    A_o = O.expand_A(bytes(seed), n, logq)
+    S = r.integers(-12, 13, size=(k, n), dtype=np.int8)
+    E = r.integers(-12, 13, size=(k, n), dtype=np.int8)
+    ctx = _sa_ctx(n, logq, items, bn)
+    out = torch.empty((k, n), dtype=torch.int16, device="cuda")
+    A = dev(A_o.view(np.int16)) if stored else None
+    lwe.matmul_modq(lwe.SIDE_SA, dev(S), out, n, logq, A=A, seedA=dev(seed), E=dev(E), ctx=ctx)
+    assert np.array_equal(as_u16(out), O.mul_SA(S, A_o, E, logq))
+    assert ctx.device_error() == 0
+
+
+@pytest.mark.parametrize("clip", [10, 12])
+def test_tensor_exact_at_worst_case_limbs(clip):
+    """A = 0x8080 splits into the extreme limbs (-128, -127); S = +c makes
+    every partial sum as large as the accumulator ever sees."""
+    n, logq, items = 976, 16, 16
+    k = 8 * items
+    A_o = np.full((n, n), 0x8080, dtype=np.uint16)
+    S = np.full((k, n), clip, dtype=np.int8)
+    S[1::2] = -clip
+    ctx = _sa_ctx(n, logq, items, clip=clip)
+    out = torch.empty((k, n), dtype=torch.int16, device="cuda")
+    lwe.matmul_modq(lwe.SIDE_SA, dev(S), out, n, logq, A=dev(A_o.view(np.int16)), ctx=ctx)
+    assert np.array_equal(as_u16(out), O.mul_SA(S, A_o, None, logq))
+
+
+@pytest.mark.parametrize("name,count", [("P640", 21), ("P976", 37), ("P1344", 19)])
+@pytest.mark.parametrize("stored", [True, False])
+def test_kem_tensor_path_matches_oracle(name, count, stored):
+    cfg = PRESETS[name]
+    p, po = params(name)
+    pk_o, sk_o, A_o, ms = oracle_keys(cfg_key(cfg), 21)
+    ctx = lwe.Ctx(p, max_batch=count)
+    ctx.set_path(lwe.PATH_TENSOR)
+    pk, sk = ctx.empty_pk(1), ctx.empty_sk(1)
+    A = torch.empty((p.n, p.n), dtype=torch.int16, device="cuda") if stored else None
+    ctx.keygen(dev(ms[None, :]), pk, sk, A_out=A)
+    cs = coins(count, seed=31)
+    ct = ctx.empty_ct(count)
+    K = torch.empty((count, 32), dtype=torch.uint8, device="cuda")
+    ctx.encaps(pk, dev(cs), ct, K, A=A)
+    K2 = torch.empty_like(K)
+    ctx.decaps(sk, ct, K2, A=A)
+    bad = ct.clone()
+    bad[::3, 7] ^= 2
+    bad[1::3, -3] ^= 1
+    Kb = torch.empty_like(K)
+    ctx.decaps(sk, bad, Kb, A=A)
+    ct_h, K_h, K2_h, Kb_h, bad_h = host(ct), host(K), host(K2), host(Kb), host(bad)
+    for i in range(count):
+        ct_o, K_o = O.encaps(po, pk_o, bytes(cs[i]), A=A_o)
+        assert np.array_equal(ct_h[i], ct_o), i
+        assert np.array_equal(K_h[i], K_o), i
+        assert np.array_equal(K2_h[i], K_o), i
+    for i in list(range(0, count, 3)) + list(range(1, count, 3))[:3]:
+        assert np.array_equal(Kb_h[i], O.decaps(po, sk_o, bad_h[i], A=A_o)), i
+    assert ctx.device_error() == 0
+
+
+def test_batched_4096_tensor_equals_skinny_and_oracle_samples():
+    """The benchmarked workload: one P976 key, 4096 encapsulations then the
+    4096 decapsulations, on the tensor path; every item equals the CUDA-core
+    path's, and sampled items equal the oracle's."""
+    name, count = "P976", 4096
+    cfg = PRESETS[name]
+    p, po = params(name)
+    pk_o, sk_o, A_o, ms = oracle_keys(cfg_key(cfg), 21)
+    ctx = lwe.Ctx(p, max_batch=count)
+    pk, sk = ctx.empty_pk(1), ctx.empty_sk(1)
+    A = torch.empty((p.n, p.n), dtype=torch.int16, device="cuda")
+    ctx.keygen(dev(ms[None, :]), pk, sk, A_out=A)
+    cs = coins(count, seed=4096)
+    res = {}
+    for path in (lwe.PATH_TENSOR, lwe.PATH_SKINNY):
+        ctx.set_path(path)
+        ct = ctx.empty_ct(count)
+        K = torch.empty((count, 32), dtype=torch.uint8, device="cuda")
+        ctx.encaps(pk, dev(cs), ct, K, A=A)
+        K2 = torch.empty_like(K)
+        ctx.decaps(sk, ct, K2, A=A)
+        res[path] = (host(ct), host(K), host(K2))
+    ct_t, K_t, K2_t = res[lwe.PATH_TENSOR]
+    ct_s, K_s, K2_s = res[lwe.PATH_SKINNY]
+    assert np.array_equal(ct_t, ct_s)
+    assert np.array_equal(K_t, K_s)
+    assert np.array_equal(K2_t, K_t)
+    assert np.array_equal(K2_s, K_s)
+    for i in [0, 1, 777, 2048, 4095]:
+        ct_o, K_o = O.encaps(po, pk_o, bytes(cs[i]), A=A_o)
+        assert np.array_equal(ct_t[i], ct_o), i
+        assert np.array_equal(K_t[i], K_o), i
+    assert ctx.device_error() == 0
