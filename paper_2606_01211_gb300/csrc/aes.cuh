@@ -58,7 +58,7 @@ LWE_DEV void aes_key_expand(const AesTab &tab, const uint32_t key[4],
       t = tab.sbox(byte_of(t, 0)) | (tab.sbox(byte_of(t, 1)) << 8) |
           (tab.sbox(byte_of(t, 2)) << 16) | (tab.sbox(byte_of(t, 3)) << 24);
       t ^= rcon;
-      rcon = (rcon << 1) ^ ((rcon & 0x80u) ? 0x1bu : 0u);
+      rcon = ((rcon << 1) ^ ((rcon & 0x80u) ? 0x1bu : 0u)) & 0xffu;
     }
     rk[i] = rk[i - 4] ^ t;
   }

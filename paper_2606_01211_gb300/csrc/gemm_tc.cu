@@ -291,7 +291,6 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     // ---------------- epilogue ----------------
     const uint32_t q = warp & 3;  // TMEM lane quarter of this warp
     const uint32_t D = a.logq, mask = (1u << D) - 1u;
-    const uint32_t mm = mask | (mask << 16);
     uint32_t it = 0;
     for (uint32_t tile = blockIdx.x; tile < num_tiles; tile += gridDim.x, ++it) {
       const uint32_t acc = it & 1, use = it >> 1;
@@ -324,7 +323,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           }
           uint32_t w[8];
 #pragma unroll
-          for (int t = 0; t < 8; t++) w[t] = (v[2 * t] | (v[2 * t + 1] << 16)) & mm;
+          for (int t = 0; t < 8; t++) w[t] = (v[2 * t] & mask) | ((v[2 * t + 1] & mask) << 16);
           uint4 *o = reinterpret_cast<uint4 *>(obase + 2 * ((size_t)kk * a.n + c));
           if (a.cmp) {
             const uint4 o0 = o[0], o1 = o[1];
