@@ -195,6 +195,38 @@ int lwe_matmul_modq(lwe_ctx *ctx, int side, const uint16_t *A,
                     uint32_t k, uint32_t logq, const int8_t *E,
                     uint16_t *out, void *stream);
 
+/* ---- Encaps without any device allocation ------------------------------ */
+
+/* Size of the library's built-in scratch area.  Every GPU that loads
+ * liblwe.so keeps this much device memory reserved until the process exits. */
+#define LWE_NOALLOC_SCRATCH_BYTES (1024u * 1024u)
+
+/* Encaps exactly as lwe_encaps (same inputs, outputs, layouts and results;
+ * CUDA-core path), for callers that cannot allocate device memory and so
+ * cannot create an lwe_ctx: code that must not call cudaMalloc/cudaFree
+ * because the host application owns every device allocation through its own
+ * pool, or because a request path cannot afford an allocation's implicit
+ * synchronisation and latency.  The paper has no counterpart; this is a
+ * deployment convenience.
+ *
+ * Instead of a context workspace it uses one fixed scratch area compiled
+ * into the library (LWE_NOALLOC_SCRATCH_BYTES on each device).  The caller
+ * still passes every input and output buffer; the call makes no cudaMalloc,
+ * cudaFree or other allocating call.  It runs on the CURRENT device; the
+ * first call on a device looks up the scratch area's device address and
+ * uploads the AES table there (one-time set-up), so make that first call
+ * outside any stream capture.  The scratch holds about
+ *   count * (16 n + 32 ceil((16 n + 128) / 1024) + 176) bytes
+ * (each part rounded up to 256 bytes); a (params, count) that does not fit
+ * returns LWE_ECAPACITY, invalid parameters or pointers LWE_EINVAL.
+ * All calls on a device share the one area and it keeps the last call's
+ * contents: every byte a call reads is written by that same call first, but
+ * calls whose work overlaps on the GPU (different streams, or different host
+ * threads) race on it and give wrong results — serialise them. */
+int lwe_encaps_noalloc(const lwe_params *p, const uint8_t *pk,
+                       const uint16_t *A, const uint8_t *coins, uint32_t count,
+                       uint8_t *ct, uint8_t *K, void *stream);
+
 /* ---- diagnostics ------------------------------------------------------- */
 const char *lwe_strerror(int code);
 /* The last CUDA error string seen by this thread's calls ("" if none). */

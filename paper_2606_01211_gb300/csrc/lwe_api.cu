@@ -5,6 +5,7 @@
 // that makes up KeyGen, Encaps and Decaps (Alg. 1, 4, 5 of the paper).
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <mutex>
@@ -361,6 +362,32 @@ int set_device_of(lwe_ctx *c) {
 
 }  // namespace
 
+// ---- built-in scratch of lwe_encaps_noalloc ------------------------------
+// One fixed area per device, compiled into the library.  Host code must not
+// pass `g_noalloc_scratch` itself to a kernel (on the host it names a
+// stand-in, not device memory): its device address is looked up once per
+// device with cudaGetSymbolAddress while that device is current.
+static __device__ __align__(256) uint8_t g_noalloc_scratch[LWE_NOALLOC_SCRATCH_BYTES];
+
+namespace {
+
+std::mutex g_noalloc_mu;
+uint8_t *g_noalloc_addr[128];
+
+int noalloc_scratch(int dev, uint8_t **out) {
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  if (!g_noalloc_addr[dev]) {
+    void *ptr = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+    if (e != cudaSuccess) return cuda_fail(e);
+    g_noalloc_addr[dev] = static_cast<uint8_t *>(ptr);
+  }
+  *out = g_noalloc_addr[dev];
+  return LWE_OK;
+}
+
+}  // namespace
+
 extern "C" {
 
 int lwe_params_preset(int id, lwe_params *out) {
@@ -697,6 +724,67 @@ int lwe_matmul_modq(lwe_ctx *c, int side, const uint16_t *A, const uint8_t *seed
   sa.out_stride = 16ull * n;
   LAUNCH(c, A ? KID_MUL_SA : KID_MUL_SA_FUSED, st, launch_mul_sa(sa, items, A == nullptr, false, st));
   return check_launch();
+}
+
+int lwe_encaps_noalloc(const lwe_params *p, const uint8_t *pk, const uint16_t *A,
+                       const uint8_t *coins, uint32_t count, uint8_t *ct, uint8_t *K,
+                       void *stream) {
+  if (params_check(p) != LWE_OK) return LWE_EINVAL;
+  if (count == 0) return LWE_OK;
+  if (!pk || !coins || !ct || !K || !aligned16(pk) || !aligned16(coins) || !aligned16(ct) ||
+      !aligned16(K) || (A && !aligned16(A)))
+    return LWE_EINVAL;
+  const size_t n = p->n, Bm = count;
+  const uint32_t tree_m =
+      (uint32_t)((std::max(ct_bytes(*p), pk_bytes(*p)) + LWE_TREE_CHUNK - 1) / LWE_TREE_CHUNK);
+  size_t off = 0;
+  auto carve = [&](size_t bytes) {
+    size_t o = off;
+    off = align_up(off + bytes, 256);
+    return o;
+  };
+  const size_t o_seeds = carve(32 * Bm), o_mu = carve(32 * Bm), o_kp = carve(32 * Bm);
+  const size_t o_flags = carve(4 * Bm), o_pkh = carve(32);
+  const size_t o_leaves = carve(32 * (size_t)tree_m * Bm);
+  const size_t o_sp8 = carve(8 * n * Bm), o_ep8 = carve(8 * n * Bm), o_epp = carve(64 * Bm);
+  if (off > LWE_NOALLOC_SCRATCH_BYTES) return LWE_ECAPACITY;
+
+  int dev = 0, sms = 0;
+  int rc = current_device_setup(&dev, &sms);
+  if (rc) return rc;
+  uint8_t *ws = nullptr;
+  rc = noalloc_scratch(dev, &ws);
+  if (rc) return rc;
+
+  // a context that borrows the built-in scratch instead of owning memory
+  lwe_ctx c;
+  c.p = *p;
+  cdf_table(p->sigma, p->clip, c.T);
+  c.device = dev;
+  c.num_sms = sms;
+  c.max_batch = count;
+  c.path = LWE_PATH_SKINNY;
+  c.has_tensor = false;
+  c.tree_m = tree_m;
+  c.seeds = ws + o_seeds;
+  c.mu = ws + o_mu;
+  c.kp = ws + o_kp;
+  c.flags = reinterpret_cast<uint32_t *>(ws + o_flags);
+  c.pkh = ws + o_pkh;
+  c.leaves = ws + o_leaves;
+  c.sp8 = reinterpret_cast<int8_t *>(ws + o_sp8);
+  c.ep8 = reinterpret_cast<int8_t *>(ws + o_ep8);
+  c.epp = reinterpret_cast<int8_t *>(ws + o_epp);
+
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t pkb = pk_bytes(*p), ctb = ct_bytes(*p);
+  rc = hash_tree(&c, pk, pkb, (uint32_t)pkb, 1, TREE_DIGEST, c.pkh, 32, nullptr, 0, nullptr, st);
+  if (rc) return rc;
+  DeriveArgs da{coins, c.pkh, c.mu, c.kp, c.seeds, count, mu_bytes(*p)};
+  LAUNCH(&c, KID_DERIVE, st, launch_derive(da, st));
+  rc = run_encrypt(&c, pk, A, count, ct, false, st);
+  if (rc) return rc;
+  return hash_tree(&c, ct, ctb, (uint32_t)ctb, count, TREE_ENC_KEY, K, 32, nullptr, 0, nullptr, st);
 }
 
 const char *lwe_strerror(int code) {

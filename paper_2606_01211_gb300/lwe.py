@@ -68,6 +68,7 @@ def _load():
         "lwe_decaps": (i32, [vp, vp, vp, vp, u32, vp, vp]),
         "lwe_expand_A": (i32, [vp, u32, u32, vp, vp]),
         "lwe_matmul_modq": (i32, [vp, i32, vp, vp, vp, u32, u32, u32, vp, vp, vp]),
+        "lwe_encaps_noalloc": (i32, [P, vp, vp, vp, u32, vp, vp, vp]),
         "lwe_strerror": (C.c_char_p, [i32]),
         "lwe_last_cuda_error": (C.c_char_p, []),
         "lwe_ctx_device_error": (i32, [vp]),
