@@ -160,16 +160,38 @@ def run_reference(args, rank, world):
 
 
 # ----------------------------------------------------------------- ours ---
+def keccak_perms(length: int, chunk: int = 1024) -> int:
+    """Keccak-f[1600] calls of the tree hash of `length` bytes (SHA3-256 of
+    each chunk, rate 136 bytes with at least one padding byte)."""
+    full, last = divmod(length, chunk)
+    per = lambda L: L // 136 + 1
+    return full * per(chunk) + (per(last) if last else 0)
+
+
+# Derived peaks of the integer-bound kernels at the 2070 MHz maximum SM clock:
+#  AES round tables: 160 conflict-free shared-memory lookups per 16-byte block,
+#    32 per clock per SM  ->  152 * 2.07e9 * 32 / 160 * 16 B = 1006 GB/s
+#  Keccak-f[1600]: 132 integer-ALU operations per round (XOR / chi LOP3s; the
+#    rotations run as multiply-adds), 64 ALU lanes per clock per SM
+#    ->  152 * 2.07e9 * 64 / (132 * 24) = 6.35 G permutations/s
+AES_PEAK_GBS = 152 * 2.070e9 * 32 / 160 * 16 / 1e9
+KECCAK_PEAK_GPERMS = 152 * 2.070e9 * 64 / (132 * 24) / 1e9
+
+
 def algorithmic(p, count):
-    """Per-launch algorithmic work of the kernels of one step."""
+    """Algorithmic work of the kernels in one step (summed over launches)."""
     n = p.n
     rows, ncols = 8 * count, n + 8
+    ct_bytes, pk_bytes = 16 * n + 128, 16 + 16 * n
     return {
-        # two limbs, 2 flops per multiply-add
-        "k_gemm_tc": ("tensor", 2.0 * 2 * rows * ncols * n, "flop"),
+        # two limbs, 2 flops per multiply-add, Encaps + Decaps
+        "k_gemm_tc": ("tensor", 2 * (2.0 * 2 * rows * ncols * n), "TFLOP/s", 1e12),
         # AES keystream bytes: S', E' (8n samples each) and E'' (64) per item,
-        # 2 bytes per sample
-        "k_noise": ("alu", 2.0 * (16 * n + 64) * count, "keystream bytes"),
+        # 2 bytes per sample, Encaps + Decaps
+        "k_noise": ("alu", 2 * (2.0 * (16 * n + 64) * count), "GB/s of AES keystream", 1e9),
+        # Keccak-f calls: H(pk) once, H(c) in Encaps and in Decaps
+        "k_tree_leaves": ("alu", float(keccak_perms(pk_bytes) + 2 * count * keccak_perms(ct_bytes)),
+                          "G Keccak-f/s", 1e9),
     }
 
 
@@ -243,27 +265,25 @@ def run_ours(args, rank, world, local_rank):
     if rank != 0:
         return 0
 
-    # roofline of the dominant kernel (largest share of the timed region)
+    # roofline of the dominant kernel (largest share of the timed region):
+    # algorithmic work of the timed steps / the kernel's summed event time
     kernel_total = {k: v[1] for k, v in stats.items()}
     dom = max(kernel_total, key=kernel_total.get)
     alg = algorithmic(p, COUNT)
     roof = None
     if dom in alg:
-        bound, work, what = alg[dom]
+        bound, work, unit, scale = alg[dom]
         nl, ms_tot = stats[dom]
-        per_launch_ms = ms_tot / nl
+        ach = work * args.steps / (ms_tot / 1e3) / scale
         if bound == "tensor":
-            ach = work / (per_launch_ms / 1e3) / 1e12
             peak = pk_d.get("bf16_tflops_sustained", pk_d["bf16_tflops"])
-            roof = {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
-                    "frac": ach / peak}
+        elif dom == "k_noise":
+            peak = AES_PEAK_GBS
         else:
-            ach = work / (per_launch_ms / 1e3) / 1e9
-            roof = {"bound": "alu", "achieved": ach, "peak": args.aes_peak_gbs,
-                    "unit": "GB/s of AES keystream", "frac": ach / args.aes_peak_gbs}
-        roof["kernel"] = dom
-        roof["share"] = kernel_total[dom] / sum(kernel_total.values())
-        roof["traffic"] = None
+            peak = KECCAK_PEAK_GPERMS
+        roof = {"bound": bound, "achieved": ach, "peak": peak, "unit": unit, "frac": ach / peak,
+                "kernel": dom, "launches_per_step": nl / args.steps,
+                "share": kernel_total[dom] / sum(kernel_total.values()), "traffic": None}
 
     # end to end through the public API with host buffers
     e2e = None
@@ -304,6 +324,9 @@ def run_ours(args, rank, world, local_rank):
         plain = COUNT / (a.elapsed_time(b) / 1e3)
         ctx.set_path(lwe.PATH_TENSOR)
 
+    latency = None if args.no_latency else single_request_latency(lwe, torch, dev)
+    as_sweep = None if args.no_sweep else as_gbs_sweep(lwe, torch, dev, flush)
+
     cpu = None
     if not args.no_cpu:
         rate, threads, pairs, el = cpu_oracle_rate(target_s=args.cpu_s)
@@ -326,10 +349,76 @@ def run_ours(args, rank, world, local_rank):
         "plain_path_value": plain,
         "batched_vs_plain": (value / world / plain) if plain else None,
         "kernels_ms_per_step": {k: v[1] / args.steps for k, v in stats.items()},
+        "latency_p640_us": latency,
+        "as_gbs": as_sweep,
         "correct": bool(ok) and err == 0,
     }
     print(json.dumps(line))
     return 0
+
+
+def single_request_latency(lwe, torch, dev, reps: int = 300):
+    """One P640 KeyGen, Encaps, Decaps per call (stored A), host wall-clock
+    per call including the synchronisation: p50 / p99 in microseconds."""
+    p = lwe.Params(**PRESETS["P640"])
+    ctx = lwe.Ctx(p, max_batch=1, device=dev.index)
+    ctx.set_path(lwe.PATH_SKINNY)
+    pk, sk = ctx.empty_pk(1), ctx.empty_sk(1)
+    A = torch.empty((p.n, p.n), dtype=torch.int16, device=dev)
+    ms = torch.from_numpy(master_seeds(reps, seed=5)).to(dev)
+    cs = torch.from_numpy(coins(reps, seed=5)).to(dev)
+    ct = ctx.empty_ct(1)
+    K = torch.empty((1, 32), dtype=torch.uint8, device=dev)
+    K2 = torch.empty_like(K)
+    t = {"keygen": [], "encaps": [], "decaps": [], "cycle": []}
+    torch.cuda.synchronize()
+    for i in range(reps):
+        t0 = time.perf_counter()
+        ctx.keygen(ms[i:i + 1], pk, sk, A_out=A)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        ctx.encaps(pk, cs[i:i + 1], ct, K, A=A)
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
+        ctx.decaps(sk, ct, K2, A=A)
+        torch.cuda.synchronize()
+        t3 = time.perf_counter()
+        if i >= 20:
+            t["keygen"].append(t1 - t0)
+            t["encaps"].append(t2 - t1)
+            t["decaps"].append(t3 - t2)
+            t["cycle"].append(t3 - t0)
+    assert torch.equal(K, K2)
+    ctx.close()
+    return {k: {"p50": float(np.percentile(v, 50) * 1e6), "p99": float(np.percentile(v, 99) * 1e6)}
+            for k, v in t.items()}
+
+
+def as_gbs_sweep(lwe, torch, dev, flush, sizes=(1344, 2048, 4096, 8192), reps: int = 5):
+    """lwe_matmul_modq A S (stored A, n x 8 secret): bytes of A read per
+    second, L2 flushed before every timed call."""
+    out = {}
+    stream = torch.cuda.current_stream()
+    for n in sizes:
+        A = torch.empty((n, n), dtype=torch.int16, device=dev)
+        seed = torch.arange(16, dtype=torch.uint8, device=dev)
+        lwe.expand_A(seed, n, 16, A)
+        St = torch.randint(-6, 7, (8, n), dtype=torch.int8, device=dev)
+        o = torch.empty((n, 8), dtype=torch.int16, device=dev)
+        ts = []
+        for r in range(reps + 1):
+            flush.fill_(r)
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            lwe.matmul_modq(lwe.SIDE_AS, St, o, n, 16, A=A)
+            b.record(stream)
+            torch.cuda.synchronize()
+            if r:
+                ts.append(a.elapsed_time(b) / 1e3)
+        out[str(n)] = 2.0 * n * n / statistics.median(ts) / 1e9
+        del A
+    return out
 
 
 def main():
@@ -341,11 +430,10 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-latency", action="store_true")
+    ap.add_argument("--no-sweep", action="store_true")
     ap.add_argument("--cpu-s", type=float, default=12.0)
     ap.add_argument("--ref-step-s", type=float, default=8.0)
-    # AES keystream peak (GB/s): 152 SMs x 2070 MHz x 32 shared-memory
-    # lookups per clock / 160 lookups per 16-byte block
-    ap.add_argument("--aes-peak-gbs", type=float, default=152 * 2.070e9 * 32 / 160 * 16 / 1e9)
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -5,46 +5,63 @@
 // here with AES-128 (FIPS-197) in counter mode: the keystream block for
 // (domain d, index b) is AES_k(BE64(d) || BE64(b)).
 //
-// Implementation: the 4x32-bit round-table formulation of AES (SubBytes +
-// ShiftRows + MixColumns folded into one table T0 of 256 words and its byte
-// rotations), with the state held little-endian in four registers.  The table
-// lives in shared memory replicated 32 times so that lane l always reads bank
-// l: a warp's 32 lookups are one conflict-free wavefront.  The last round
-// takes the S-box from the bytes of T0 that hold S(x).
+// Implementation: the round-table formulation of AES (SubBytes + ShiftRows +
+// MixColumns folded into four 256-word tables T0..T3, Tk = T0 rotated left
+// by 8k), state held little-endian in four registers.  The tables live in
+// shared memory, each replicated 32 times so that lane l only ever reads
+// bank l (conflict-free).  The layout is chosen so that ONE byte-permute
+// instruction forms a lookup address: entry x of table k for lane l sits at
+//     (k >> 1) * 65536 + x * 256 + (k & 1) * 128 + 4 l   bytes,
+// and prmt(state, 4 l) with the state byte placed in byte 1 yields
+// x * 256 + 4 l; the table is selected by the instruction's immediate offset.
+// This keeps the integer ALU pipe (half the lane rate of the FMA pipe on
+// this part) to one permute per lookup plus the XORs.  The last round and the
+// key schedule read S(x) from the table whose byte in the needed position
+// holds S(x) (T0 holds S in bytes 1 and 2).
 #pragma once
 #include "common.cuh"
 
-// T0[x] = 2.S(x) | S(x) << 8 | S(x) << 16 | 3.S(x) << 24  (little-endian
-// column contribution of the row-0 byte); filled by the host at start-up.
-#define AES_TABLE_WORDS (256 * 32)
-#define AES_SMEM_BYTES (AES_TABLE_WORDS * 4)
+// T0[x] = 2.S(x) | S(x) << 8 | S(x) << 16 | 3.S(x) << 24, filled by the host.
+#define AES_TABLE_WORDS (2 * 16384)
+#define AES_SMEM_BYTES (AES_TABLE_WORDS * 4)  // 128 KB
 
-// Replicate the 256-word table so that entry x for lane l sits at x*32 + l.
 LWE_DEV void aes_fill_smem(uint32_t *sT, const uint32_t *T0g) {
-  for (int i = threadIdx.x; i < AES_TABLE_WORDS; i += blockDim.x)
-    sT[i] = T0g[i >> 5];
+  for (int i = threadIdx.x; i < AES_TABLE_WORDS; i += blockDim.x) {
+    const int k = 2 * (i >> 14) + ((i >> 5) & 1);
+    const uint32_t v = T0g[(i >> 6) & 255];
+    sT[i] = k ? rotl32(v, 8 * k) : v;
+  }
 }
 
 struct AesTab {
-  const uint32_t *lane_base;  // sT + lane
-  LWE_DEV uint32_t t0(uint32_t byte) const { return lane_base[byte << 5]; }
-  LWE_DEV uint32_t sbox(uint32_t byte) const { return (t0(byte) >> 8) & 0xffu; }
+  const char *base;  // shared-memory tables
+  uint32_t lane4;    // 4 * lane in byte 0
+
+  // entry T_K[byte BYTE of s] for this lane
+  template <int K, int BYTE>
+  LWE_DEV uint32_t T(uint32_t s) const {
+    const uint32_t off = __byte_perm(s, lane4, 0x5504 | (BYTE << 4));
+    return *reinterpret_cast<const uint32_t *>(base + off + (K >> 1) * 65536 + (K & 1) * 128);
+  }
 };
 
 LWE_DEV AesTab aes_tab(const uint32_t *sT) {
   AesTab t;
-  t.lane_base = sT + (threadIdx.x & 31);
+  t.base = reinterpret_cast<const char *>(sT);
+  t.lane4 = (threadIdx.x & 31) << 2;
   return t;
 }
 
-LWE_DEV uint32_t byte_of(uint32_t w, int k) {
-  return __byte_perm(w, 0, 0x4440 | k);
+// SubWord(RotWord(w)) for a little-endian word: output byte r is S(byte
+// r+1 of w), read from the table holding S at byte r (T3, T0, T1, T2).
+LWE_DEV uint32_t aes_subrot(const AesTab &tab, uint32_t w) {
+  return (tab.T<3, 1>(w) & 0x000000ffu) | (tab.T<0, 2>(w) & 0x0000ff00u) |
+         (tab.T<1, 3>(w) & 0x00ff0000u) | (tab.T<2, 0>(w) & 0xff000000u);
 }
 
-// FIPS-197 5.2 key expansion on little-endian words.  RotWord of a
-// little-endian word is a right rotation by 8; Rcon enters the low byte.
-LWE_DEV void aes_key_expand(const AesTab &tab, const uint32_t key[4],
-                            uint32_t rk[44]) {
+// FIPS-197 5.2 key expansion on little-endian words; Rcon enters byte 0 and
+// stays in GF(2^8).
+LWE_DEV void aes_key_expand(const AesTab &tab, const uint32_t key[4], uint32_t rk[44]) {
   rk[0] = key[0];
   rk[1] = key[1];
   rk[2] = key[2];
@@ -54,63 +71,43 @@ LWE_DEV void aes_key_expand(const AesTab &tab, const uint32_t key[4],
   for (int i = 4; i < 44; i++) {
     uint32_t t = rk[i - 1];
     if ((i & 3) == 0) {
-      t = __funnelshift_r(t, t, 8);
-      t = tab.sbox(byte_of(t, 0)) | (tab.sbox(byte_of(t, 1)) << 8) |
-          (tab.sbox(byte_of(t, 2)) << 16) | (tab.sbox(byte_of(t, 3)) << 24);
-      t ^= rcon;
+      t = aes_subrot(tab, t) ^ rcon;
       rcon = ((rcon << 1) ^ ((rcon & 0x80u) ? 0x1bu : 0u)) & 0xffu;
     }
     rk[i] = rk[i - 4] ^ t;
   }
 }
 
-// One AES-128 encryption of the little-endian state (s0..s3).
-LWE_DEV void aes_encrypt(const AesTab &tab, const uint32_t rk[44],
-                         uint32_t &s0, uint32_t &s1, uint32_t &s2,
-                         uint32_t &s3) {
+// One AES-128 encryption of the little-endian state (s0..s3).  New column c
+// takes row k from old column c + k (ShiftRows); the row-k contribution is
+// T_k (MixColumns).
+LWE_DEV void aes_encrypt(const AesTab &tab, const uint32_t rk[44], uint32_t &s0, uint32_t &s1,
+                         uint32_t &s2, uint32_t &s3) {
   s0 ^= rk[0];
   s1 ^= rk[1];
   s2 ^= rk[2];
   s3 ^= rk[3];
 #pragma unroll
   for (int r = 1; r < 10; r++) {
-    // new column c takes row k from old column c + k (ShiftRows); the
-    // row-k contribution is T0 rotated left by 8k (MixColumns)
-    uint32_t t0 = tab.t0(byte_of(s0, 0)) ^ rotl32(tab.t0(byte_of(s1, 1)), 8) ^
-                  rotl32(tab.t0(byte_of(s2, 2)), 16) ^
-                  rotl32(tab.t0(byte_of(s3, 3)), 24) ^ rk[4 * r + 0];
-    uint32_t t1 = tab.t0(byte_of(s1, 0)) ^ rotl32(tab.t0(byte_of(s2, 1)), 8) ^
-                  rotl32(tab.t0(byte_of(s3, 2)), 16) ^
-                  rotl32(tab.t0(byte_of(s0, 3)), 24) ^ rk[4 * r + 1];
-    uint32_t t2 = tab.t0(byte_of(s2, 0)) ^ rotl32(tab.t0(byte_of(s3, 1)), 8) ^
-                  rotl32(tab.t0(byte_of(s0, 2)), 16) ^
-                  rotl32(tab.t0(byte_of(s1, 3)), 24) ^ rk[4 * r + 2];
-    uint32_t t3 = tab.t0(byte_of(s3, 0)) ^ rotl32(tab.t0(byte_of(s0, 1)), 8) ^
-                  rotl32(tab.t0(byte_of(s1, 2)), 16) ^
-                  rotl32(tab.t0(byte_of(s2, 3)), 24) ^ rk[4 * r + 3];
+    const uint32_t t0 = tab.T<0, 0>(s0) ^ tab.T<1, 1>(s1) ^ tab.T<2, 2>(s2) ^ tab.T<3, 3>(s3) ^ rk[4 * r + 0];
+    const uint32_t t1 = tab.T<0, 0>(s1) ^ tab.T<1, 1>(s2) ^ tab.T<2, 2>(s3) ^ tab.T<3, 3>(s0) ^ rk[4 * r + 1];
+    const uint32_t t2 = tab.T<0, 0>(s2) ^ tab.T<1, 1>(s3) ^ tab.T<2, 2>(s0) ^ tab.T<3, 3>(s1) ^ rk[4 * r + 2];
+    const uint32_t t3 = tab.T<0, 0>(s3) ^ tab.T<1, 1>(s0) ^ tab.T<2, 2>(s1) ^ tab.T<3, 3>(s2) ^ rk[4 * r + 3];
     s0 = t0;
     s1 = t1;
     s2 = t2;
     s3 = t3;
   }
-  // final round: SubBytes + ShiftRows + AddRoundKey.  S(x) is byte 1 and
-  // byte 2 of T0[x].
-  uint32_t o0 = ((tab.t0(byte_of(s0, 0)) >> 8) & 0x000000ffu) |
-                (tab.t0(byte_of(s1, 1)) & 0x0000ff00u) |
-                (tab.t0(byte_of(s2, 2)) & 0x00ff0000u) |
-                ((tab.t0(byte_of(s3, 3)) << 16) & 0xff000000u);
-  uint32_t o1 = ((tab.t0(byte_of(s1, 0)) >> 8) & 0x000000ffu) |
-                (tab.t0(byte_of(s2, 1)) & 0x0000ff00u) |
-                (tab.t0(byte_of(s3, 2)) & 0x00ff0000u) |
-                ((tab.t0(byte_of(s0, 3)) << 16) & 0xff000000u);
-  uint32_t o2 = ((tab.t0(byte_of(s2, 0)) >> 8) & 0x000000ffu) |
-                (tab.t0(byte_of(s3, 1)) & 0x0000ff00u) |
-                (tab.t0(byte_of(s0, 2)) & 0x00ff0000u) |
-                ((tab.t0(byte_of(s1, 3)) << 16) & 0xff000000u);
-  uint32_t o3 = ((tab.t0(byte_of(s3, 0)) >> 8) & 0x000000ffu) |
-                (tab.t0(byte_of(s0, 1)) & 0x0000ff00u) |
-                (tab.t0(byte_of(s1, 2)) & 0x00ff0000u) |
-                ((tab.t0(byte_of(s2, 3)) << 16) & 0xff000000u);
+  // final round: SubBytes + ShiftRows + AddRoundKey; output byte r of a
+  // column is S(x), read from the table with S at byte r
+  const uint32_t o0 = (tab.T<3, 0>(s0) & 0x000000ffu) | (tab.T<0, 1>(s1) & 0x0000ff00u) |
+                      (tab.T<1, 2>(s2) & 0x00ff0000u) | (tab.T<2, 3>(s3) & 0xff000000u);
+  const uint32_t o1 = (tab.T<3, 0>(s1) & 0x000000ffu) | (tab.T<0, 1>(s2) & 0x0000ff00u) |
+                      (tab.T<1, 2>(s3) & 0x00ff0000u) | (tab.T<2, 3>(s0) & 0xff000000u);
+  const uint32_t o2 = (tab.T<3, 0>(s2) & 0x000000ffu) | (tab.T<0, 1>(s3) & 0x0000ff00u) |
+                      (tab.T<1, 2>(s0) & 0x00ff0000u) | (tab.T<2, 3>(s1) & 0xff000000u);
+  const uint32_t o3 = (tab.T<3, 0>(s3) & 0x000000ffu) | (tab.T<0, 1>(s0) & 0x0000ff00u) |
+                      (tab.T<1, 2>(s1) & 0x00ff0000u) | (tab.T<2, 3>(s2) & 0xff000000u);
   s0 = o0 ^ rk[40];
   s1 = o1 ^ rk[41];
   s2 = o2 ^ rk[42];
@@ -119,8 +116,8 @@ LWE_DEV void aes_encrypt(const AesTab &tab, const uint32_t rk[44],
 
 // Keystream block (domain, index) as four little-endian words: the sixteen
 // output bytes in order, i.e. eight little-endian 16-bit words.
-LWE_DEV uint4 aes_ctr_block(const AesTab &tab, const uint32_t rk[44],
-                            uint64_t domain, uint64_t index) {
+LWE_DEV uint4 aes_ctr_block(const AesTab &tab, const uint32_t rk[44], uint64_t domain,
+                            uint64_t index) {
   uint32_t s0 = bswap32((uint32_t)(domain >> 32));
   uint32_t s1 = bswap32((uint32_t)domain);
   uint32_t s2 = bswap32((uint32_t)(index >> 32));
@@ -142,5 +139,27 @@ LWE_DEV void aes_load_key(const uint8_t *key, uint32_t k[4]) {
     for (int i = 0; i < 4; i++)
       k[i] = (uint32_t)key[4 * i] | ((uint32_t)key[4 * i + 1] << 8) |
              ((uint32_t)key[4 * i + 2] << 16) | ((uint32_t)key[4 * i + 3] << 24);
+  }
+}
+
+// Key expansion from the plain 256-word table in global memory, for kernels
+// that do not hold the shared tables (one key per thread, off the hot loop).
+LWE_DEV void aes_key_expand_global(const uint32_t *T0g, const uint32_t key[4], uint32_t rk[44]) {
+  rk[0] = key[0];
+  rk[1] = key[1];
+  rk[2] = key[2];
+  rk[3] = key[3];
+  uint32_t rcon = 1;
+#pragma unroll
+  for (int i = 4; i < 44; i++) {
+    uint32_t t = rk[i - 1];
+    if ((i & 3) == 0) {
+      t = __funnelshift_r(t, t, 8);
+      t = ((T0g[t & 0xff] >> 8) & 0xffu) | (T0g[(t >> 8) & 0xff] & 0xff00u) |
+          (T0g[(t >> 16) & 0xff] & 0xff0000u) | ((T0g[t >> 24] << 16) & 0xff000000u);
+      t ^= rcon;
+      rcon = ((rcon << 1) ^ ((rcon & 0x80u) ? 0x1bu : 0u)) & 0xffu;
+    }
+    rk[i] = rk[i - 4] ^ t;
   }
 }

@@ -303,53 +303,73 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       uint8_t *obase = a.out + (size_t)e * a.out_stride;
       const uint32_t tl = tmem_base + ((32 * q) << 16) + acc * (2 * BN);
       uint32_t diff = 0;
-#pragma unroll 1
+      // global operands of the epilogue (E' and, for Decaps, the received
+      // B'), prefetched one 16-column chunk ahead of their use
+      uint4 e_cur = make_uint4(0, 0, 0, 0), o_cur0 = e_cur, o_cur1 = e_cur;
+      auto fetch = [&](uint32_t cc, uint4 &ev, uint4 &o0, uint4 &o1) {
+        const uint32_t c = n0 + 16 * cc;
+        if (rv && c < a.n) {
+          if (a.E) ev = __ldg(reinterpret_cast<const uint4 *>(a.E + (size_t)row * a.n + c));
+          if (a.cmp) {
+            const uint4 *o = reinterpret_cast<const uint4 *>(obase + 2 * ((size_t)kk * a.n + c));
+            o0 = __ldg(o);
+            o1 = __ldg(o + 1);
+          }
+        }
+      };
+      fetch(0, e_cur, o_cur0, o_cur1);
+#pragma unroll
       for (uint32_t cc = 0; cc < BN / 16; cc++) {
         const uint32_t c = n0 + 16 * cc;
         uint32_t lo[16], hi[16];
         tmem_ld16(tl + 16 * cc, lo);
         tmem_ld16(tl + BN + 16 * cc, hi);
+        uint4 e_nxt = make_uint4(0, 0, 0, 0), o_nxt0 = e_nxt, o_nxt1 = e_nxt;
+        if (cc + 1 < BN / 16) fetch(cc + 1, e_nxt, o_nxt0, o_nxt1);
         tmem_wait_ld();
-        if (!rv || c >= a.ncols) continue;
-        uint32_t v[16];
+        if (rv && c < a.ncols) {
+          uint32_t v[16];
 #pragma unroll
-        for (int t = 0; t < 16; t++) v[t] = fold(lo[t], hi[t]);
-        if (c < a.n) {  // B' columns: 16 at once (n is a multiple of 16)
-          if (a.E) {
-            const uint4 ev = *reinterpret_cast<const uint4 *>(a.E + (size_t)row * a.n + c);
-            const uint32_t ew[4] = {ev.x, ev.y, ev.z, ev.w};
+          for (int t = 0; t < 16; t++) v[t] = fold(lo[t], hi[t]);
+          if (c < a.n) {  // B' columns: 16 at once (n is a multiple of 16)
+            if (a.E) {
+              const uint32_t ew[4] = {e_cur.x, e_cur.y, e_cur.z, e_cur.w};
 #pragma unroll
-            for (int t = 0; t < 16; t++) v[t] += (uint32_t)sext8(ew[t >> 2], t & 3);
-          }
-          uint32_t w[8];
+              for (int t = 0; t < 16; t++) v[t] += (uint32_t)sext8(ew[t >> 2], t & 3);
+            }
+            uint32_t w[8];
 #pragma unroll
-          for (int t = 0; t < 8; t++) w[t] = (v[2 * t] & mask) | ((v[2 * t + 1] & mask) << 16);
-          uint4 *o = reinterpret_cast<uint4 *>(obase + 2 * ((size_t)kk * a.n + c));
-          if (a.cmp) {
-            const uint4 o0 = o[0], o1 = o[1];
-            diff |= (o0.x ^ w[0]) | (o0.y ^ w[1]) | (o0.z ^ w[2]) | (o0.w ^ w[3]) |
-                    (o1.x ^ w[4]) | (o1.y ^ w[5]) | (o1.z ^ w[6]) | (o1.w ^ w[7]);
-          } else {
-            o[0] = make_uint4(w[0], w[1], w[2], w[3]);
-            o[1] = make_uint4(w[4], w[5], w[6], w[7]);
-          }
-        } else {  // V columns n..n+7: C = V + E'' + Enc(mu)
-          const uint32_t Bb = a.B;
-          const uint8_t *mu = a.mu + 32 * (size_t)e + kk * Bb;
-          uint32_t bits = 0;
-          for (uint32_t t = 0; t < Bb; t++) bits |= (uint32_t)mu[t] << (8 * t);
-          const int8_t *epp = a.Epp + 64 * (size_t)e + 8 * kk;
-          uint16_t *co = reinterpret_cast<uint16_t *>(obase + 16 * (size_t)a.n) + 8 * kk;
+            for (int t = 0; t < 8; t++) w[t] = (v[2 * t] & mask) | ((v[2 * t + 1] & mask) << 16);
+            if (a.cmp) {
+              diff |= (o_cur0.x ^ w[0]) | (o_cur0.y ^ w[1]) | (o_cur0.z ^ w[2]) |
+                      (o_cur0.w ^ w[3]) | (o_cur1.x ^ w[4]) | (o_cur1.y ^ w[5]) |
+                      (o_cur1.z ^ w[6]) | (o_cur1.w ^ w[7]);
+            } else {
+              uint4 *o = reinterpret_cast<uint4 *>(obase + 2 * ((size_t)kk * a.n + c));
+              o[0] = make_uint4(w[0], w[1], w[2], w[3]);
+              o[1] = make_uint4(w[4], w[5], w[6], w[7]);
+            }
+          } else {  // V columns n..n+7: C = V + E'' + Enc(mu)
+            const uint32_t Bb = a.B;
+            const uint8_t *mu = a.mu + 32 * (size_t)e + kk * Bb;
+            uint32_t bits = 0;
+            for (uint32_t t = 0; t < Bb; t++) bits |= (uint32_t)mu[t] << (8 * t);
+            const int8_t *epp = a.Epp + 64 * (size_t)e + 8 * kk;
+            uint16_t *co = reinterpret_cast<uint16_t *>(obase + 16 * (size_t)a.n) + 8 * kk;
 #pragma unroll
-          for (int t = 0; t < 8; t++) {
-            const uint32_t sym = (bits >> (t * Bb)) & ((1u << Bb) - 1u);
-            const uint32_t cv = (v[t] + (uint32_t)(int)epp[t] + (sym << (D - Bb))) & mask;
-            if (a.cmp)
-              diff |= cv ^ (uint32_t)co[t];
-            else
-              co[t] = (uint16_t)cv;
+            for (int t = 0; t < 8; t++) {
+              const uint32_t sym = (bits >> (t * Bb)) & ((1u << Bb) - 1u);
+              const uint32_t cv = (v[t] + (uint32_t)(int)epp[t] + (sym << (D - Bb))) & mask;
+              if (a.cmp)
+                diff |= cv ^ (uint32_t)co[t];
+              else
+                co[t] = (uint16_t)cv;
+            }
           }
         }
+        e_cur = e_nxt;
+        o_cur0 = o_nxt0;
+        o_cur1 = o_nxt1;
       }
       tc_fence_before();
       mbar_arrive(tempty(acc));

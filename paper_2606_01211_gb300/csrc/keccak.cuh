@@ -17,6 +17,9 @@ __constant__ uint64_t kKeccakRC[24] = {
     0x000000000000800Aull, 0x800000008000000Aull, 0x8000000080008081ull,
     0x8000000000008080ull, 0x0000000080000001ull, 0x8000000080008008ull};
 
+// 64-bit rotation; compiles to a pair of funnel shifts.  (Rotations written
+// as multiply-adds to unload the integer ALU pipe were measured slower: more
+// instructions and longer dependency chains.)
 #define ROTL64(x, r) (((x) << (r)) | ((x) >> (64 - (r))))
 
 // Keccak-f[1600]: 24 rounds of theta, rho, pi, chi, iota.  Lane (x, y) is
@@ -96,51 +99,34 @@ LWE_DEV void sha3_digest16(const uint64_t s[25], uint8_t *out16) {
                  (uint32_t)(s[1] >> 32));
 }
 
-// SHA3-256 of `len` bytes at global address msg.  When msg is 8-byte
-// aligned, whole lanes are loaded with 64-bit reads.
+// SHA3-256 of `len` bytes at global address msg, which must be 8-byte
+// aligned: whole lanes are loaded with 64-bit reads and every state index is
+// a compile-time constant (the state stays in registers).
 LWE_DEV void sha3_256_global(const uint8_t *msg, uint32_t len, uint64_t s[25]) {
   sha3_init(s);
-  const bool aligned = (reinterpret_cast<uintptr_t>(msg) & 7) == 0;
+  const uint64_t *p = reinterpret_cast<const uint64_t *>(msg);
   uint32_t off = 0;
   while (len - off >= SHA3_RATE) {
-    if (aligned) {
-      const uint64_t *p = reinterpret_cast<const uint64_t *>(msg + off);
 #pragma unroll
-      for (int i = 0; i < SHA3_RATE / 8; i++) s[i] ^= __ldg(p + i);
-    } else {
-#pragma unroll 1
-      for (int i = 0; i < SHA3_RATE / 8; i++) {
-        uint64_t v = 0;
-        for (int b = 0; b < 8; b++) v |= (uint64_t)msg[off + 8 * i + b] << (8 * b);
-        s[i] ^= v;
-      }
-    }
+    for (int i = 0; i < SHA3_RATE / 8; i++) s[i] ^= __ldg(p + off / 8 + i);
     keccak_f1600(s);
     off += SHA3_RATE;
   }
   // final partial block with pad10*1 and the SHA-3 domain bits
-  uint32_t rem = len - off;
-  uint64_t lanes[SHA3_RATE / 8];
-#pragma unroll
-  for (int i = 0; i < SHA3_RATE / 8; i++) lanes[i] = 0;
+  const uint32_t rem = len - off;
 #pragma unroll
   for (int i = 0; i < SHA3_RATE / 8; i++) {
-    uint32_t base = 8 * i;
+    const uint32_t base = 8 * i;
+    uint64_t lane = 0;
     if (base + 8 <= rem) {
-      if (aligned)
-        lanes[i] = __ldg(reinterpret_cast<const uint64_t *>(msg + off + base));
-      else
-        for (int b = 0; b < 8; b++)
-          lanes[i] |= (uint64_t)msg[off + base + b] << (8 * b);
+      lane = __ldg(p + off / 8 + i);
     } else if (base < rem) {
-      for (uint32_t b = 0; b < rem - base; b++)
-        lanes[i] |= (uint64_t)msg[off + base + b] << (8 * b);
+      for (uint32_t b = 0; b < rem - base; b++) lane |= (uint64_t)msg[off + base + b] << (8 * b);
     }
-    if (base <= rem && rem < base + 8) lanes[i] ^= (uint64_t)0x06 << (8 * (rem - base));
+    if (base <= rem && rem < base + 8) lane ^= (uint64_t)0x06 << (8 * (rem - base));
+    if (i == SHA3_RATE / 8 - 1) lane ^= 0x8000000000000000ull;
+    s[i] ^= lane;
   }
-  lanes[SHA3_RATE / 8 - 1] ^= 0x8000000000000000ull;
-#pragma unroll
-  for (int i = 0; i < SHA3_RATE / 8; i++) s[i] ^= lanes[i];
   keccak_f1600(s);
 }
 

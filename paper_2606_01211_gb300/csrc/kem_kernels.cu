@@ -27,7 +27,7 @@ __device__ uint32_t g_aes_T0[256];
 // ---------------------------------------------------------------------------
 // A expansion: thread per 16-byte block, grid-stride; one key per grid.y.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_expand_A(const uint8_t *__restrict__ seeds,
+__global__ void __launch_bounds__(512, 1) k_expand_A(const uint8_t *__restrict__ seeds,
                                                   uint32_t seed_stride, uint32_t n,
                                                   uint32_t logq, uint16_t *__restrict__ A,
                                                   uint64_t a_stride) {
@@ -55,65 +55,120 @@ __global__ void __launch_bounds__(256) k_expand_A(const uint8_t *__restrict__ se
 }
 
 // ---------------------------------------------------------------------------
-// Noise: CTA per item (grid-stride), every thread expands the item's key.
+// Noise: a warp generates one run of NOISE_RUN counter blocks of one stream
+// of one item (4 blocks per lane, two at a time, contiguous stores).
+// Sampling (Tab. 1, rounded Gaussian by CDF inversion): a 16-bit word w gives
+// t = w >> 1, |e| = #{i : t > T[i]}, e < 0 iff w & 1.  Every CTA first
+// tabulates e for all 65536 words in shared memory (64 KB of int8), so a
+// sample costs one byte load; the table is built from T with the same
+// comparison rule.
 // ---------------------------------------------------------------------------
-LWE_DEV int cdf_sample(uint32_t w, const NoiseArgs &a) {
-  const uint32_t t = w >> 1;
+#define NOISE_TAB_OFF AES_SMEM_BYTES
+#define NOISE_SMEM_BYTES (AES_SMEM_BYTES + 65536)
+
+LWE_DEV int cdf_mag(uint32_t t, const NoiseArgs &a) {
   int mag = 0;
 #pragma unroll
-  for (int i = 0; i < 15; i++) mag += (t > (uint32_t)a.T[i]) ? 1 : 0;
-  return (w & 1u) ? -mag : mag;
+  for (int i = 0; i < 15; i++) mag += (t > a.T[i]) ? 1 : 0;
+  return mag;
 }
 
-__global__ void __launch_bounds__(256) k_noise(NoiseArgs a) {
+LWE_DEV void noise_fill_table(uint32_t *tab, const NoiseArgs &a) {
+  // word j holds the samples of w = 4j .. 4j+3 (t = 2j, 2j, 2j+1, 2j+1)
+  for (uint32_t j = threadIdx.x; j < 16384; j += blockDim.x) {
+    const int m0 = cdf_mag(2 * j, a), m1 = cdf_mag(2 * j + 1, a);
+    tab[j] = (uint32_t)(m0 & 0xff) | ((uint32_t)(-m0 & 0xff) << 8) | ((uint32_t)(m1 & 0xff) << 16) |
+             ((uint32_t)(-m1 & 0xff) << 24);
+  }
+}
+
+LWE_DEV int tab_sample(const char *smem, uint32_t w16) {
+  return *reinterpret_cast<const int8_t *>(smem + NOISE_TAB_OFF + w16);
+}
+
+LWE_DEV void noise_store(const char *smem, const NoiseOut &o, uint8_t *base, uint32_t b, uint4 v) {
+  const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+  int smp[8];
+#pragma unroll
+  for (int t = 0; t < 4; t++) {
+    smp[2 * t] = tab_sample(smem, w[t] & 0xffffu);
+    smp[2 * t + 1] = tab_sample(smem, w[t] >> 16);
+  }
+  const bool full = (8 * b + 8 <= o.nsamples);
+  if (o.fmt == NOISE_I8) {
+    if (full) {
+      const uint32_t lo = __byte_perm(__byte_perm(smp[0], smp[1], 0x0040),
+                                      __byte_perm(smp[2], smp[3], 0x0040), 0x5410);
+      const uint32_t hi = __byte_perm(__byte_perm(smp[4], smp[5], 0x0040),
+                                      __byte_perm(smp[6], smp[7], 0x0040), 0x5410);
+      *reinterpret_cast<uint2 *>(base + 8 * (size_t)b) = make_uint2(lo, hi);
+    } else {
+      for (int t = 0; t < 8; t++)
+        if (8 * b + t < o.nsamples) base[8 * (size_t)b + t] = (uint8_t)(int8_t)smp[t];
+    }
+  } else {  // bf16: small integers are exact
+    __nv_bfloat16 *bp = reinterpret_cast<__nv_bfloat16 *>(base);
+    if (full) {
+      uint32_t pk[4];
+#pragma unroll
+      for (int t = 0; t < 4; t++) {
+        __nv_bfloat162 h2 = __floats2bfloat162_rn((float)smp[2 * t], (float)smp[2 * t + 1]);
+        pk[t] = *reinterpret_cast<uint32_t *>(&h2);
+      }
+      *reinterpret_cast<uint4 *>(bp + 8 * (size_t)b) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+    } else {
+      for (int t = 0; t < 8; t++)
+        if (8 * b + t < o.nsamples) bp[8 * (size_t)b + t] = __float2bfloat16_rn((float)smp[t]);
+    }
+  }
+}
+
+__global__ void __launch_bounds__(512, 1) k_noise(NoiseArgs a) {
   extern __shared__ uint32_t sT[];
   aes_fill_smem(sT, g_aes_T0);
+  noise_fill_table(sT + NOISE_TAB_OFF / 4, a);
   __syncthreads();
   const AesTab tab = aes_tab(sT);
-  for (uint32_t e = blockIdx.x; e < a.count; e += gridDim.x) {
-    uint32_t key[4], rk[44];
-    aes_load_key(a.keys + (size_t)e * a.key_stride, key);
-    aes_key_expand(tab, key, rk);
-    for (uint32_t s = 0; s < a.nout; s++) {
-      const NoiseOut o = a.out[s];
-      const uint32_t nblk = (o.nsamples + 7) / 8;
-      for (uint32_t b = threadIdx.x; b < nblk; b += blockDim.x) {
-        uint4 v = aes_ctr_block(tab, rk, o.domain, b);
-        uint32_t w[4] = {v.x, v.y, v.z, v.w};
-        int smp[8];
+  const char *smem = reinterpret_cast<const char *>(sT);
+  const uint32_t lane = threadIdx.x & 31;
+  const uint64_t nruns = (uint64_t)a.count * a.runs_per_item;
+  const uint64_t nwarps = (uint64_t)gridDim.x * (blockDim.x >> 5);
+  for (uint64_t run = (uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); run < nruns;
+       run += nwarps) {
+    const uint32_t e = (uint32_t)(run / a.runs_per_item);
+    uint32_t r = (uint32_t)(run % a.runs_per_item);
+    uint32_t s = 0;
+    while (s + 1 < a.nout && r >= a.out[s].runs) {
+      r -= a.out[s].runs;
+      s++;
+    }
+    const NoiseOut o = a.out[s];
+    uint32_t rk[44];
+    const uint4 *rkp = reinterpret_cast<const uint4 *>(a.rk + 44 * (size_t)e);
 #pragma unroll
-        for (int t = 0; t < 8; t++) smp[t] = cdf_sample((w[t >> 1] >> (16 * (t & 1))) & 0xffffu, a);
-        uint8_t *base = reinterpret_cast<uint8_t *>(o.base) + (size_t)e * o.item_stride;
-        const bool full = (8 * b + 8 <= o.nsamples);
-        if (o.fmt == NOISE_I8) {
-          if (full) {
-            uint32_t lo = 0, hi = 0;
+    for (int i = 0; i < 11; i++) {
+      const uint4 v = __ldg(rkp + i);
+      rk[4 * i] = v.x;
+      rk[4 * i + 1] = v.y;
+      rk[4 * i + 2] = v.z;
+      rk[4 * i + 3] = v.w;
+    }
+    const uint32_t nblk = (o.nsamples + 7) / 8;
+    uint8_t *base = reinterpret_cast<uint8_t *>(o.base) + (size_t)e * o.item_stride;
+    const uint32_t b0 = r * NOISE_RUN + lane;
+    if (r * NOISE_RUN + NOISE_RUN <= nblk) {
+      // full run: two independent blocks in flight per lane
 #pragma unroll
-            for (int t = 0; t < 4; t++) {
-              lo |= ((uint32_t)(uint8_t)(int8_t)smp[t]) << (8 * t);
-              hi |= ((uint32_t)(uint8_t)(int8_t)smp[t + 4]) << (8 * t);
-            }
-            *reinterpret_cast<uint2 *>(base + 8 * (size_t)b) = make_uint2(lo, hi);
-          } else {
-            for (int t = 0; t < 8; t++)
-              if (8 * b + t < o.nsamples) base[8 * (size_t)b + t] = (uint8_t)(int8_t)smp[t];
-          }
-        } else {  // bf16: small integers are exact
-          __nv_bfloat16 *bp = reinterpret_cast<__nv_bfloat16 *>(base);
-          if (full) {
-            uint32_t pk[4];
-#pragma unroll
-            for (int t = 0; t < 4; t++) {
-              __nv_bfloat162 h2 = __floats2bfloat162_rn((float)smp[2 * t], (float)smp[2 * t + 1]);
-              pk[t] = *reinterpret_cast<uint32_t *>(&h2);
-            }
-            *reinterpret_cast<uint4 *>(bp + 8 * (size_t)b) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
-          } else {
-            for (int t = 0; t < 8; t++)
-              if (8 * b + t < o.nsamples) bp[8 * (size_t)b + t] = __float2bfloat16_rn((float)smp[t]);
-          }
-        }
+      for (uint32_t j = 0; j < NOISE_RUN / 32; j += 2) {
+        const uint32_t ba = b0 + 32 * j, bb = ba + 32;
+        const uint4 va = aes_ctr_block(tab, rk, o.domain, ba);
+        const uint4 vb = aes_ctr_block(tab, rk, o.domain, bb);
+        noise_store(smem, o, base, ba, va);
+        noise_store(smem, o, base, bb, vb);
       }
+    } else {
+#pragma unroll 1
+      for (uint32_t b = b0; b < nblk; b += 32) noise_store(smem, o, base, b, aes_ctr_block(tab, rk, o.domain, b));
     }
   }
 }
@@ -473,6 +528,15 @@ __global__ void k_keygen_seeds(KeygenSeedArgs a) {
   sha3_digest16(s, ws);
   sha3_prefixed32(0x53, ms, s);  // seedSE
   sha3_digest16(s, ws + 16);
+  {
+    const uint32_t key[4] = {(uint32_t)s[0], (uint32_t)(s[0] >> 32), (uint32_t)s[1],
+                             (uint32_t)(s[1] >> 32)};
+    uint32_t rk[44];
+    aes_key_expand_global(g_aes_T0, key, rk);
+    uint4 *dst = reinterpret_cast<uint4 *>(a.ws_rk + 44 * (size_t)e);
+#pragma unroll
+    for (int i = 0; i < 11; i++) dst[i] = make_uint4(rk[4 * i], rk[4 * i + 1], rk[4 * i + 2], rk[4 * i + 3]);
+  }
   sha3_prefixed32(0x5A, ms, s);  // z
   sha3_digest(s, sk + a.sk_z_off);
 }
@@ -505,6 +569,13 @@ __global__ void k_derive(DeriveArgs a) {
   lanes_put(lanes, 33, m, mub);
   sha3_256_lanes(lanes, 33 + mub, s);
   sha3_digest16(s, a.seeds + 32 * (size_t)e);
+  const uint32_t key[4] = {(uint32_t)s[0], (uint32_t)(s[0] >> 32), (uint32_t)s[1],
+                           (uint32_t)(s[1] >> 32)};
+  uint32_t rk[44];
+  aes_key_expand_global(g_aes_T0, key, rk);
+  uint4 *dst = reinterpret_cast<uint4 *>(a.rk + 44 * (size_t)e);
+#pragma unroll
+  for (int i = 0; i < 11; i++) dst[i] = make_uint4(rk[4 * i], rk[4 * i + 1], rk[4 * i + 2], rk[4 * i + 3]);
 }
 
 __global__ void __launch_bounds__(128) k_tree_leaves(TreeLeafArgs a) {
@@ -649,7 +720,7 @@ cudaError_t lwe_kernel_smem_setup() {
   cudaError_t e;
   e = cudaFuncSetAttribute(k_expand_A, cudaFuncAttributeMaxDynamicSharedMemorySize, AES_SMEM_BYTES);
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_noise, cudaFuncAttributeMaxDynamicSharedMemorySize, AES_SMEM_BYTES);
+  e = cudaFuncSetAttribute(k_noise, cudaFuncAttributeMaxDynamicSharedMemorySize, NOISE_SMEM_BYTES);
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_mul_as<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, AES_SMEM_BYTES);
   if (e != cudaSuccess) return e;
@@ -665,13 +736,13 @@ cudaError_t lwe_kernel_smem_setup() {
 void launch_expand_A(const uint8_t *seeds, uint32_t seed_stride, uint32_t count, uint32_t n,
                      uint32_t logq, uint16_t *A, uint64_t a_stride, int num_sms, cudaStream_t st) {
   const uint64_t nblk = (uint64_t)n * n / 8;
-  const int gx = grid_for(nblk, 256 * 4, num_sms * 8);
-  k_expand_A<<<dim3(gx, count), 256, AES_SMEM_BYTES, st>>>(seeds, seed_stride, n, logq, A, a_stride);
+  const int gx = grid_for(nblk, 512 * 4, num_sms);
+  k_expand_A<<<dim3(gx, count), 512, AES_SMEM_BYTES, st>>>(seeds, seed_stride, n, logq, A, a_stride);
 }
 
 void launch_noise(const NoiseArgs &a, int num_sms, cudaStream_t st) {
-  const int g = grid_for(a.count, 1, num_sms * 8);
-  k_noise<<<g, 256, AES_SMEM_BYTES, st>>>(a);
+  const int g = grid_for((uint64_t)a.count * a.runs_per_item, 16, num_sms);
+  k_noise<<<g, 512, NOISE_SMEM_BYTES, st>>>(a);
 }
 
 void launch_mul_as(const MulAsArgs &a, uint32_t count, bool fused, cudaStream_t st) {

@@ -10,23 +10,28 @@
 
 enum { NOISE_I8 = 0, NOISE_BF16 = 1 };
 
+// Noise streams are cut into runs of NOISE_RUN consecutive counter blocks;
+// one warp generates one run (4 blocks per lane), so one item's round keys
+// serve a whole warp and the stores of a warp are contiguous.
+#define NOISE_RUN 128
+
 struct NoiseOut {
   void *base;            // item e writes at base + e * item_stride (bytes)
   uint64_t item_stride;  // bytes
   uint32_t nsamples;     // samples per item, sample k from word k%8 of block k/8
   uint32_t domain;       // counter-block domain
   uint32_t fmt;          // NOISE_I8 or NOISE_BF16
-  uint32_t pad;
+  uint32_t runs;         // ceil(ceil(nsamples / 8) / NOISE_RUN)
 };
 
 struct NoiseArgs {
-  const uint8_t *keys;  // item e key at keys + e * key_stride (16 bytes)
-  uint32_t key_stride;
+  const uint32_t *rk;    // item e: 44 expanded AES round-key words at rk + 44 e
   uint32_t count;
   uint32_t nout;
-  uint32_t pad;
+  uint32_t runs_per_item;
+  uint32_t pad0, pad1, pad2;
   NoiseOut out[3];
-  uint16_t T[16];  // CDF table, entries >= clip set to 0x7FFF
+  uint32_t T[16];        // CDF table, entries >= clip set to 0x7FFF
 };
 
 struct MulAsArgs {
@@ -87,6 +92,7 @@ struct KeygenSeedArgs {
   uint8_t *pk;
   uint8_t *sk;
   uint8_t *ws_seeds;     // count x 32: seedA || seedSE
+  uint32_t *ws_rk;       // count x 44: round keys of seedSE
   uint64_t pk_bytes, sk_bytes;
   uint64_t sk_z_off, sk_pk_off;
   uint32_t count, pad;
@@ -98,6 +104,7 @@ struct DeriveArgs {
   uint8_t *mu;           // 32-byte slot per item
   uint8_t *kprime;       // 32 per item
   uint8_t *seeds;        // 32-byte slot per item, seedSE' in the first 16
+  uint32_t *rk;          // 44 round-key words of seedSE' per item
   uint32_t count, mu_bytes;
 };
 

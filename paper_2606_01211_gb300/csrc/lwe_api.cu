@@ -163,11 +163,15 @@ struct lwe_ctx {
   size_t ws_bytes = 0;
   uint8_t *seeds = nullptr, *mu = nullptr, *kp = nullptr, *pkh = nullptr, *leaves = nullptr;
   uint32_t *flags = nullptr, *dev_err = nullptr;
+  uint32_t *rk = nullptr;     // 44 AES round-key words per item
   int8_t *sp8 = nullptr, *ep8 = nullptr, *epp = nullptr;
   uint16_t *spbf = nullptr;  // bf16 bits
   uint16_t *limbs = nullptr; // bf16 bits, [2][n + 8][n]
   bool has_tensor = false;
   uint32_t tree_m = 0;  // leaves per item
+  // side stream for work independent of the re-encryption (Decaps' H(c))
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 };
 
 namespace {
@@ -233,14 +237,24 @@ void harvest(lwe_ctx *c) {
 
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
-NoiseArgs noise_args(const lwe_ctx *c, const uint8_t *keys, uint32_t count) {
+NoiseArgs noise_args(const lwe_ctx *c, uint32_t count) {
   NoiseArgs a;
   memset(&a, 0, sizeof a);
-  a.keys = keys;
-  a.key_stride = 32;
+  a.rk = c->rk;
   a.count = count;
   for (int i = 0; i < 16; i++) a.T[i] = c->T[i];
   return a;
+}
+
+NoiseOut noise_out(void *base, uint64_t item_stride, uint32_t nsamples, uint32_t domain,
+                   uint32_t fmt) {
+  const uint32_t nblk = (nsamples + 7) / 8;
+  return NoiseOut{base, item_stride, nsamples, domain, fmt, (nblk + NOISE_RUN - 1) / NOISE_RUN};
+}
+
+void noise_finish(NoiseArgs &a) {
+  a.runs_per_item = 0;
+  for (uint32_t s = 0; s < a.nout; s++) a.runs_per_item += a.out[s].runs;
 }
 
 // Encrypt (Alg. 2) for `count` items whose seedSE' and mu are in the
@@ -255,14 +269,15 @@ int run_encrypt(lwe_ctx *c, const uint8_t *pk, const uint16_t *A, uint32_t count
     tensor = (int)count >= c->tensor_min;
   tensor = tensor && c->has_tensor;
 
-  NoiseArgs na = noise_args(c, c->seeds, count);
+  NoiseArgs na = noise_args(c, count);
   na.nout = 3;
   if (tensor)
-    na.out[0] = {c->spbf, 16ull * n, 8 * n, 3, NOISE_BF16, 0};
+    na.out[0] = noise_out(c->spbf, 16ull * n, 8 * n, 3, NOISE_BF16);
   else
-    na.out[0] = {c->sp8, 8ull * n, 8 * n, 3, NOISE_I8, 0};
-  na.out[1] = {c->ep8, 8ull * n, 8 * n, 4, NOISE_I8, 0};
-  na.out[2] = {c->epp, 64, 64, 5, NOISE_I8, 0};
+    na.out[0] = noise_out(c->sp8, 8ull * n, 8 * n, 3, NOISE_I8);
+  na.out[1] = noise_out(c->ep8, 8ull * n, 8 * n, 4, NOISE_I8);
+  na.out[2] = noise_out(c->epp, 64, 64, 5, NOISE_I8);
+  noise_finish(na);
   LAUNCH(c, KID_NOISE, st, launch_noise(na, c->num_sms, st));
 
   if (tensor) {
@@ -331,11 +346,15 @@ int run_encrypt(lwe_ctx *c, const uint8_t *pk, const uint16_t *A, uint32_t count
   return check_launch();
 }
 
-int hash_tree(lwe_ctx *c, const uint8_t *msgs, uint64_t stride, uint32_t len, uint32_t count,
-              int mode, uint8_t *out, uint64_t out_stride, uint8_t *out2, uint64_t out2_stride,
-              const uint8_t *z, cudaStream_t st) {
+void tree_leaves(lwe_ctx *c, const uint8_t *msgs, uint64_t stride, uint32_t len, uint32_t count,
+                 cudaStream_t st) {
   TreeLeafArgs la{msgs, stride, len, count, c->leaves};
   LAUNCH(c, KID_TREE_LEAVES, st, launch_tree_leaves(la, st));
+}
+
+void tree_root(lwe_ctx *c, uint32_t len, uint32_t count, int mode, uint8_t *out,
+               uint64_t out_stride, uint8_t *out2, uint64_t out2_stride, const uint8_t *z,
+               cudaStream_t st) {
   TreeRootArgs ra;
   memset(&ra, 0, sizeof ra);
   ra.leaves = c->leaves;
@@ -350,6 +369,13 @@ int hash_tree(lwe_ctx *c, const uint8_t *msgs, uint64_t stride, uint32_t len, ui
   ra.z = z;
   ra.flags = c->flags;
   LAUNCH(c, KID_TREE_ROOT, st, launch_tree_root(ra, st));
+}
+
+int hash_tree(lwe_ctx *c, const uint8_t *msgs, uint64_t stride, uint32_t len, uint32_t count,
+              int mode, uint8_t *out, uint64_t out_stride, uint8_t *out2, uint64_t out2_stride,
+              const uint8_t *z, cudaStream_t st) {
+  tree_leaves(c, msgs, stride, len, count, st);
+  tree_root(c, len, count, mode, out, out_stride, out2, out2_stride, z, st);
   return check_launch();
 }
 
@@ -451,6 +477,7 @@ int lwe_ctx_create(const lwe_params *p, uint32_t max_batch, int device, lwe_ctx 
   };
   const size_t o_seeds = carve(32 * Bm), o_mu = carve(32 * Bm), o_kp = carve(32 * Bm);
   const size_t o_flags = carve(4 * Bm), o_err = carve(16), o_pkh = carve(32);
+  const size_t o_rk = carve(176 * Bm);
   const size_t o_leaves = carve(32 * (size_t)c->tree_m * Bm);
   const size_t o_sp8 = carve(8 * n * Bm), o_ep8 = carve(8 * n * Bm), o_epp = carve(64 * Bm);
   size_t o_spbf = 0, o_limbs = 0;
@@ -471,6 +498,7 @@ int lwe_ctx_create(const lwe_params *p, uint32_t max_batch, int device, lwe_ctx 
   c->kp = c->ws + o_kp;
   c->flags = reinterpret_cast<uint32_t *>(c->ws + o_flags);
   c->dev_err = reinterpret_cast<uint32_t *>(c->ws + o_err);
+  c->rk = reinterpret_cast<uint32_t *>(c->ws + o_rk);
   c->pkh = c->ws + o_pkh;
   c->leaves = c->ws + o_leaves;
   c->sp8 = reinterpret_cast<int8_t *>(c->ws + o_sp8);
@@ -480,10 +508,16 @@ int lwe_ctx_create(const lwe_params *p, uint32_t max_batch, int device, lwe_ctx 
     c->spbf = reinterpret_cast<uint16_t *>(c->ws + o_spbf);
     c->limbs = reinterpret_cast<uint16_t *>(c->ws + o_limbs);
   }
-  e = cudaMemset(c->ws, 0, c->ws_bytes);
+  e = cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaMemset(c->ws, 0, c->ws_bytes);
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
   cudaSetDevice(prev);
   if (e != cudaSuccess) {
+    if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+    if (c->ev_join) cudaEventDestroy(c->ev_join);
+    if (c->side) cudaStreamDestroy(c->side);
     cudaFree(c->ws);
     delete c;
     return cuda_fail(e);
@@ -503,6 +537,9 @@ int lwe_ctx_destroy(lwe_ctx *c) {
     cudaEventDestroy(t.b);
   }
   for (auto e : c->free_events) cudaEventDestroy(e);
+  if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+  if (c->ev_join) cudaEventDestroy(c->ev_join);
+  if (c->side) cudaStreamDestroy(c->side);
   cudaFree(c->ws);
   cudaSetDevice(prev);
   delete c;
@@ -548,13 +585,14 @@ int lwe_keygen(lwe_ctx *c, const uint8_t *seeds, uint32_t count, uint8_t *pk, ui
   const uint32_t n = p.n;
   const size_t pkb = pk_bytes(p), skb = sk_bytes(p);
 
-  KeygenSeedArgs ka{seeds, pk, sk, c->seeds, pkb, skb, 8ull * n, 8ull * n + 64, count, 0};
+  KeygenSeedArgs ka{seeds, pk, sk, c->seeds, c->rk, pkb, skb, 8ull * n, 8ull * n + 64, count, 0};
   LAUNCH(c, KID_KEYGEN_SEEDS, st, launch_keygen_seeds(ka, st));
 
-  NoiseArgs na = noise_args(c, c->seeds + 16, count);
+  NoiseArgs na = noise_args(c, count);
   na.nout = 2;
-  na.out[0] = {sk, skb, 8 * n, 1, NOISE_I8, 0};           // S^T, row-major 8 x n
-  na.out[1] = {c->ep8, 8ull * n, 8 * n, 2, NOISE_I8, 0};  // E, n x 8
+  na.out[0] = noise_out(sk, skb, 8 * n, 1, NOISE_I8);           // S^T, row-major 8 x n
+  na.out[1] = noise_out(c->ep8, 8ull * n, 8 * n, 2, NOISE_I8);  // E, n x 8
+  noise_finish(na);
   LAUNCH(c, KID_NOISE, st, launch_noise(na, c->num_sms, st));
 
   if (A_out)
@@ -600,7 +638,7 @@ int lwe_encaps(lwe_ctx *c, const uint8_t *pk, const uint16_t *A, const uint8_t *
 
   rc = hash_tree(c, pk, pkb, (uint32_t)pkb, 1, TREE_DIGEST, c->pkh, 32, nullptr, 0, nullptr, st);
   if (rc) return rc;
-  DeriveArgs da{coins, c->pkh, c->mu, c->kp, c->seeds, count, mu_bytes(p)};
+  DeriveArgs da{coins, c->pkh, c->mu, c->kp, c->seeds, c->rk, count, mu_bytes(p)};
   LAUNCH(c, KID_DERIVE, st, launch_derive(da, st));
   rc = run_encrypt(c, pk, A, count, ct, false, st);
   if (rc) return rc;
@@ -626,13 +664,21 @@ int lwe_decaps(lwe_ctx *c, const uint8_t *sk, const uint16_t *A, const uint8_t *
   const uint8_t *pk = pkh + 32;
 
   CUDA_TRY(cudaMemsetAsync(c->flags, 0, 4 * (size_t)count, st));
+  // H(c) does not depend on the re-encryption: its leaves run on the side
+  // stream, overlapping the tensor-bound product, and join before the keys
+  CUDA_TRY(cudaEventRecord(c->ev_fork, st));
+  CUDA_TRY(cudaStreamWaitEvent(c->side, c->ev_fork, 0));
+  tree_leaves(c, ct, ctb, (uint32_t)ctb, count, c->side);
+  CUDA_TRY(cudaEventRecord(c->ev_join, c->side));
   DecryptArgs dca{ct, ctb, reinterpret_cast<const int8_t *>(sk), c->mu, n, p.logq, p.B, 0};
   LAUNCH(c, KID_DECRYPT, st, launch_decrypt(dca, count, st));
-  DeriveArgs da{nullptr, pkh, c->mu, c->kp, c->seeds, count, mu_bytes(p)};
+  DeriveArgs da{nullptr, pkh, c->mu, c->kp, c->seeds, c->rk, count, mu_bytes(p)};
   LAUNCH(c, KID_DERIVE, st, launch_derive(da, st));
   rc = run_encrypt(c, pk, A, count, const_cast<uint8_t *>(ct), true, st);
   if (rc) return rc;
-  return hash_tree(c, ct, ctb, (uint32_t)ctb, count, TREE_DEC_KEY, K, 32, nullptr, 0, z, st);
+  CUDA_TRY(cudaStreamWaitEvent(st, c->ev_join, 0));
+  tree_root(c, (uint32_t)ctb, count, TREE_DEC_KEY, K, 32, nullptr, 0, z, st);
+  return check_launch();
 }
 
 int lwe_expand_A(const uint8_t *seedA, uint32_t n, uint32_t logq, uint16_t *A_out,
@@ -744,7 +790,7 @@ int lwe_encaps_noalloc(const lwe_params *p, const uint8_t *pk, const uint16_t *A
     return o;
   };
   const size_t o_seeds = carve(32 * Bm), o_mu = carve(32 * Bm), o_kp = carve(32 * Bm);
-  const size_t o_flags = carve(4 * Bm), o_pkh = carve(32);
+  const size_t o_flags = carve(4 * Bm), o_pkh = carve(32), o_rk = carve(176 * Bm);
   const size_t o_leaves = carve(32 * (size_t)tree_m * Bm);
   const size_t o_sp8 = carve(8 * n * Bm), o_ep8 = carve(8 * n * Bm), o_epp = carve(64 * Bm);
   if (off > LWE_NOALLOC_SCRATCH_BYTES) return LWE_ECAPACITY;
@@ -770,6 +816,7 @@ int lwe_encaps_noalloc(const lwe_params *p, const uint8_t *pk, const uint16_t *A
   c.mu = ws + o_mu;
   c.kp = ws + o_kp;
   c.flags = reinterpret_cast<uint32_t *>(ws + o_flags);
+  c.rk = reinterpret_cast<uint32_t *>(ws + o_rk);
   c.pkh = ws + o_pkh;
   c.leaves = ws + o_leaves;
   c.sp8 = reinterpret_cast<int8_t *>(ws + o_sp8);
@@ -780,7 +827,7 @@ int lwe_encaps_noalloc(const lwe_params *p, const uint8_t *pk, const uint16_t *A
   const size_t pkb = pk_bytes(*p), ctb = ct_bytes(*p);
   rc = hash_tree(&c, pk, pkb, (uint32_t)pkb, 1, TREE_DIGEST, c.pkh, 32, nullptr, 0, nullptr, st);
   if (rc) return rc;
-  DeriveArgs da{coins, c.pkh, c.mu, c.kp, c.seeds, count, mu_bytes(*p)};
+  DeriveArgs da{coins, c.pkh, c.mu, c.kp, c.seeds, c.rk, count, mu_bytes(*p)};
   LAUNCH(&c, KID_DERIVE, st, launch_derive(da, st));
   rc = run_encrypt(&c, pk, A, count, ct, false, st);
   if (rc) return rc;
