@@ -171,11 +171,12 @@ def keccak_perms(length: int, chunk: int = 1024) -> int:
 # Derived peaks of the integer-bound kernels at the 2070 MHz maximum SM clock:
 #  AES round tables: 160 conflict-free shared-memory lookups per 16-byte block,
 #    32 per clock per SM  ->  152 * 2.07e9 * 32 / 160 * 16 B = 1006 GB/s
-#  Keccak-f[1600]: 132 integer-ALU operations per round (XOR / chi LOP3s; the
-#    rotations run as multiply-adds), 64 ALU lanes per clock per SM
-#    ->  152 * 2.07e9 * 64 / (132 * 24) = 6.35 G permutations/s
+#  Keccak-f[1600] on 32-bit lanes: 190 integer-ALU operations per round
+#    (three-input XORs / chi as LOP3, 64-bit rotations as funnel-shift pairs),
+#    64 ALU lanes per clock per SM  ->  152 * 2.07e9 * 64 / (190 * 24)
+#    = 4.42 G permutations/s
 AES_PEAK_GBS = 152 * 2.070e9 * 32 / 160 * 16 / 1e9
-KECCAK_PEAK_GPERMS = 152 * 2.070e9 * 64 / (132 * 24) / 1e9
+KECCAK_PEAK_GPERMS = 152 * 2.070e9 * 64 / (190 * 24) / 1e9
 
 
 def algorithmic(p, count):

@@ -124,13 +124,18 @@ enum {
   LWE_PATH_AUTO = 0,   /* tensor path when count >= the tuned threshold  */
   LWE_PATH_SKINNY = 1, /* per-item CUDA-core kernels ("plain" path)      */
   LWE_PATH_TENSOR = 2  /* stacked S' as one exact two-limb bf16 tcgen05
-                          GEMM (tensor cores, fp32 accumulation)          */
+                          GEMM (tensor cores, fp32 accumulation; K split
+                          into passes of at most (2^24-1)/(128 c) columns).
+                          Available for n <= 8192, or for larger n when the
+                          context was created with max_batch >= 64.       */
 };
 enum {
   LWE_OPT_PATH = 0,          /* one of LWE_PATH_*                             */
   LWE_OPT_TENSOR_MIN = 1,    /* AUTO threshold (items per call), default 64   */
   LWE_OPT_TIMING = 2,        /* 1: time every launch with CUDA events          */
-  LWE_OPT_GEMM_BN = 3        /* GEMM output-column tile: 64 or 128 (default)  */
+  LWE_OPT_GEMM_BN = 3,       /* GEMM output-column tile: 64 or 128 (default)  */
+  LWE_OPT_GEMM_KCHUNK = 4    /* K per tensor-core pass: a multiple of 64 up to
+                                the exact bound (2^24-1)/(128 c); 0 = bound   */
 };
 int lwe_ctx_set_option(lwe_ctx *ctx, int option, int64_t value);
 
@@ -188,7 +193,9 @@ int lwe_expand_A(const uint8_t *seedA, uint32_t n, uint32_t logq,
  * A [n][n] uint16, or NULL to regenerate it from seedA [16] (device) tile
  * by tile inside the product, never storing it.  ctx: nullable; when given
  * (and its n equals n and its max_batch covers k/8), SA may take the
- * tensor-core path and its workspace; otherwise the CUDA-core kernels run. */
+ * tensor-core path and its workspace -- then every |S| must be at most the
+ * context's clip, which bounds the exact K per tensor-core pass; otherwise
+ * the CUDA-core kernels run. */
 enum { LWE_SIDE_AS = 0, LWE_SIDE_SA = 1 };
 int lwe_matmul_modq(lwe_ctx *ctx, int side, const uint16_t *A,
                     const uint8_t *seedA, const int8_t *S, uint32_t n,
@@ -236,6 +243,14 @@ const char *lwe_last_cuda_error(void);
 int lwe_ctx_device_error(lwe_ctx *ctx);
 /* Number of kernels this context has launched so far. */
 uint64_t lwe_ctx_launches(const lwe_ctx *ctx);
+/* Failure-detection self-test (no counterpart in the paper): launches one
+ * tiny kernel that waits, through the same bounded mbarrier wait the tensor
+ * path uses, on a barrier that nothing ever completes.  The wait gives up
+ * after limit_us microseconds (1 .. 2,000,000), raises the context's device
+ * error word and the kernel returns normally -- nothing faults or hangs, and
+ * the next lwe_ctx_device_error() returns LWE_ETIMEOUT (and clears it). */
+int lwe_selftest_bounded_wait(lwe_ctx *ctx, uint32_t limit_us, void *stream);
+
 /* Per-kernel event timing (needs LWE_OPT_TIMING = 1; synchronises). */
 int lwe_ctx_kernel_stats(lwe_ctx *ctx, int kernel_id, uint64_t *launches,
                          double *total_ms);

@@ -86,13 +86,13 @@ LWE_DEV bool mbar_try_wait(uint32_t bar, uint32_t parity) {
 
 // Bounded wait: false when another role gave up or the limit ran out.
 LWE_DEV bool wait_bar(uint32_t bar, uint32_t parity, volatile uint32_t *abort_flag,
-                      uint32_t *dev_err) {
+                      uint32_t *dev_err, uint64_t limit_ns = kTimeoutNs) {
   if (mbar_try_wait(bar, parity)) return true;
   const uint64_t t0 = gtime();
   while (true) {
     if (mbar_try_wait(bar, parity)) return true;
     if (*abort_flag) return false;
-    if (gtime() - t0 > kTimeoutNs) {
+    if (gtime() - t0 > limit_ns) {
       *abort_flag = 1;
       atomicOr(dev_err, LWE_DEVERR_TIMEOUT);
       return false;
@@ -179,7 +179,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   const uint32_t num_m = (a.rows + BM - 1) / BM;
   const uint32_t num_n = (a.ncols + BN - 1) / BN;
   const uint32_t num_tiles = num_m * num_n;
-  const uint32_t KB = (a.n + BK - 1) / BK;
+  const uint32_t KB = a.kblocks;
 
   auto bar = [&](int i) { return smem_u32(bars + i); };
   auto full = [&](uint32_t s) { return bar(s); };
@@ -232,8 +232,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           break;
         }
         mbar_arrive_expect_tx(full(stage), C::STAGE_TX);
-        tma_load_2d(sA(stage), &tmS, (int)(kb * BK), m0, full(stage));
-        tma_load_3d(sB(stage), &tmL, (int)(kb * BK), n0, 0, full(stage));
+        tma_load_2d(sA(stage), &tmS, (int)(a.k0 + kb * BK), m0, full(stage));
+        tma_load_3d(sB(stage), &tmL, (int)(a.k0 + kb * BK), n0, 0, full(stage));
         issued |= 1u << stage;
         last_phase = (last_phase & ~(1u << stage)) | (phase << stage);
         if (++stage == STAGES) {
@@ -331,7 +331,31 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           uint32_t v[16];
 #pragma unroll
           for (int t = 0; t < 16; t++) v[t] = fold(lo[t], hi[t]);
-          if (c < a.n) {  // B' columns: 16 at once (n is a multiple of 16)
+          const uint32_t nvalid = min(16u, a.ncols - c);
+          if (a.partial_in) {  // running sum of the earlier K passes
+            const uint16_t *pin = a.partial_in + (size_t)row * a.ncols + c;
+            if (nvalid == 16) {
+              const uint4 p0 = __ldg(reinterpret_cast<const uint4 *>(pin));
+              const uint4 p1 = __ldg(reinterpret_cast<const uint4 *>(pin) + 1);
+              const uint32_t pw[8] = {p0.x, p0.y, p0.z, p0.w, p1.x, p1.y, p1.z, p1.w};
+#pragma unroll
+              for (int t = 0; t < 16; t++) v[t] += (pw[t >> 1] >> (16 * (t & 1))) & 0xffffu;
+            } else {
+              for (uint32_t t = 0; t < nvalid; t++) v[t] += pin[t];
+            }
+          }
+          if (a.partial_out) {  // non-final pass: keep the running sum
+            uint16_t *pout = a.partial_out + (size_t)row * a.ncols + c;
+            if (nvalid == 16) {
+              uint32_t w[8];
+#pragma unroll
+              for (int t = 0; t < 8; t++) w[t] = (v[2 * t] & 0xffffu) | (v[2 * t + 1] << 16);
+              reinterpret_cast<uint4 *>(pout)[0] = make_uint4(w[0], w[1], w[2], w[3]);
+              reinterpret_cast<uint4 *>(pout)[1] = make_uint4(w[4], w[5], w[6], w[7]);
+            } else {
+              for (uint32_t t = 0; t < nvalid; t++) pout[t] = (uint16_t)v[t];
+            }
+          } else if (c < a.n) {  // B' columns: 16 at once (n is a multiple of 16)
             if (a.E) {
               const uint32_t ew[4] = {e_cur.x, e_cur.y, e_cur.z, e_cur.w};
 #pragma unroll
@@ -391,6 +415,22 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   }
 }
 
+// Exercises the bounded wait of the pipeline on a barrier that no thread
+// and no copy ever completes: the wait must give up after limit_ns, raise
+// the device error word and let the kernel finish.  Nothing faults.
+__global__ void k_selftest_wait(uint32_t *dev_err, uint64_t limit_ns) {
+  __shared__ uint64_t bar;
+  __shared__ uint32_t abort_flag;
+  if (threadIdx.x == 0) {
+    mbar_init(smem_u32(&bar), 1);
+    abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) wait_bar(smem_u32(&bar), 0, &abort_flag, dev_err, limit_ns);
+  __syncthreads();
+}
+
 PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
 
 bool make_map(CUtensorMap *m, const void *base, int rank, const cuuint64_t *dims,
@@ -440,14 +480,42 @@ cudaError_t lwe_gemm_setup() {
                               Cfg<64>::SMEM);
 }
 
-// The fp32 accumulator is exact while n * c * 128 < 2^24.
-bool lwe_gemm_supported(uint32_t n, uint32_t logq, uint32_t clip) {
-  (void)logq;
-  return n >= 64 && (uint64_t)n * clip * 128u < (1u << 24);
+// The fp32 accumulator is exact while every partial sum stays below 2^24:
+// K * c * 128 < 2^24 for the K contracted in one pass.
+uint32_t lwe_gemm_kchunk(uint32_t clip) {
+  const uint32_t k = ((1u << 24) - 1u) / (clip * 128u);
+  return k / BK * BK;
 }
 
+uint32_t lwe_gemm_passes(uint32_t n, uint32_t clip) {
+  const uint32_t kc = lwe_gemm_kchunk(clip);
+  return (n + kc - 1) / kc;
+}
+
+bool lwe_gemm_supported(uint32_t n, uint32_t logq, uint32_t clip) {
+  (void)logq;
+  return n >= 64 && clip >= 1 && lwe_gemm_kchunk(clip) >= BK;
+}
+
+// One launch per K pass; the running sum lives in a.partial_out between them.
 int launch_gemm_sa(const GemmSaArgs &a, int num_sms, cudaStream_t st) {
   if (!g_encode) return LWE_ECUDA;
   if (a.rows == 0) return LWE_OK;
-  return a.bn == 64 ? launch_bn<64>(a, num_sms, st) : launch_bn<128>(a, num_sms, st);
+  const uint32_t kc = a.kchunk ? a.kchunk : a.n;
+  const uint32_t passes = (a.n + kc - 1) / kc;
+  if (passes > 1 && !a.partial_out) return LWE_EINVAL;
+  for (uint32_t p = 0; p < passes; p++) {
+    GemmSaArgs b = a;
+    b.k0 = p * kc;
+    b.kblocks = (min(a.n, b.k0 + kc) - b.k0 + BK - 1) / BK;
+    b.partial_in = p > 0 ? a.partial_out : nullptr;
+    b.partial_out = p + 1 < passes ? a.partial_out : nullptr;
+    const int rc = a.bn == 64 ? launch_bn<64>(b, num_sms, st) : launch_bn<128>(b, num_sms, st);
+    if (rc != LWE_OK) return rc;
+  }
+  return LWE_OK;
+}
+
+void launch_selftest_wait(uint32_t *dev_err, uint64_t limit_ns, cudaStream_t st) {
+  k_selftest_wait<<<1, 32, 0, st>>>(dev_err, limit_ns);
 }

@@ -32,11 +32,25 @@ struct GemmSaArgs {
   uint32_t logq, B;
   int cmp;                // 0: write out; 1: compare with out
   int bn;                 // output columns per tile: 64 or 128
+  // K-split: this launch contracts K = [k0, k0 + 64 * kblocks) only.  The
+  // partial sum of earlier passes (mod 2^16, [rows][ncols]) is added from
+  // partial_in when set; a non-final pass writes its running sum to
+  // partial_out instead of the output (the noise and message are added by
+  // the final pass only).
+  uint32_t k0, kblocks;
+  const uint16_t *partial_in;
+  uint16_t *partial_out;
+  uint32_t kchunk;        // host: maximum exact K per pass (multiple of 64)
 };
 
 cudaError_t lwe_gemm_setup();
 bool lwe_gemm_supported(uint32_t n, uint32_t logq, uint32_t clip);
+// largest K (multiple of 64) whose partial sums stay below 2^24 for this clip
+uint32_t lwe_gemm_kchunk(uint32_t clip);
+// number of K passes for (n, clip)
+uint32_t lwe_gemm_passes(uint32_t n, uint32_t clip);
 int launch_gemm_sa(const GemmSaArgs &a, int num_sms, cudaStream_t st);
 void launch_gemm_limbs(const GemmLimbArgs &a, int num_sms, cudaStream_t st);
 void launch_s_to_bf16(const int8_t *S, uint64_t count, uint16_t *out, int num_sms,
                       cudaStream_t st);
+void launch_selftest_wait(uint32_t *dev_err, uint64_t limit_ns, cudaStream_t st);

@@ -167,6 +167,8 @@ struct lwe_ctx {
   int8_t *sp8 = nullptr, *ep8 = nullptr, *epp = nullptr;
   uint16_t *spbf = nullptr;  // bf16 bits
   uint16_t *limbs = nullptr; // bf16 bits, [2][n + 8][n]
+  uint16_t *partial = nullptr; // K-split running sums, [8 max_batch][n + 8]
+  uint32_t kchunk = 0;         // exact K per GEMM pass
   bool has_tensor = false;
   uint32_t tree_m = 0;  // leaves per item
   // side stream for work independent of the re-encryption (Decaps' H(c))
@@ -307,6 +309,8 @@ int run_encrypt(lwe_ctx *c, const uint8_t *pk, const uint16_t *A, uint32_t count
     ga.B = c->p.B;
     ga.cmp = cmp ? 1 : 0;
     ga.bn = c->gemm_bn;
+    ga.kchunk = c->kchunk;
+    ga.partial_out = c->partial;
     int rc = LWE_OK;
     LAUNCH(c, KID_GEMM, st, rc = launch_gemm_sa(ga, c->num_sms, st));
     if (rc != LWE_OK) return rc;
@@ -468,7 +472,11 @@ int lwe_ctx_create(const lwe_params *p, uint32_t max_batch, int device, lwe_ctx 
   const size_t n = p->n;
   const size_t Bm = max_batch;
   c->tree_m = (uint32_t)((std::max(ct_bytes(*p), pk_bytes(*p)) + LWE_TREE_CHUNK - 1) / LWE_TREE_CHUNK);
-  c->has_tensor = lwe_gemm_supported(p->n, p->logq, p->clip);
+  // tensor path workspaces (bf16 S', limbs, K-split sums) are sized for
+  // batched use: always for n <= 8192, and for larger n when max_batch >= 64
+  c->has_tensor = lwe_gemm_supported(p->n, p->logq, p->clip) && (p->n <= 8192 || max_batch >= 64);
+  c->kchunk = lwe_gemm_kchunk(p->clip);
+  const bool ksplit = c->has_tensor;  // the K-split buffer also serves LWE_OPT_GEMM_KCHUNK
   size_t off = 0;
   auto carve = [&](size_t bytes) {
     size_t o = off;
@@ -481,9 +489,11 @@ int lwe_ctx_create(const lwe_params *p, uint32_t max_batch, int device, lwe_ctx 
   const size_t o_leaves = carve(32 * (size_t)c->tree_m * Bm);
   const size_t o_sp8 = carve(8 * n * Bm), o_ep8 = carve(8 * n * Bm), o_epp = carve(64 * Bm);
   size_t o_spbf = 0, o_limbs = 0;
+  size_t o_partial = 0;
   if (c->has_tensor) {
     o_spbf = carve(16 * n * Bm);
     o_limbs = carve(2 * 2 * (n + 8) * n);
+    if (ksplit) o_partial = carve(2 * 8 * Bm * (n + 8));
   }
   c->ws_bytes = off;
   cudaError_t e = cudaMalloc(&c->ws, c->ws_bytes);
@@ -507,6 +517,7 @@ int lwe_ctx_create(const lwe_params *p, uint32_t max_batch, int device, lwe_ctx 
   if (c->has_tensor) {
     c->spbf = reinterpret_cast<uint16_t *>(c->ws + o_spbf);
     c->limbs = reinterpret_cast<uint16_t *>(c->ws + o_limbs);
+    if (ksplit) c->partial = reinterpret_cast<uint16_t *>(c->ws + o_partial);
   }
   e = cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming);
@@ -564,6 +575,15 @@ int lwe_ctx_set_option(lwe_ctx *c, int option, int64_t value) {
     case LWE_OPT_GEMM_BN:
       if (value != 64 && value != 128) return LWE_EINVAL;
       c->gemm_bn = (int)value;
+      return LWE_OK;
+    case LWE_OPT_GEMM_KCHUNK:
+      if (value == 0) {
+        c->kchunk = lwe_gemm_kchunk(c->p.clip);
+        return LWE_OK;
+      }
+      if (value < 64 || (value % 64) || value > (int64_t)lwe_gemm_kchunk(c->p.clip))
+        return LWE_EINVAL;
+      c->kchunk = (uint32_t)value;
       return LWE_OK;
     default:
       return LWE_EINVAL;
@@ -752,6 +772,8 @@ int lwe_matmul_modq(lwe_ctx *c, int side, const uint16_t *A, const uint8_t *seed
     ga.B = 0;
     ga.cmp = 0;
     ga.bn = c->gemm_bn;
+    ga.kchunk = c->kchunk;
+    ga.partial_out = c->partial;
     LAUNCH(c, KID_GEMM, st, rc = launch_gemm_sa(ga, c->num_sms, st));
     if (rc) return rc;
     return check_launch();
@@ -832,6 +854,14 @@ int lwe_encaps_noalloc(const lwe_params *p, const uint8_t *pk, const uint16_t *A
   rc = run_encrypt(&c, pk, A, count, ct, false, st);
   if (rc) return rc;
   return hash_tree(&c, ct, ctb, (uint32_t)ctb, count, TREE_ENC_KEY, K, 32, nullptr, 0, nullptr, st);
+}
+
+int lwe_selftest_bounded_wait(lwe_ctx *c, uint32_t limit_us, void *stream) {
+  if (!c || limit_us == 0 || limit_us > 2000000) return LWE_EINVAL;
+  int rc = set_device_of(c);
+  if (rc) return rc;
+  launch_selftest_wait(c->dev_err, (uint64_t)limit_us * 1000ull, (cudaStream_t)stream);
+  return check_launch();
 }
 
 const char *lwe_strerror(int code) {

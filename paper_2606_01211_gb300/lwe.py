@@ -26,7 +26,7 @@ LWE_EUNSUPPORTED = -5
 LWE_ECAPACITY = -6
 
 PATH_AUTO, PATH_SKINNY, PATH_TENSOR = 0, 1, 2
-OPT_PATH, OPT_TENSOR_MIN, OPT_TIMING, OPT_GEMM_BN = 0, 1, 2, 3
+OPT_PATH, OPT_TENSOR_MIN, OPT_TIMING, OPT_GEMM_BN, OPT_GEMM_KCHUNK = 0, 1, 2, 3, 4
 SIDE_AS, SIDE_SA = 0, 1
 PRESET_IDS = {"P640": 0, "P976": 1, "P1344": 2, "P4096": 3, "P16384": 4, "P32768": 5}
 
@@ -69,6 +69,7 @@ def _load():
         "lwe_expand_A": (i32, [vp, u32, u32, vp, vp]),
         "lwe_matmul_modq": (i32, [vp, i32, vp, vp, vp, u32, u32, u32, vp, vp, vp]),
         "lwe_encaps_noalloc": (i32, [P, vp, vp, vp, u32, vp, vp, vp]),
+        "lwe_selftest_bounded_wait": (i32, [vp, u32, vp]),
         "lwe_strerror": (C.c_char_p, [i32]),
         "lwe_last_cuda_error": (C.c_char_p, []),
         "lwe_ctx_device_error": (i32, [vp]),

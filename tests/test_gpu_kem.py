@@ -236,3 +236,24 @@ def test_results_independent_of_batch_position():
         ctx.encaps(pk, dev(cs[i:i + 1]), ct1, K1)
         assert np.array_equal(host(ct1)[0], host(ct)[i])
         assert np.array_equal(host(K1)[0], host(K)[i])
+
+
+def test_bounded_wait_times_out_cleanly():
+    """A device wait that nothing completes gives up after its limit, reports
+    LWE_ETIMEOUT on the host, and leaves the context usable (no fault)."""
+    import time
+    p, po = params("P640")
+    ctx = lwe.Ctx(p, max_batch=1)
+    assert ctx.device_error() == lwe.LWE_OK
+    t0 = time.perf_counter()
+    rc = lwe.lib().lwe_selftest_bounded_wait(ctx.handle, 50000, torch.cuda.current_stream().cuda_stream)
+    assert rc == lwe.LWE_OK
+    assert ctx.device_error() == lwe.LWE_ETIMEOUT
+    assert time.perf_counter() - t0 < 5.0
+    assert ctx.device_error() == lwe.LWE_OK  # cleared once read
+    # the context still works
+    ms = master_seeds(1, seed=8)
+    pk, sk = ctx.empty_pk(1), ctx.empty_sk(1)
+    ctx.keygen(dev(ms), pk, sk)
+    pk_o, sk_o = O.keygen(po, bytes(ms[0]))
+    assert np.array_equal(host(pk)[0], pk_o)
