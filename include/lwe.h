@@ -175,6 +175,27 @@ int lwe_encaps(lwe_ctx *ctx, const uint8_t *pk, const uint16_t *A,
 int lwe_decaps(lwe_ctx *ctx, const uint8_t *sk, const uint16_t *A,
                const uint8_t *ct, uint32_t count, uint8_t *K, void *stream);
 
+/* Encaps / Decaps of `count` items that each use their OWN key (a server
+ * batching requests across keys).  Item e uses:
+ *   pk_ptrs[e]  (Encaps)  device array of count device pointers to pk;
+ *   pkh_ptrs[e] (Encaps)  nullable device array of pointers to H(pk)
+ *               (32 bytes, e.g. inside the matching sk); NULL computes it;
+ *   sk_ptrs[e]  (Decaps)  device array of count device pointers to sk;
+ *   A_ptrs[e]   nullable device array of pointers to each item's stored A;
+ *               NULL regenerates every item's A from its seed.  A batch is
+ *               either all-stored or all-regenerated.
+ * coins / ct / K are laid out as in lwe_encaps / lwe_decaps.  Results are
+ * identical to one single-key call per item.  These calls always take the
+ * CUDA-core product (the tensor path needs one shared A).  Pointer arrays
+ * must be 8-byte aligned, key objects 16-byte aligned. */
+int lwe_encaps_multi(lwe_ctx *ctx, const uint8_t *const *pk_ptrs,
+                     const uint8_t *const *pkh_ptrs, const uint16_t *const *A_ptrs,
+                     const uint8_t *coins, uint32_t count, uint8_t *ct,
+                     uint8_t *K, void *stream);
+int lwe_decaps_multi(lwe_ctx *ctx, const uint8_t *const *sk_ptrs,
+                     const uint16_t *const *A_ptrs, const uint8_t *ct,
+                     uint32_t count, uint8_t *K, void *stream);
+
 /* ---- standalone hot-path kernels --------------------------------------- */
 
 /* sample(seedA) of Alg. 1: A[i][j..j+7] = the eight little-endian 16-bit

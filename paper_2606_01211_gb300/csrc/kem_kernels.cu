@@ -258,9 +258,10 @@ __global__ void __launch_bounds__(256) k_decrypt(DecryptArgs a) {
   const uint32_t n = a.n;
   const uint8_t *ct = a.ct + (size_t)e * a.ct_bytes;
   const uint16_t *Brow = reinterpret_cast<const uint16_t *>(ct) + (size_t)r * n;
+  const int8_t *St = a.sk_ptrs ? reinterpret_cast<const int8_t *>(a.sk_ptrs[e]) : a.St;
   int acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
   for (uint32_t jc = lane; jc < n / 8; jc += 32)
-    dot8_chunk(ld_nc_u4(Brow + 8 * (size_t)jc), a.St, n, 8 * jc, acc);
+    dot8_chunk(ld_nc_u4(Brow + 8 * (size_t)jc), St, n, 8 * jc, acc);
   warp_allreduce8(acc);
   if (lane == 0) {
     const uint32_t D = a.logq, Bb = a.B, m = (1u << D) - 1u;
@@ -290,6 +291,7 @@ __global__ void __launch_bounds__(256) k_mul_sa(MulSaArgs a) {
   const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t n = a.n;
   const int8_t *S = a.S + (size_t)e * a.s_stride;
+  const uint16_t *Aitem = a.A_ptrs ? a.A_ptrs[e] : a.A;
   const uint32_t j = j0 + 2 * lane;
   const bool jvalid = j < n;
   int acc[8][2];
@@ -306,7 +308,7 @@ __global__ void __launch_bounds__(256) k_mul_sa(MulSaArgs a) {
     const uint32_t rows = min((uint32_t)SA_CH, n - i0);
     for (uint32_t ii = warp; ii < rows; ii += 8) {
       uint32_t av = 0;
-      if (jvalid) av = __ldg(reinterpret_cast<const uint32_t *>(a.A + (size_t)(i0 + ii) * n + j));
+      if (jvalid) av = __ldg(reinterpret_cast<const uint32_t *>(Aitem + (size_t)(i0 + ii) * n + j));
       const int x0 = (int)(av & 0xffffu), x1 = (int)(av >> 16);
       const int4 s0 = sS[ii][0], s1 = sS[ii][1];
       const int s[8] = {s0.x, s0.y, s0.z, s0.w, s1.x, s1.y, s1.z, s1.w};
@@ -367,11 +369,11 @@ __global__ void __launch_bounds__(256) k_mul_sa_fused(MulSaArgs a) {
   aes_fill_smem(sT, g_aes_T0);
   __syncthreads();
   const AesTab tab = aes_tab(sT);
+  const uint32_t e = blockIdx.y, j0 = blockIdx.x * 64;
   uint32_t key[4], rk[44];
-  aes_load_key(a.seedA, key);
+  aes_load_key(a.seed_ptrs ? a.seed_ptrs[e] + a.seed_off : a.seedA, key);
   aes_key_expand(tab, key, rk);
 
-  const uint32_t e = blockIdx.y, j0 = blockIdx.x * 64;
   const uint32_t cb = threadIdx.x & 7, rs = threadIdx.x >> 3;
   const uint32_t n = a.n;
   const uint32_t mq = (1u << a.logq) - 1u, mm = mq | (mq << 16);
@@ -467,7 +469,8 @@ __global__ void __launch_bounds__(256) k_v_encode(VEncArgs a) {
   const uint32_t k = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t n = a.n;
   const int8_t *S = a.S + (size_t)e * a.s_stride + (size_t)k * n;
-  const uint16_t *Bm = reinterpret_cast<const uint16_t *>(a.pk + 16);
+  const uint8_t *pk = a.pk_ptrs ? a.pk_ptrs[e] + a.pk_off : a.pk;
+  const uint16_t *Bm = reinterpret_cast<const uint16_t *>(pk + 16);
   int acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
   for (uint32_t i = lane; i < n; i += 32) {
     const int s = S[i];
@@ -555,17 +558,18 @@ __global__ void k_derive(DeriveArgs a) {
   }
   uint8_t m[32];
   for (uint32_t t = 0; t < mub; t++) m[t] = mu[t];
+  const uint8_t *pkh = a.pkh_ptrs ? a.pkh_ptrs[e] + a.pkh_off : a.pkh + (size_t)e * a.pkh_stride;
   // K' = H(pkh || mu)
   uint64_t lanes[SHA3_RATE / 8];
   lanes_zero(lanes);
-  lanes_put(lanes, 0, a.pkh, 32);
+  lanes_put(lanes, 0, pkh, 32);
   lanes_put(lanes, 32, m, mub);
   sha3_256_lanes(lanes, 32 + mub, s);
   sha3_digest(s, a.kprime + 32 * (size_t)e);
   // seedSE' = H(0x01 || pkh || mu)[0:16]
   lanes_zero(lanes);
   lanes[0] = 0x01;
-  lanes_put(lanes, 1, a.pkh, 32);
+  lanes_put(lanes, 1, pkh, 32);
   lanes_put(lanes, 33, m, mub);
   sha3_256_lanes(lanes, 33 + mub, s);
   sha3_digest16(s, a.seeds + 32 * (size_t)e);
@@ -586,7 +590,8 @@ __global__ void __launch_bounds__(128) k_tree_leaves(TreeLeafArgs a) {
   const uint32_t off = c * LWE_TREE_CHUNK;
   const uint32_t len = min((uint32_t)LWE_TREE_CHUNK, a.len - off);
   uint64_t s[25];
-  sha3_256_global(a.msgs + (size_t)e * a.stride + off, len, s);
+  const uint8_t *msg = a.msg_ptrs ? a.msg_ptrs[e] : a.msgs + (size_t)e * a.stride;
+  sha3_256_global(msg + off, len, s);
   uint64_t *dst = reinterpret_cast<uint64_t *>(a.leaves + 32 * (size_t)t);
   dst[0] = s[0];
   dst[1] = s[1];
@@ -614,7 +619,7 @@ __global__ void __launch_bounds__(128) k_tree_root(TreeRootArgs a) {
     // all-ones when the re-encryption matched (flag == 0), else zero
     const uint32_t f = a.flags[e];
     const uint64_t keep = (uint64_t)0 - (uint64_t)(((f | (0u - f)) >> 31) ^ 1u);
-    const uint64_t *z = reinterpret_cast<const uint64_t *>(a.z);
+    const uint64_t *z = reinterpret_cast<const uint64_t *>(a.z_ptrs ? a.z_ptrs[e] + a.z_off : a.z);
     for (int i = 0; i < 4; i++) lanes[i] = (kp[i] & keep) | (z[i] & ~keep);
   }
   for (int i = 0; i < 4; i++) lanes[4 + i] = s[i];

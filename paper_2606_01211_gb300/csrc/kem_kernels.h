@@ -56,6 +56,7 @@ struct DecryptArgs {
   const uint8_t *ct;     // item e at ct + e * ct_bytes
   uint64_t ct_bytes;
   const int8_t *St;      // one secret S^T (8 x n)
+  const uint8_t *const *sk_ptrs;  // per-item secret keys (then St unused)
   uint8_t *mu;           // 32-byte slot per item
   uint32_t n, logq, B, pad;
 };
@@ -72,10 +73,15 @@ struct MulSaArgs {
   uint8_t *out;          // item e rows at out + e*out_stride + 2 k n (uint16)
   uint64_t out_stride;
   uint32_t *flags;       // compare mode: atomicOr(flags[e], 1) on mismatch
+  const uint16_t *const *A_ptrs;  // per-item stored A (then A unused)
+  const uint8_t *const *seed_ptrs;  // per-item seedA at seed_ptrs[e] + seed_off (fused)
+  uint64_t seed_off;
 };
 
 struct VEncArgs {
   const uint8_t *pk;     // seedA || B (n x 8 uint16)
+  const uint8_t *const *pk_ptrs;  // per-item public key at pk_ptrs[e] + pk_off
+  uint64_t pk_off;
   const int8_t *S;       // item e: S' (8 x n) at S + e * s_stride
   uint64_t s_stride;
   const int8_t *Epp;     // item e: E'' (8 x 8) at Epp + e * epp_stride
@@ -101,6 +107,9 @@ struct KeygenSeedArgs {
 struct DeriveArgs {
   const uint8_t *coins;  // Encaps: count x 32; Decaps: NULL (mu given)
   const uint8_t *pkh;    // 32 bytes
+  const uint8_t *const *pkh_ptrs;  // per-item H(pk) at pkh_ptrs[e] + pkh_off
+  uint64_t pkh_off;
+  uint64_t pkh_stride;   // without pointers: H(pk) of item e at pkh + e * pkh_stride
   uint8_t *mu;           // 32-byte slot per item
   uint8_t *kprime;       // 32 per item
   uint8_t *seeds;        // 32-byte slot per item, seedSE' in the first 16
@@ -110,6 +119,7 @@ struct DeriveArgs {
 
 struct TreeLeafArgs {
   const uint8_t *msgs;   // item e at msgs + e * stride
+  const uint8_t *const *msg_ptrs;  // per-item messages (then msgs unused)
   uint64_t stride;
   uint32_t len;          // bytes per item
   uint32_t count;
@@ -128,6 +138,8 @@ struct TreeRootArgs {
   uint64_t out2_stride;
   const uint8_t *kprime; // 32 per item
   const uint8_t *z;      // Decaps: 32 bytes
+  const uint8_t *const *z_ptrs;  // per-item z at z_ptrs[e] + z_off
+  uint64_t z_off;
   const uint32_t *flags; // Decaps: mismatch flag per item
 };
 

@@ -164,6 +164,7 @@ struct lwe_ctx {
   uint8_t *seeds = nullptr, *mu = nullptr, *kp = nullptr, *pkh = nullptr, *leaves = nullptr;
   uint32_t *flags = nullptr, *dev_err = nullptr;
   uint32_t *rk = nullptr;     // 44 AES round-key words per item
+  uint8_t *pkhs = nullptr;    // H(pk) per item (multi-key Encaps)
   int8_t *sp8 = nullptr, *ep8 = nullptr, *epp = nullptr;
   uint16_t *spbf = nullptr;  // bf16 bits
   uint16_t *limbs = nullptr; // bf16 bits, [2][n + 8][n]
@@ -259,17 +260,56 @@ void noise_finish(NoiseArgs &a) {
   for (uint32_t s = 0; s < a.nout; s++) a.runs_per_item += a.out[s].runs;
 }
 
+DeriveArgs derive_args(const lwe_ctx *c, const uint8_t *coins, const uint8_t *pkh,
+                       uint32_t count) {
+  DeriveArgs d;
+  memset(&d, 0, sizeof d);
+  d.coins = coins;
+  d.pkh = pkh;
+  d.mu = c->mu;
+  d.kprime = c->kp;
+  d.seeds = c->seeds;
+  d.rk = c->rk;
+  d.count = count;
+  d.mu_bytes = mu_bytes(c->p);
+  return d;
+}
+
+DecryptArgs decrypt_args(const lwe_ctx *c, const uint8_t *ct, const int8_t *St,
+                         const uint8_t *const *sk_ptrs) {
+  DecryptArgs d;
+  memset(&d, 0, sizeof d);
+  d.ct = ct;
+  d.ct_bytes = ct_bytes(c->p);
+  d.St = St;
+  d.sk_ptrs = sk_ptrs;
+  d.mu = c->mu;
+  d.n = c->p.n;
+  d.logq = c->p.logq;
+  d.B = c->p.B;
+  return d;
+}
+
 // Encrypt (Alg. 2) for `count` items whose seedSE' and mu are in the
 // workspace; writes ct, or (cmp) compares against ct and sets flags.
+// Per-item key material of the multi-key calls: item e's key object is
+// ptrs[e] (its public key at ptrs[e] + pk_off), its stored A is A_ptrs[e]
+// (A_ptrs NULL: every item regenerates A from its seed).
+struct ItemKeys {
+  const uint8_t *const *ptrs = nullptr;
+  uint64_t pk_off = 0;
+  const uint16_t *const *A_ptrs = nullptr;
+};
+
 int run_encrypt(lwe_ctx *c, const uint8_t *pk, const uint16_t *A, uint32_t count, uint8_t *ct,
-                bool cmp, cudaStream_t st) {
+                bool cmp, cudaStream_t st, const ItemKeys *ik = nullptr) {
   const uint32_t n = c->p.n;
   bool tensor = false;
   if (c->path == LWE_PATH_TENSOR)
     tensor = true;
   else if (c->path == LWE_PATH_AUTO)
     tensor = (int)count >= c->tensor_min;
-  tensor = tensor && c->has_tensor;
+  tensor = tensor && c->has_tensor && !ik;  // one GEMM needs one shared A
 
   NoiseArgs na = noise_args(c, count);
   na.nout = 3;
@@ -330,11 +370,22 @@ int run_encrypt(lwe_ctx *c, const uint8_t *pk, const uint16_t *A, uint32_t count
   sa.out = ct;
   sa.out_stride = ct_bytes(c->p);
   sa.flags = c->flags;
-  LAUNCH(c, A ? KID_MUL_SA : KID_MUL_SA_FUSED, st, launch_mul_sa(sa, count, A == nullptr, cmp, st));
+  bool fused = A == nullptr;
+  if (ik) {
+    sa.A_ptrs = ik->A_ptrs;
+    sa.seed_ptrs = ik->ptrs;
+    sa.seed_off = ik->pk_off;
+    fused = ik->A_ptrs == nullptr;
+  }
+  LAUNCH(c, fused ? KID_MUL_SA_FUSED : KID_MUL_SA, st, launch_mul_sa(sa, count, fused, cmp, st));
 
   VEncArgs va;
   memset(&va, 0, sizeof va);
   va.pk = pk;
+  if (ik) {
+    va.pk_ptrs = ik->ptrs;
+    va.pk_off = ik->pk_off;
+  }
   va.S = c->sp8;
   va.s_stride = 8ull * n;
   va.Epp = c->epp;
@@ -351,14 +402,21 @@ int run_encrypt(lwe_ctx *c, const uint8_t *pk, const uint16_t *A, uint32_t count
 }
 
 void tree_leaves(lwe_ctx *c, const uint8_t *msgs, uint64_t stride, uint32_t len, uint32_t count,
-                 cudaStream_t st) {
-  TreeLeafArgs la{msgs, stride, len, count, c->leaves};
+                 cudaStream_t st, const uint8_t *const *msg_ptrs = nullptr) {
+  TreeLeafArgs la;
+  memset(&la, 0, sizeof la);
+  la.msgs = msgs;
+  la.msg_ptrs = msg_ptrs;
+  la.stride = stride;
+  la.len = len;
+  la.count = count;
+  la.leaves = c->leaves;
   LAUNCH(c, KID_TREE_LEAVES, st, launch_tree_leaves(la, st));
 }
 
 void tree_root(lwe_ctx *c, uint32_t len, uint32_t count, int mode, uint8_t *out,
                uint64_t out_stride, uint8_t *out2, uint64_t out2_stride, const uint8_t *z,
-               cudaStream_t st) {
+               cudaStream_t st, const uint8_t *const *z_ptrs = nullptr, uint64_t z_off = 0) {
   TreeRootArgs ra;
   memset(&ra, 0, sizeof ra);
   ra.leaves = c->leaves;
@@ -371,6 +429,8 @@ void tree_root(lwe_ctx *c, uint32_t len, uint32_t count, int mode, uint8_t *out,
   ra.out2_stride = out2_stride;
   ra.kprime = c->kp;
   ra.z = z;
+  ra.z_ptrs = z_ptrs;
+  ra.z_off = z_off;
   ra.flags = c->flags;
   LAUNCH(c, KID_TREE_ROOT, st, launch_tree_root(ra, st));
 }
@@ -485,7 +545,7 @@ int lwe_ctx_create(const lwe_params *p, uint32_t max_batch, int device, lwe_ctx 
   };
   const size_t o_seeds = carve(32 * Bm), o_mu = carve(32 * Bm), o_kp = carve(32 * Bm);
   const size_t o_flags = carve(4 * Bm), o_err = carve(16), o_pkh = carve(32);
-  const size_t o_rk = carve(176 * Bm);
+  const size_t o_rk = carve(176 * Bm), o_pkhs = carve(32 * Bm);
   const size_t o_leaves = carve(32 * (size_t)c->tree_m * Bm);
   const size_t o_sp8 = carve(8 * n * Bm), o_ep8 = carve(8 * n * Bm), o_epp = carve(64 * Bm);
   size_t o_spbf = 0, o_limbs = 0;
@@ -509,6 +569,7 @@ int lwe_ctx_create(const lwe_params *p, uint32_t max_batch, int device, lwe_ctx 
   c->flags = reinterpret_cast<uint32_t *>(c->ws + o_flags);
   c->dev_err = reinterpret_cast<uint32_t *>(c->ws + o_err);
   c->rk = reinterpret_cast<uint32_t *>(c->ws + o_rk);
+  c->pkhs = c->ws + o_pkhs;
   c->pkh = c->ws + o_pkh;
   c->leaves = c->ws + o_leaves;
   c->sp8 = reinterpret_cast<int8_t *>(c->ws + o_sp8);
@@ -658,7 +719,7 @@ int lwe_encaps(lwe_ctx *c, const uint8_t *pk, const uint16_t *A, const uint8_t *
 
   rc = hash_tree(c, pk, pkb, (uint32_t)pkb, 1, TREE_DIGEST, c->pkh, 32, nullptr, 0, nullptr, st);
   if (rc) return rc;
-  DeriveArgs da{coins, c->pkh, c->mu, c->kp, c->seeds, c->rk, count, mu_bytes(p)};
+  DeriveArgs da = derive_args(c, coins, c->pkh, count);
   LAUNCH(c, KID_DERIVE, st, launch_derive(da, st));
   rc = run_encrypt(c, pk, A, count, ct, false, st);
   if (rc) return rc;
@@ -690,14 +751,85 @@ int lwe_decaps(lwe_ctx *c, const uint8_t *sk, const uint16_t *A, const uint8_t *
   CUDA_TRY(cudaStreamWaitEvent(c->side, c->ev_fork, 0));
   tree_leaves(c, ct, ctb, (uint32_t)ctb, count, c->side);
   CUDA_TRY(cudaEventRecord(c->ev_join, c->side));
-  DecryptArgs dca{ct, ctb, reinterpret_cast<const int8_t *>(sk), c->mu, n, p.logq, p.B, 0};
+  DecryptArgs dca = decrypt_args(c, ct, reinterpret_cast<const int8_t *>(sk), nullptr);
   LAUNCH(c, KID_DECRYPT, st, launch_decrypt(dca, count, st));
-  DeriveArgs da{nullptr, pkh, c->mu, c->kp, c->seeds, c->rk, count, mu_bytes(p)};
+  DeriveArgs da = derive_args(c, nullptr, pkh, count);
   LAUNCH(c, KID_DERIVE, st, launch_derive(da, st));
   rc = run_encrypt(c, pk, A, count, const_cast<uint8_t *>(ct), true, st);
   if (rc) return rc;
   CUDA_TRY(cudaStreamWaitEvent(st, c->ev_join, 0));
   tree_root(c, (uint32_t)ctb, count, TREE_DEC_KEY, K, 32, nullptr, 0, z, st);
+  return check_launch();
+}
+
+int lwe_encaps_multi(lwe_ctx *c, const uint8_t *const *pk_ptrs, const uint8_t *const *pkh_ptrs,
+                     const uint16_t *const *A_ptrs, const uint8_t *coins, uint32_t count,
+                     uint8_t *ct, uint8_t *K, void *stream) {
+  if (!c) return LWE_EINVAL;
+  if (count == 0) return LWE_OK;
+  if (count > c->max_batch) return LWE_ECAPACITY;
+  if (!pk_ptrs || !coins || !ct || !K || !aligned16(coins) || !aligned16(ct) || !aligned16(K) ||
+      (reinterpret_cast<uintptr_t>(pk_ptrs) & 7) || (reinterpret_cast<uintptr_t>(pkh_ptrs) & 7) ||
+      (reinterpret_cast<uintptr_t>(A_ptrs) & 7))
+    return LWE_EINVAL;
+  int rc = set_device_of(c);
+  if (rc) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  const lwe_params &p = c->p;
+  const size_t pkb = pk_bytes(p), ctb = ct_bytes(p);
+  DeriveArgs da = derive_args(c, coins, nullptr, count);
+  if (pkh_ptrs) {
+    da.pkh_ptrs = pkh_ptrs;
+  } else {  // H(pk) of every item's key
+    tree_leaves(c, nullptr, 0, (uint32_t)pkb, count, st, pk_ptrs);
+    tree_root(c, (uint32_t)pkb, count, TREE_DIGEST, c->pkhs, 32, nullptr, 0, nullptr, st);
+    da.pkh = c->pkhs;
+    da.pkh_stride = 32;
+  }
+  LAUNCH(c, KID_DERIVE, st, launch_derive(da, st));
+  ItemKeys ik;
+  ik.ptrs = pk_ptrs;
+  ik.pk_off = 0;
+  ik.A_ptrs = A_ptrs;
+  rc = run_encrypt(c, nullptr, nullptr, count, ct, false, st, &ik);
+  if (rc) return rc;
+  return hash_tree(c, ct, ctb, (uint32_t)ctb, count, TREE_ENC_KEY, K, 32, nullptr, 0, nullptr, st);
+}
+
+int lwe_decaps_multi(lwe_ctx *c, const uint8_t *const *sk_ptrs, const uint16_t *const *A_ptrs,
+                     const uint8_t *ct, uint32_t count, uint8_t *K, void *stream) {
+  if (!c) return LWE_EINVAL;
+  if (count == 0) return LWE_OK;
+  if (count > c->max_batch) return LWE_ECAPACITY;
+  if (!sk_ptrs || !ct || !K || !aligned16(ct) || !aligned16(K) ||
+      (reinterpret_cast<uintptr_t>(sk_ptrs) & 7) || (reinterpret_cast<uintptr_t>(A_ptrs) & 7))
+    return LWE_EINVAL;
+  int rc = set_device_of(c);
+  if (rc) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  const lwe_params &p = c->p;
+  const uint32_t n = p.n;
+  const size_t ctb = ct_bytes(p);
+  CUDA_TRY(cudaMemsetAsync(c->flags, 0, 4 * (size_t)count, st));
+  CUDA_TRY(cudaEventRecord(c->ev_fork, st));
+  CUDA_TRY(cudaStreamWaitEvent(c->side, c->ev_fork, 0));
+  tree_leaves(c, ct, ctb, (uint32_t)ctb, count, c->side);
+  CUDA_TRY(cudaEventRecord(c->ev_join, c->side));
+  DecryptArgs dca = decrypt_args(c, ct, nullptr, sk_ptrs);
+  LAUNCH(c, KID_DECRYPT, st, launch_decrypt(dca, count, st));
+  DeriveArgs da = derive_args(c, nullptr, nullptr, count);
+  da.pkh_ptrs = sk_ptrs;  // H(pk) is stored inside sk
+  da.pkh_off = 8ull * n + 32;
+  LAUNCH(c, KID_DERIVE, st, launch_derive(da, st));
+  ItemKeys ik;
+  ik.ptrs = sk_ptrs;
+  ik.pk_off = 8ull * n + 64;  // pk is stored inside sk
+  ik.A_ptrs = A_ptrs;
+  rc = run_encrypt(c, nullptr, nullptr, count, const_cast<uint8_t *>(ct), true, st, &ik);
+  if (rc) return rc;
+  CUDA_TRY(cudaStreamWaitEvent(st, c->ev_join, 0));
+  tree_root(c, (uint32_t)ctb, count, TREE_DEC_KEY, K, 32, nullptr, 0, nullptr, st, sk_ptrs,
+            8ull * n);
   return check_launch();
 }
 
@@ -849,7 +981,7 @@ int lwe_encaps_noalloc(const lwe_params *p, const uint8_t *pk, const uint16_t *A
   const size_t pkb = pk_bytes(*p), ctb = ct_bytes(*p);
   rc = hash_tree(&c, pk, pkb, (uint32_t)pkb, 1, TREE_DIGEST, c.pkh, 32, nullptr, 0, nullptr, st);
   if (rc) return rc;
-  DeriveArgs da{coins, c.pkh, c.mu, c.kp, c.seeds, c.rk, count, mu_bytes(*p)};
+  DeriveArgs da = derive_args(&c, coins, c.pkh, count);
   LAUNCH(&c, KID_DERIVE, st, launch_derive(da, st));
   rc = run_encrypt(&c, pk, A, count, ct, false, st);
   if (rc) return rc;

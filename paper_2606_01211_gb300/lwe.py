@@ -66,6 +66,8 @@ def _load():
         "lwe_keygen": (i32, [vp, vp, u32, vp, vp, vp, vp]),
         "lwe_encaps": (i32, [vp, vp, vp, vp, u32, vp, vp, vp]),
         "lwe_decaps": (i32, [vp, vp, vp, vp, u32, vp, vp]),
+        "lwe_encaps_multi": (i32, [vp, vp, vp, vp, vp, u32, vp, vp, vp]),
+        "lwe_decaps_multi": (i32, [vp, vp, vp, vp, u32, vp, vp]),
         "lwe_expand_A": (i32, [vp, u32, u32, vp, vp]),
         "lwe_matmul_modq": (i32, [vp, i32, vp, vp, vp, u32, u32, u32, vp, vp, vp]),
         "lwe_encaps_noalloc": (i32, [P, vp, vp, vp, u32, vp, vp, vp]),
@@ -252,6 +254,32 @@ class Ctx:
             _ptr(K, torch.uint8, 32 * count, "K"), _stream(stream))
         _check(rc, "lwe_encaps")
 
+    def encaps_multi(self, pk_ptrs: torch.Tensor, coins: torch.Tensor, ct: torch.Tensor,
+                     K: torch.Tensor, pkh_ptrs: torch.Tensor | None = None,
+                     A_ptrs: torch.Tensor | None = None, count: int | None = None, stream=None):
+        """Item e against its own key: pk_ptrs / pkh_ptrs / A_ptrs are device
+        int64 tensors of device pointers (the data_ptr() of each key)."""
+        p = self.params
+        if count is None:
+            count = coins.shape[0]
+        rc = _lib.lwe_encaps_multi(
+            self._h, _ptr_array(pk_ptrs, count, "pk_ptrs"), _ptr_array(pkh_ptrs, count, "pkh_ptrs"),
+            _ptr_array(A_ptrs, count, "A_ptrs"), _ptr(coins, torch.uint8, 32 * count, "coins"),
+            count, _ptr(ct, torch.uint8, count * p.ct_bytes, "ct"),
+            _ptr(K, torch.uint8, 32 * count, "K"), _stream(stream))
+        _check(rc, "lwe_encaps_multi")
+
+    def decaps_multi(self, sk_ptrs: torch.Tensor, ct: torch.Tensor, K: torch.Tensor,
+                     A_ptrs: torch.Tensor | None = None, count: int | None = None, stream=None):
+        p = self.params
+        if count is None:
+            count = ct.shape[0]
+        rc = _lib.lwe_decaps_multi(
+            self._h, _ptr_array(sk_ptrs, count, "sk_ptrs"), _ptr_array(A_ptrs, count, "A_ptrs"),
+            _ptr(ct, torch.uint8, count * p.ct_bytes, "ct"), count,
+            _ptr(K, torch.uint8, 32 * count, "K"), _stream(stream))
+        _check(rc, "lwe_decaps_multi")
+
     def decaps(self, sk: torch.Tensor, ct: torch.Tensor, K: torch.Tensor,
                A: torch.Tensor | None = None, stream=None, count: int | None = None):
         p = self.params
@@ -263,6 +291,14 @@ class Ctx:
             _ptr(ct, torch.uint8, count * p.ct_bytes, "ct"), count,
             _ptr(K, torch.uint8, 32 * count, "K"), _stream(stream))
         _check(rc, "lwe_decaps")
+
+
+def _ptr_array(ptrs: torch.Tensor | None, count: int, what: str) -> int | None:
+    if ptrs is None:
+        return None
+    if ptrs.dtype != torch.int64 or not ptrs.is_cuda or ptrs.numel() < count:
+        raise ValueError("%s must be a CUDA int64 tensor of at least %d pointers" % (what, count))
+    return ptrs.data_ptr()
 
 
 def expand_A(seedA: torch.Tensor, n: int, logq: int, A_out: torch.Tensor, stream=None):

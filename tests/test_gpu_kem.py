@@ -257,3 +257,50 @@ def test_bounded_wait_times_out_cleanly():
     ctx.keygen(dev(ms), pk, sk)
     pk_o, sk_o = O.keygen(po, bytes(ms[0]))
     assert np.array_equal(host(pk)[0], pk_o)
+
+
+@pytest.mark.parametrize("name", ["P640", "P976"])
+@pytest.mark.parametrize("stored", [True, False])
+@pytest.mark.parametrize("give_pkh", [True, False])
+def test_multi_key_calls_equal_single_key_calls(name, stored, give_pkh):
+    """lwe_encaps_multi / lwe_decaps_multi (each item with its own key) give
+    exactly what one single-key call per item gives, and the oracle's."""
+    p, po = params(name)
+    nk, count = 5, 23
+    ms = master_seeds(nk, seed=40)
+    ctx = lwe.Ctx(p, max_batch=max(nk, count))
+    ctx.set_path(lwe.PATH_SKINNY)
+    pk, sk = ctx.empty_pk(nk), ctx.empty_sk(nk)
+    A = torch.empty((nk, p.n, p.n), dtype=torch.int16, device="cuda")
+    ctx.keygen(dev(ms), pk, sk, A_out=A)
+    keys = np.random.default_rng(41).integers(0, nk, size=count)
+    pk_ptrs = torch.tensor([pk[k].data_ptr() for k in keys], dtype=torch.int64, device="cuda")
+    sk_ptrs = torch.tensor([sk[k].data_ptr() for k in keys], dtype=torch.int64, device="cuda")
+    pkh_ptrs = torch.tensor([sk[k].data_ptr() + 8 * p.n + 32 for k in keys], dtype=torch.int64,
+                            device="cuda")
+    A_ptrs = torch.tensor([A[k].data_ptr() for k in keys], dtype=torch.int64, device="cuda")
+    cs = coins(count, seed=42)
+    ct = ctx.empty_ct(count)
+    K = torch.empty((count, 32), dtype=torch.uint8, device="cuda")
+    ctx.encaps_multi(pk_ptrs, dev(cs), ct, K, pkh_ptrs=pkh_ptrs if give_pkh else None,
+                     A_ptrs=A_ptrs if stored else None)
+    K2 = torch.empty_like(K)
+    ctx.decaps_multi(sk_ptrs, ct, K2, A_ptrs=A_ptrs if stored else None)
+    bad = ct.clone()
+    bad[::2, 11] ^= 1
+    Kb = torch.empty_like(K)
+    ctx.decaps_multi(sk_ptrs, bad, Kb, A_ptrs=A_ptrs if stored else None)
+    ct1, K1 = ctx.empty_ct(1), torch.empty((1, 32), dtype=torch.uint8, device="cuda")
+    Kb1 = torch.empty_like(K1)
+    for i, k in enumerate(keys):
+        ctx.encaps(pk[k], dev(cs[i:i + 1]), ct1, K1, A=A[k])
+        assert torch.equal(ct1[0], ct[i]) and torch.equal(K1[0], K[i]), i
+        ctx.decaps(sk[k], bad[i:i + 1], Kb1, A=A[k])
+        assert torch.equal(Kb1[0], Kb[i]), i
+    assert torch.equal(K2, K)
+    assert not (host(Kb)[::2] == host(K)[::2]).all(axis=1).any()
+    k0 = int(keys[0])
+    pk_o, sk_o = O.keygen(po, bytes(ms[k0]))
+    ct_o, K_o = O.encaps(po, pk_o, bytes(cs[0]))
+    assert np.array_equal(host(ct)[0], ct_o) and np.array_equal(host(K)[0], K_o)
+    assert ctx.device_error() == 0
