@@ -204,8 +204,11 @@ def run_ours(args, rank, world, local_rank):
     dev = torch.device("cuda", local_rank)
     pk_d, _ = peaks()
     p = lwe.Params(**PRESETS[PRESET])
+    from paper_2606_01211_gb300 import batch
+    tuned = batch.autotune(PRESET, COUNT)
     ctx = lwe.Ctx(p, max_batch=COUNT, device=local_rank)
     ctx.set_path(lwe.PATH_TENSOR)
+    ctx.set_option(lwe.OPT_GEMM_BN, tuned["gemm_bn"])
     pk, sk = ctx.empty_pk(1), ctx.empty_sk(1)
     A = torch.empty((p.n, p.n), dtype=torch.int16, device=dev)
     ms = torch.from_numpy(master_seeds(1, seed=1 + rank)).to(dev)
@@ -325,6 +328,27 @@ def run_ours(args, rank, world, local_rank):
         plain = COUNT / (a.elapsed_time(b) / 1e3)
         ctx.set_path(lwe.PATH_TENSOR)
 
+    # the same step replayed from a CUDA graph (one launch per step)
+    graph_value = None
+    if not args.no_graph:
+        kem = batch.BatchedKem(PRESET, COUNT, seed=1 + rank, gemm_bn=tuned["gemm_bn"])
+        kem.capture()
+        ts = []
+        for i in range(args.warmup + args.steps):
+            flush.fill_(i)
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            kem.replay(cs_all[i])
+            b.record(stream)
+            torch.cuda.synchronize()
+            if i >= args.warmup:
+                ts.append(a.elapsed_time(b))
+        assert torch.equal(kem.K, kem.K2)
+        graph_value = COUNT * len(ts) / (sum(ts) / 1e3)
+        kem.close()
+
+    served = None if args.no_serve else serve_measure(torch)
     latency = None if args.no_latency else single_request_latency(lwe, torch, dev)
     as_sweep = None if args.no_sweep else as_gbs_sweep(lwe, torch, dev, flush)
 
@@ -350,12 +374,35 @@ def run_ours(args, rank, world, local_rank):
         "plain_path_value": plain,
         "batched_vs_plain": (value / world / plain) if plain else None,
         "kernels_ms_per_step": {k: v[1] / args.steps for k, v in stats.items()},
+        "graph_value": graph_value,
+        "autotune": {"gemm_bn": tuned["gemm_bn"], "tensor_min": tuned["tensor_min"]},
+        "served": served,
         "latency_p640_us": latency,
         "as_gbs": as_sweep,
         "correct": bool(ok) and err == 0,
     }
     print(json.dumps(line))
     return 0
+
+
+def serve_measure(torch, rate: float = 1e5, requests: int = 20000):
+    """The served mix (KeyGen/Encaps/Decaps 10/70/20 over n in {640, 976,
+    1344, 4096}, 10 000 resident keys, Zipf 1.1) at one open-loop arrival
+    rate, continuous batching versus one launch per request."""
+    from paper_2606_01211_gb300 import serve
+    cfg = serve.ServeConfig(rate=rate, requests=requests)
+    store = serve.KeyStore(cfg, torch.device("cuda", torch.cuda.current_device()))
+    out = {}
+    for plain in (False, True):
+        c = serve.ServeConfig(**{**cfg.__dict__, "plain": plain,
+                                 "requests": requests if not plain else 8000})
+        st = serve.Engine(c, store=store).run()
+        out["plain" if plain else "batched"] = {k: st[k] for k in
+                                               ("ops_per_s", "p50_ms", "p99_ms", "mean_batch",
+                                                "requests")}
+    out["rate"] = rate
+    out["served_vs_plain"] = out["batched"]["ops_per_s"] / out["plain"]["ops_per_s"]
+    return out
 
 
 def single_request_latency(lwe, torch, dev, reps: int = 300):
@@ -432,6 +479,8 @@ def main():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-latency", action="store_true")
+    ap.add_argument("--no-graph", action="store_true")
+    ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-sweep", action="store_true")
     ap.add_argument("--cpu-s", type=float, default=12.0)
     ap.add_argument("--ref-step-s", type=float, default=8.0)

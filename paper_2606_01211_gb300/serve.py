@@ -63,19 +63,26 @@ def zipf_keys(count: int, n_keys: int, s: float, r: np.random.Generator) -> np.n
 
 
 class KeyStore:
-    """Resident key pairs per dimension and an LRU cache of expanded A."""
+    """Resident key pairs per dimension and an LRU cache of expanded A.
 
-    def __init__(self, cfg: ServeConfig, device: torch.device):
+    The cache is an arena allocated once (the budget split evenly over the
+    dimensions, one fixed slot of 2 n^2 bytes per cached A), so admitting a
+    key never allocates device memory while serving.  A slot that is
+    reused waits, on the stream that refills it, for the last batch that
+    read it.  The most popular keys are expanded up front."""
+
+    def __init__(self, cfg: ServeConfig, device: torch.device, prefill: bool = True):
         self.dev = device
         self.params = {}
         self.pk, self.sk = {}, {}
-        self.budget = cfg.a_budget_bytes
-        self.used = 0
-        self.cache: "collections.OrderedDict[tuple, torch.Tensor]" = collections.OrderedDict()
         self.hits = self.misses = 0
+        self.arena, self.slot_of, self.lru, self.free, self.last_use = {}, {}, {}, {}, {}
+        self.ready = {}
+        share = cfg.a_budget_bytes // max(1, len(cfg.presets))
         for i, name in enumerate(cfg.presets):
             p = lwe.Params(**PRESETS[name])
-            self.params[p.n] = p
+            n = p.n
+            self.params[n] = p
             ctx = lwe.Ctx(p, max_batch=min(cfg.keys_per_n, 256), device=device.index)
             ms = torch.from_numpy(master_seeds(cfg.keys_per_n, seed=cfg.seed * 100 + i)).to(device)
             pk = torch.empty((cfg.keys_per_n, p.pk_bytes), dtype=torch.uint8, device=device)
@@ -83,38 +90,62 @@ class KeyStore:
             for a in range(0, cfg.keys_per_n, 256):
                 b = min(cfg.keys_per_n, a + 256)
                 ctx.keygen(ms[a:b], pk[a:b], sk[a:b])
-            self.pk[p.n], self.sk[p.n] = pk, sk
+            self.pk[n], self.sk[n] = pk, sk
             ctx.close()
+            slots = int(min(cfg.keys_per_n, share // (2 * n * n)))
+            self.arena[n] = torch.empty((max(slots, 0), n, n), dtype=torch.int16, device=device)
+            self.slot_of[n] = {}
+            self.lru[n] = collections.OrderedDict()
+            self.free[n] = list(range(slots - 1, -1, -1))
+            self.last_use[n] = [None] * slots
+            self.ready[n] = [None] * slots
+            if prefill:  # key k is the (k+1)-th most popular (Zipf rank)
+                for k in range(slots):
+                    self._fill(n, k, torch.cuda.current_stream(device))
         torch.cuda.synchronize(device)
+        self.hits = self.misses = 0
+
+    def _fill(self, n, key, stream):
+        if self.free[n]:
+            s = self.free[n].pop()
+        else:
+            old, s = self.lru[n].popitem(last=False)
+            del self.slot_of[n][old]
+            if self.last_use[n][s] is not None:
+                stream.wait_event(self.last_use[n][s])
+        with torch.cuda.stream(stream):
+            lwe.expand_A(self.pk[n][key, :16], n, self.params[n].logq, self.arena[n][s], stream=stream)
+            ev = torch.cuda.Event()
+            ev.record(stream)
+        self.ready[n][s] = ev
+        self.slot_of[n][key] = s
+        self.lru[n][key] = s
+        return s
 
     def cached(self, n: int, key: int) -> bool:
-        return (n, key) in self.cache
+        return key in self.slot_of[n]
 
-    def A(self, n: int, key: int, stream: torch.cuda.Stream):
-        """The cached A of a key, expanding it on a miss while the budget
-        allows (least recently used entries are evicted); None = regenerate
-        A inside the kernels."""
-        k = (n, key)
-        t = self.cache.get(k)
-        if t is not None:
-            self.cache.move_to_end(k)
+    def A(self, n: int, key: int, stream: torch.cuda.Stream, admit: bool = True):
+        """The cached A of a key (LRU order refreshed), expanding it into a
+        free or least recently used slot on a miss; None = regenerate A
+        inside the kernels (no slot for this dimension, or admit=False)."""
+        s = self.slot_of[n].get(key)
+        if s is not None:
+            self.lru[n].move_to_end(key)
             self.hits += 1
-            t.record_stream(stream)
-            return t
+            stream.wait_event(self.ready[n][s])  # filled, possibly on another stream
+            return self.arena[n][s]
         self.misses += 1
-        need = 2 * n * n
-        if need > self.budget:
+        if not admit or self.arena[n].shape[0] == 0:
             return None
-        while self.used + need > self.budget and self.cache:
-            _, old = self.cache.popitem(last=False)
-            self.used -= old.numel() * 2
-            del old
-        with torch.cuda.stream(stream):
-            t = torch.empty((n, n), dtype=torch.int16, device=self.dev)
-            lwe.expand_A(self.pk[n][key, :16], n, self.params[n].logq, t, stream=stream)
-        self.cache[k] = t
-        self.used += need
-        return t
+        return self.arena[n][self._fill(n, key, stream)]
+
+    def used_by(self, n: int, keys, event: torch.cuda.Event):
+        """Record the batch that reads these keys' cached A."""
+        for k in keys:
+            s = self.slot_of[n].get(int(k))
+            if s is not None:
+                self.last_use[n][s] = event
 
 
 class Slot:
@@ -282,6 +313,8 @@ class Engine:
                 P["K"].index_copy_(0, rows_d, B["K"][:cnt])
             ev = torch.cuda.Event()
             ev.record(st)
+        if op != "keygen":
+            self.store.used_by(n, {q.key for q in group}, ev)
         slot.event, slot.reqs = ev, group
 
     def _take(self, fifo: collections.deque, per_key: collections.Counter, mb: int):

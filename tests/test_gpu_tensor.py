@@ -128,3 +128,28 @@ def test_batched_4096_tensor_equals_skinny_and_oracle_samples():
         assert np.array_equal(ct_t[i], ct_o), i
         assert np.array_equal(K_t[i], K_o), i
     assert ctx.device_error() == 0
+
+
+def test_graph_replay_equals_direct_calls():
+    """The captured Encaps+Decaps step, replayed with new coins, gives what
+    the direct calls give."""
+    from paper_2606_01211_gb300 import batch
+    kem = batch.BatchedKem("P976", 96, seed=9)
+    kem.capture()
+    for s in (1, 2):
+        cs = dev(coins(96, seed=900 + s))
+        kem.replay(cs)
+        torch.cuda.synchronize()
+        ct_g, K_g, K2_g = kem.ct.clone(), kem.K.clone(), kem.K2.clone()
+        ct = kem.ctx.empty_ct(96)
+        K = torch.empty((96, 32), dtype=torch.uint8, device="cuda")
+        kem.ctx.encaps(kem.pk, cs, ct, K, A=kem.A)
+        assert torch.equal(ct, ct_g) and torch.equal(K, K_g) and torch.equal(K2_g, K_g)
+    kem.close()
+
+
+def test_autotune_returns_a_valid_choice():
+    from paper_2606_01211_gb300 import batch
+    res = batch.autotune("P640", 256, cache=None)
+    assert res["gemm_bn"] in (64, 128)
+    assert 16 <= res["tensor_min"] <= 257
