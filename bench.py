@@ -196,39 +196,42 @@ def algorithmic(p, count):
     }
 
 
+def max_over_ranks(x: float, dist, device) -> float:
+    """The slowest rank's value (whole-job time of independent replicas)."""
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_seeds(rank: int) -> tuple:
+    """Each rank is an independent replica with its own key and coins."""
+    return 1 + rank, 7 + rank
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
-    from paper_2606_01211_gb300 import lwe
+    from paper_2606_01211_gb300 import batch, lwe
 
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
     pk_d, _ = peaks()
     p = lwe.Params(**PRESETS[PRESET])
-    from paper_2606_01211_gb300 import batch
     tuned = batch.autotune(PRESET, COUNT)
-    ctx = lwe.Ctx(p, max_batch=COUNT, device=local_rank)
-    ctx.set_path(lwe.PATH_TENSOR)
-    ctx.set_option(lwe.OPT_GEMM_BN, tuned["gemm_bn"])
-    pk, sk = ctx.empty_pk(1), ctx.empty_sk(1)
-    A = torch.empty((p.n, p.n), dtype=torch.int16, device=dev)
-    ms = torch.from_numpy(master_seeds(1, seed=1 + rank)).to(dev)
-    ctx.keygen(ms, pk, sk, A_out=A)
     nsteps = args.warmup + args.steps
-    cs_all = torch.from_numpy(coins(COUNT * nsteps, seed=7 + rank)).to(dev).view(nsteps, COUNT, 32)
-    ct = ctx.empty_ct(COUNT)
-    K = torch.empty((COUNT, 32), dtype=torch.uint8, device=dev)
-    K2 = torch.empty_like(K)
+    key_seed, coin_seed = replica_seeds(rank)
+    cs_all = torch.from_numpy(coins(COUNT * nsteps, seed=coin_seed)).to(dev).view(nsteps, COUNT, 32)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.int32, device=dev)
     stream = torch.cuda.current_stream()
 
-    def step(i):
-        ctx.encaps(pk, cs_all[i], ct, K, A=A)
-        ctx.decaps(sk, ct, K2, A=A)
-
+    # the step: 4096 Encaps + 4096 Decaps against one key (direct launches,
+    # CUDA events around every kernel on its launch stream)
+    kem = batch.BatchedKem(PRESET, COUNT, seed=key_seed, gemm_bn=tuned["gemm_bn"])
     for i in range(args.warmup):
-        step(i)
+        kem.coins.copy_(cs_all[i])
+        kem.step()
     torch.cuda.synchronize()
-    assert torch.equal(K, K2), "decapsulated keys differ from the encapsulated keys"
+    assert torch.equal(kem.K, kem.K2), "decapsulated keys differ from the encapsulated keys"
 
     dist = None
     if world > 1:
@@ -236,37 +239,56 @@ def run_ours(args, rank, world, local_rank):
         dist = dist_
         dist.barrier()
     torch.cuda.synchronize()
-    ctx.set_option(lwe.OPT_TIMING, 1)
-    ctx.reset_stats()
-    launches0 = ctx.launches()
+    kem.ctx.set_option(lwe.OPT_TIMING, 1)
+    kem.ctx.reset_stats()
+    launches0 = kem.ctx.launches()
     clk = ClockSampler(local_rank)
     clk.start()
+    step_ms = []
     evs = []
     for i in range(args.warmup, nsteps):
         flush.fill_(i)  # L2 flush, outside the timed events
+        kem.coins.copy_(cs_all[i])
         a = torch.cuda.Event(enable_timing=True)
         b = torch.cuda.Event(enable_timing=True)
         a.record(stream)
-        step(i)
+        kem.step()
         b.record(stream)
         evs.append((a, b))
     torch.cuda.synchronize()
     clocks = clk.stop()
-    launches = ctx.launches() - launches0
-    stats = ctx.kernel_stats()
-    ctx.set_option(lwe.OPT_TIMING, 0)
     step_ms = [a.elapsed_time(b) for a, b in evs]
+    stats = kem.ctx.kernel_stats()
+    kem.ctx.set_option(lwe.OPT_TIMING, 0)
+    launches = kem.ctx.launches() - launches0
     tot_ms = sum(step_ms)
     if dist is not None:
-        t = torch.tensor([tot_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        tot_ms = float(t.item())
+        tot_ms = max_over_ranks(tot_ms, dist, dev)
         dist.barrier()
-    ok = torch.equal(K, K2)
-    err = ctx.device_error()
+    ok = torch.equal(kem.K, kem.K2)
+    err = kem.ctx.device_error()
     value = world * COUNT * args.steps / (tot_ms / 1e3)
 
+    # the same step replayed from a CUDA graph (one launch per step)
+    graph_value = None
+    if not args.no_plain:
+        kem.capture()
+        ts = []
+        for i in range(args.warmup + args.steps):
+            flush.fill_(i)
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            kem.replay(cs_all[i])
+            b.record(stream)
+            torch.cuda.synchronize()
+            if i >= args.warmup:
+                ts.append(a.elapsed_time(b))
+        assert torch.equal(kem.K, kem.K2)
+        graph_value = world * COUNT * len(ts) / (sum(ts) / 1e3)
+
     if rank != 0:
+        kem.close()
         return 0
 
     # roofline of the dominant kernel (largest share of the timed region):
@@ -289,22 +311,21 @@ def run_ours(args, rank, world, local_rank):
                 "kernel": dom, "launches_per_step": nl / args.steps,
                 "share": kernel_total[dom] / sum(kernel_total.values()), "traffic": None}
 
-    # end to end through the public API with host buffers
+    # end to end through the public API: coins from pinned host memory into
+    # the step's input buffer, the replayed step, both key sets back to host
     e2e = None
     if not args.no_e2e:
         hc = torch.from_numpy(coins(COUNT, seed=99)).pin_memory()
         hK = torch.empty((COUNT, 32), dtype=torch.uint8).pin_memory()
         hK2 = torch.empty_like(hK).pin_memory()
-        dc = torch.empty((COUNT, 32), dtype=torch.uint8, device=dev)
         ts = []
         for i in range(args.warmup + args.steps):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            dc.copy_(hc, non_blocking=True)
-            ctx.encaps(pk, dc, ct, K, A=A)
-            ctx.decaps(sk, ct, K2, A=A)
-            hK.copy_(K, non_blocking=True)
-            hK2.copy_(K2, non_blocking=True)
+            kem.coins.copy_(hc, non_blocking=True)
+            kem.step()
+            hK.copy_(kem.K, non_blocking=True)
+            hK2.copy_(kem.K2, non_blocking=True)
             torch.cuda.synchronize()
             if i >= args.warmup:
                 ts.append(time.perf_counter() - t0)
@@ -312,41 +333,28 @@ def run_ours(args, rank, world, local_rank):
         e2e = {"value": COUNT / statistics.mean(ts), "unit": UNIT,
                "h2d_bytes_per_step": COUNT * 32, "d2h_bytes_per_step": 2 * COUNT * 32}
 
-    # the plain per-request path (CUDA cores, one item per row of CTAs)
-    plain = None
-    if not args.no_plain:
-        ctx.set_path(lwe.PATH_SKINNY)
+    # the same step with direct launches (no graph), and on the plain
+    # per-request path (CUDA cores, one item per row of CTAs)
+    def direct_rate(path):
+        kem.ctx.set_path(path)
         for i in range(2):
-            step(i)
+            kem.step()
         torch.cuda.synchronize()
-        a = torch.cuda.Event(enable_timing=True)
-        b = torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        step(0)
-        b.record(stream)
-        torch.cuda.synchronize()
-        plain = COUNT / (a.elapsed_time(b) / 1e3)
-        ctx.set_path(lwe.PATH_TENSOR)
-
-    # the same step replayed from a CUDA graph (one launch per step)
-    graph_value = None
-    if not args.no_graph:
-        kem = batch.BatchedKem(PRESET, COUNT, seed=1 + rank, gemm_bn=tuned["gemm_bn"])
-        kem.capture()
         ts = []
-        for i in range(args.warmup + args.steps):
+        for i in range(3):
             flush.fill_(i)
             a = torch.cuda.Event(enable_timing=True)
             b = torch.cuda.Event(enable_timing=True)
             a.record(stream)
-            kem.replay(cs_all[i])
+            kem.step()
             b.record(stream)
             torch.cuda.synchronize()
-            if i >= args.warmup:
-                ts.append(a.elapsed_time(b))
-        assert torch.equal(kem.K, kem.K2)
-        graph_value = COUNT * len(ts) / (sum(ts) / 1e3)
-        kem.close()
+            ts.append(a.elapsed_time(b))
+        kem.ctx.set_path(lwe.PATH_TENSOR)
+        return COUNT / (statistics.median(ts) / 1e3)
+
+    plain = None if args.no_plain else direct_rate(lwe.PATH_SKINNY)
+    kem.close()
 
     served = None if args.no_serve else serve_measure(torch)
     latency = None if args.no_latency else single_request_latency(lwe, torch, dev)
@@ -364,6 +372,7 @@ def run_ours(args, rank, world, local_rank):
         "scaling": "weak", "vs_baseline": None, "dtype": "u16",
         "data": "synthetic (seeded random keys and coins)",
         "config": {"workload": WORKLOAD, "n": p.n, "batch": COUNT, "path": "tensor",
+                   "launch": "direct launches (graph replay reported as graph_value)",
                    "l2": "flushed between timed steps (256 MiB write), per-step CUDA events",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "gpu_launches": launches,
@@ -371,10 +380,10 @@ def run_ours(args, rank, world, local_rank):
         "cpu_baseline": cpu,
         "e2e": e2e,
         "clocks": clocks,
+        "graph_value": graph_value,
         "plain_path_value": plain,
         "batched_vs_plain": (value / world / plain) if plain else None,
         "kernels_ms_per_step": {k: v[1] / args.steps for k, v in stats.items()},
-        "graph_value": graph_value,
         "autotune": {"gemm_bn": tuned["gemm_bn"], "tensor_min": tuned["tensor_min"]},
         "served": served,
         "latency_p640_us": latency,
@@ -396,7 +405,9 @@ def serve_measure(torch, rate: float = 1e5, requests: int = 20000):
     for plain in (False, True):
         c = serve.ServeConfig(**{**cfg.__dict__, "plain": plain,
                                  "requests": requests if not plain else 8000})
-        st = serve.Engine(c, store=store).run()
+        eng = serve.Engine(c, store=store)
+        eng.warmup()
+        st = eng.run()
         out["plain" if plain else "batched"] = {k: st[k] for k in
                                                ("ops_per_s", "p50_ms", "p99_ms", "mean_batch",
                                                 "requests")}
@@ -479,7 +490,6 @@ def main():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-latency", action="store_true")
-    ap.add_argument("--no-graph", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-sweep", action="store_true")
     ap.add_argument("--cpu-s", type=float, default=12.0)

@@ -276,6 +276,13 @@ int lwe_selftest_bounded_wait(lwe_ctx *ctx, uint32_t limit_us, void *stream);
 int lwe_ctx_kernel_stats(lwe_ctx *ctx, int kernel_id, uint64_t *launches,
                          double *total_ms);
 int lwe_ctx_reset_stats(lwe_ctx *ctx);
+/* Timing of launches captured into a CUDA graph: after capturing with
+ * LWE_OPT_TIMING = 1, lwe_ctx_timing_mark keeps the captured event pairs
+ * (their records are graph nodes, re-recorded by every replay); after each
+ * replay has completed, lwe_ctx_timing_replay adds their durations to the
+ * per-kernel statistics.  Marking again releases the previous pairs. */
+int lwe_ctx_timing_mark(lwe_ctx *ctx);
+int lwe_ctx_timing_replay(lwe_ctx *ctx);
 /* Name of kernel id 0..lwe_num_kernels()-1, NULL out of range. */
 const char *lwe_kernel_name(int kernel_id);
 int lwe_num_kernels(void);

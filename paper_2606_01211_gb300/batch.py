@@ -53,19 +53,37 @@ class BatchedKem:
         self.ctx.encaps(self.pk, self.coins, self.ct, self.K, A=self.A)
         self.ctx.decaps(self.sk, self.ct, self.K2, A=self.A)
 
-    def capture(self):
+    def capture(self, timing: bool = False):
+        """Capture one step.  With timing, CUDA events around every kernel
+        are captured too; call timed_replay_done() after each completed
+        replay to add the kernels' durations to the context statistics."""
         s = torch.cuda.Stream(device=self.dev)
         s.wait_stream(torch.cuda.current_stream(self.dev))
+        if timing:  # creates the event pairs outside the capture
+            self.ctx.set_option(lwe.OPT_TIMING, 1)
         with torch.cuda.stream(s):
             self.step()
         torch.cuda.current_stream(self.dev).wait_stream(s)
         torch.cuda.synchronize(self.dev)
+        if timing:
+            self.ctx.set_option(lwe.OPT_TIMING, 0)
+            self.ctx.reset_stats()
         g = torch.cuda.CUDAGraph()
+        launches0 = self.ctx.launches()
+        if timing:
+            self.ctx.set_option(lwe.OPT_TIMING, 1)
         with torch.cuda.graph(g):
             self.step()
+        if timing:
+            self.ctx.set_option(lwe.OPT_TIMING, 0)
+            self.ctx.timing_mark()
         torch.cuda.synchronize(self.dev)
+        self.launches_per_step = self.ctx.launches() - launches0
         self.graph = g
         return g
+
+    def timed_replay_done(self):
+        self.ctx.timing_replay()
 
     def replay(self, coins: torch.Tensor | None = None):
         """One step from the captured graph; new coins are copied into the

@@ -155,6 +155,7 @@ struct lwe_ctx {
   bool timing = false;
   uint64_t launches = 0;
   std::vector<TimedLaunch> pending;
+  std::vector<TimedLaunch> replay;  // pairs captured into a CUDA graph
   std::vector<cudaEvent_t> free_events;
   uint64_t stat_launches[KID_COUNT] = {};
   double stat_ms[KID_COUNT] = {};
@@ -195,18 +196,24 @@ struct LaunchScope {
   int kid;
   cudaStream_t st;
   cudaEvent_t a = nullptr, b = nullptr;
+  unsigned flags = cudaEventRecordDefault;
   LaunchScope(lwe_ctx *c_, int kid_, cudaStream_t st_) : c(c_), kid(kid_), st(st_) {
     if (c && c->timing) {
       a = take_event(c);
       b = take_event(c);
-      if (a && b) cudaEventRecord(a, st);
+      // inside a stream capture the records must become event-record nodes
+      // of the graph (re-recorded by every replay), not capture dependencies
+      cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+      if (cudaStreamIsCapturing(st, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusActive)
+        flags = cudaEventRecordExternal;
+      if (a && b) cudaEventRecordWithFlags(a, st, flags);
     }
   }
   ~LaunchScope() {
     if (!c) return;
     c->launches++;
     if (a && b) {
-      cudaEventRecord(b, st);
+      cudaEventRecordWithFlags(b, st, flags);
       c->pending.push_back({kid, a, b});
     }
   }
@@ -605,6 +612,10 @@ int lwe_ctx_destroy(lwe_ctx *c) {
   cudaSetDevice(c->device);
   cudaDeviceSynchronize();
   for (auto &t : c->pending) {
+    cudaEventDestroy(t.a);
+    cudaEventDestroy(t.b);
+  }
+  for (auto &t : c->replay) {
     cudaEventDestroy(t.a);
     cudaEventDestroy(t.b);
   }
@@ -1032,6 +1043,29 @@ int lwe_ctx_kernel_stats(lwe_ctx *c, int kid, uint64_t *launches, double *total_
   harvest(c);
   if (launches) *launches = c->stat_launches[kid];
   if (total_ms) *total_ms = c->stat_ms[kid];
+  return LWE_OK;
+}
+
+int lwe_ctx_timing_mark(lwe_ctx *c) {
+  if (!c) return LWE_EINVAL;
+  for (auto &t : c->replay) {
+    cudaEventDestroy(t.a);
+    cudaEventDestroy(t.b);
+  }
+  c->replay.swap(c->pending);
+  c->pending.clear();
+  return LWE_OK;
+}
+
+int lwe_ctx_timing_replay(lwe_ctx *c) {
+  if (!c) return LWE_EINVAL;
+  for (auto &t : c->replay) {
+    CUDA_TRY(cudaEventSynchronize(t.b));
+    float ms = 0.f;
+    CUDA_TRY(cudaEventElapsedTime(&ms, t.a, t.b));
+    c->stat_launches[t.kid]++;
+    c->stat_ms[t.kid] += ms;
+  }
   return LWE_OK;
 }
 

@@ -78,6 +78,8 @@ def _load():
         "lwe_ctx_launches": (C.c_uint64, [vp]),
         "lwe_ctx_kernel_stats": (i32, [vp, i32, C.POINTER(C.c_uint64), C.POINTER(C.c_double)]),
         "lwe_ctx_reset_stats": (i32, [vp]),
+        "lwe_ctx_timing_mark": (i32, [vp]),
+        "lwe_ctx_timing_replay": (i32, [vp]),
         "lwe_kernel_name": (C.c_char_p, [i32]),
         "lwe_num_kernels": (i32, []),
     }
@@ -219,6 +221,12 @@ class Ctx:
 
     def reset_stats(self):
         _check(_lib.lwe_ctx_reset_stats(self._h), "lwe_ctx_reset_stats")
+
+    def timing_mark(self):
+        _check(_lib.lwe_ctx_timing_mark(self._h), "lwe_ctx_timing_mark")
+
+    def timing_replay(self):
+        _check(_lib.lwe_ctx_timing_replay(self._h), "lwe_ctx_timing_replay")
 
     # ---- buffers -------------------------------------------------------
     def empty_pk(self, count: int = 1) -> torch.Tensor:

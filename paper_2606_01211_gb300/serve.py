@@ -75,7 +75,7 @@ class KeyStore:
         self.dev = device
         self.params = {}
         self.pk, self.sk = {}, {}
-        self.hits = self.misses = 0
+        self.hits = self.misses = self.fills = 0
         self.arena, self.slot_of, self.lru, self.free, self.last_use = {}, {}, {}, {}, {}
         self.ready = {}
         share = cfg.a_budget_bytes // max(1, len(cfg.presets))
@@ -103,9 +103,10 @@ class KeyStore:
                 for k in range(slots):
                     self._fill(n, k, torch.cuda.current_stream(device))
         torch.cuda.synchronize(device)
-        self.hits = self.misses = 0
+        self.hits = self.misses = self.fills = 0
 
     def _fill(self, n, key, stream):
+        self.fills += 1
         if self.free[n]:
             s = self.free[n].pop()
         else:
@@ -334,6 +335,31 @@ class Engine:
             per_key[q.key] -= 1
         return group, self.cfg.plain
 
+    def warmup(self):
+        """Push one small batch of every kind (KeyGen; single-key and
+        multi-key Encaps / Decaps with stored and regenerated A; the tensor
+        path) through every slot, so that first-use costs of kernels and
+        streams stay out of the measured run.  Results go to scratch rows."""
+        for slot in self.slots:
+            for n in self.store.params:
+                P = self.pool[n]
+                reqs = [q for q in self.reqs if q.n == n][:1]
+                if not reqs:
+                    continue
+                base = reqs[0]
+                for op in range(3):
+                    for single in (True, False):
+                        for key in (0, self.cfg.keys_per_n - 1):
+                            q = Request(base.rid, op, n, key if op else -1, 0.0)
+                            k = min(self.cfg.max_batch, 2 if self.cfg.plain else
+                                    (self.HOT if single and op else 2))
+                            self._launch(slot, [q] * (1 if self.cfg.plain else k),
+                                         single or self.cfg.plain)
+                            slot.event.synchronize()
+                            slot.event, slot.reqs = None, []
+        torch.cuda.synchronize(self.dev)
+        self.store.hits = self.store.misses = 0
+
     def run(self) -> dict:
         cfg = self.cfg
         mb = 1 if cfg.plain else cfg.max_batch
@@ -342,6 +368,8 @@ class Engine:
         nxt, done = 0, 0
         N = len(self.reqs)
         batches = 0
+        host_launch = 0.0
+        fills0 = self.store.fills
         torch.cuda.synchronize(self.dev)
         t0 = time.perf_counter()
         while done < N:
@@ -365,7 +393,9 @@ class Engine:
                     continue
                 k = min(live, key=lambda k: fifos[k][0].t_arr)  # oldest waiting request
                 group, single = self._take(fifos[k], counts[k], mb)
+                tl = time.perf_counter()
                 self._launch(s, group, single)
+                host_launch += time.perf_counter() - tl
                 batches += 1
         makespan = max(q.t_done for q in self.reqs) - self.reqs[0].t_arr
         lat = np.array([q.t_done - q.t_arr for q in self.reqs])
@@ -374,7 +404,8 @@ class Engine:
                "p99_ms": float(np.percentile(lat, 99) * 1e3),
                "batches": batches, "mean_batch": N / max(batches, 1),
                "a_cache_hits": self.store.hits, "a_cache_misses": self.store.misses,
-               "plain": cfg.plain}
+               "a_cache_fills": self.store.fills - fills0, "host_launch_s": host_launch,
+               "makespan_s": makespan, "plain": cfg.plain}
         by_op = {}
         for i, name in enumerate(OPS):
             li = np.array([q.t_done - q.t_arr for q in self.reqs if q.op == i])
@@ -421,7 +452,9 @@ def main():
             cfg = ServeConfig(**{**base.__dict__, "rate": rate, "plain": plain,
                                  "requests": min(args.requests, max(2000, int(rate * 2)))
                                  if plain else args.requests})
-            st = Engine(cfg, store=store).run()
+            eng = Engine(cfg, store=store)
+            eng.warmup()
+            st = eng.run()
             print(json.dumps(st), flush=True)
 
 

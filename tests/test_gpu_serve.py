@@ -21,6 +21,7 @@ def served():
     cfg = serve.ServeConfig(presets=("P640", "P976"), keys_per_n=24, requests=700, rate=3e4,
                             max_batch=96, slots=3, a_budget_bytes=3 << 20, seed=5)
     eng = serve.Engine(cfg)
+    eng.warmup()
     stats = eng.run()
     torch.cuda.synchronize()
     return eng, stats
