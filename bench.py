@@ -161,11 +161,13 @@ def run_reference(args, rank, world):
 
 # ----------------------------------------------------------------- ours ---
 def keccak_perms(length: int, chunk: int = 1024) -> int:
-    """Keccak-f[1600] calls of the tree hash of `length` bytes (SHA3-256 of
-    each chunk, rate 136 bytes with at least one padding byte)."""
+    """Keccak-f[1600] calls of the tree hash of `length` bytes: SHA3-256 of
+    each chunk, then of the concatenated 32-byte chunk digests (rate 136
+    bytes with at least one padding byte)."""
     full, last = divmod(length, chunk)
     per = lambda L: L // 136 + 1
-    return full * per(chunk) + (per(last) if last else 0)
+    leaves = full + (1 if last else 0)
+    return full * per(chunk) + (per(last) if last else 0) + per(32 * leaves)
 
 
 # Derived peaks of the integer-bound kernels at the 2070 MHz maximum SM clock:
@@ -190,9 +192,10 @@ def algorithmic(p, count):
         # AES keystream bytes: S', E' (8n samples each) and E'' (64) per item,
         # 2 bytes per sample, Encaps + Decaps
         "k_noise": ("alu", 2 * (2.0 * (16 * n + 64) * count), "GB/s of AES keystream", 1e9),
-        # Keccak-f calls: H(pk) once, H(c) in Encaps and in Decaps
-        "k_tree_leaves": ("alu", float(keccak_perms(pk_bytes) + 2 * count * keccak_perms(ct_bytes)),
-                          "G Keccak-f/s", 1e9),
+        # Keccak-f calls: H(pk) once, H(c) in Encaps and in Decaps, and
+        # Encaps' K = H(K' || H(c))
+        "k_tree": ("alu", float(keccak_perms(pk_bytes) + 2 * count * keccak_perms(ct_bytes) + count),
+                   "G Keccak-f/s", 1e9),
     }
 
 

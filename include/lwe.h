@@ -244,7 +244,7 @@ int lwe_matmul_modq(lwe_ctx *ctx, int side, const uint16_t *A,
  * first call on a device looks up the scratch area's device address and
  * uploads the AES table there (one-time set-up), so make that first call
  * outside any stream capture.  The scratch holds about
- *   count * (16 n + 32 ceil((16 n + 128) / 1024) + 352) bytes
+ *   count * (16 n + 352) bytes
  * (each part rounded up to 256 bytes); a (params, count) that does not fit
  * returns LWE_ECAPACITY, invalid parameters or pointers LWE_EINVAL.
  * All calls on a device share the one area and it keeps the last call's

@@ -17,8 +17,8 @@ enum LweKernel {
   KID_MUL_SA,
   KID_MUL_SA_FUSED,
   KID_V_ENCODE,
-  KID_TREE_LEAVES,
-  KID_TREE_ROOT,
+  KID_TREE,
+  KID_FINAL_KEY,
   KID_DERIVE,
   KID_LIMBS,
   KID_GEMM,

@@ -130,6 +130,30 @@ LWE_DEV void sha3_256_global(const uint8_t *msg, uint32_t len, uint64_t s[25]) {
   keccak_f1600(s);
 }
 
+// SHA3-256 of `len` bytes at an 8-byte aligned address in shared or global
+// memory (generic loads; len a multiple of 8).
+LWE_DEV void sha3_256_mem(const uint8_t *msg, uint32_t len, uint64_t s[25]) {
+  sha3_init(s);
+  const uint64_t *p = reinterpret_cast<const uint64_t *>(msg);
+  uint32_t off = 0;
+  while (len - off >= SHA3_RATE) {
+#pragma unroll
+    for (int i = 0; i < SHA3_RATE / 8; i++) s[i] ^= p[off / 8 + i];
+    keccak_f1600(s);
+    off += SHA3_RATE;
+  }
+  const uint32_t rem = len - off;
+#pragma unroll
+  for (int i = 0; i < SHA3_RATE / 8; i++) {
+    const uint32_t base = 8 * i;
+    uint64_t lane = (base + 8 <= rem) ? p[off / 8 + i] : 0;
+    if (base == rem) lane ^= 0x06;
+    if (i == SHA3_RATE / 8 - 1) lane ^= 0x8000000000000000ull;
+    s[i] ^= lane;
+  }
+  keccak_f1600(s);
+}
+
 // SHA3-256 of a short message (< 136 bytes) given as little-endian lanes
 // already holding the message bytes (the rest zero); `len` in bytes.
 LWE_DEV void sha3_256_lanes(uint64_t lanes[SHA3_RATE / 8], uint32_t len,

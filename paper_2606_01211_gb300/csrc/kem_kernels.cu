@@ -11,9 +11,11 @@
 //                   stored A; with a compare epilogue for Alg. 5.
 //   k_mul_sa_fused  the same with A regenerated from its seed in-CTA.
 //   k_v_encode      V = S' B + E'', C = V + Enc(mu) of Alg. 2 (or compare).
-//   k_keygen_seeds, k_derive, k_tree_leaves, k_tree_root: the hashing of
+//   k_keygen_seeds, k_derive, k_tree, k_final_key: the hashing of
 //                   Alg. 4-5 (SHA3-256) and the Fujisaki-Okamoto selection.
 #include <cuda_bf16.h>
+
+#include <algorithm>
 
 #include "aes.cuh"
 #include "common.cuh"
@@ -582,49 +584,68 @@ __global__ void k_derive(DeriveArgs a) {
   for (int i = 0; i < 11; i++) dst[i] = make_uint4(rk[4 * i], rk[4 * i + 1], rk[4 * i + 2], rk[4 * i + 3]);
 }
 
-__global__ void __launch_bounds__(128) k_tree_leaves(TreeLeafArgs a) {
-  const uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const uint32_t m = (a.len + LWE_TREE_CHUNK - 1) / LWE_TREE_CHUNK;
-  if (t >= (uint64_t)a.count * m) return;
-  const uint32_t e = (uint32_t)(t / m), c = (uint32_t)(t % m);
-  const uint32_t off = c * LWE_TREE_CHUNK;
-  const uint32_t len = min((uint32_t)LWE_TREE_CHUNK, a.len - off);
+// Tree hash: tpi threads per message compute its 1024-byte-chunk digests
+// into shared memory; threads 0..ipc-1 (one per message, so the root phase
+// fills whole warps) then hash the digests -- the root -- and, for Encaps,
+// derive the key.  A message's digests sit at a stride of 4 m + 1 words so
+// the root threads' 64-bit reads fall in different banks.
+__global__ void __launch_bounds__(TREE_MAX_THREADS) k_tree(TreeArgs a) {
+  extern __shared__ uint64_t sleaf[];  // [ipc][4 m + 1]
+  const uint32_t words = 4 * a.m + 1;
+  const uint32_t e0 = blockIdx.x * a.ipc;
+  {
+    const uint32_t li = threadIdx.x / a.tpi, lt = threadIdx.x % a.tpi;
+    const uint32_t e = e0 + li;
+    if (li < a.ipc && e < a.count) {
+      const uint8_t *msg = a.msg_ptrs ? a.msg_ptrs[e] : a.msgs + (size_t)e * a.stride;
+      uint64_t *mine = sleaf + (size_t)li * words;
+      uint64_t s[25];
+      for (uint32_t c = lt; c < a.m; c += a.tpi) {
+        const uint32_t off = c * LWE_TREE_CHUNK;
+        sha3_256_global(msg + off, min((uint32_t)LWE_TREE_CHUNK, a.len - off), s);
+        mine[4 * c] = s[0];
+        mine[4 * c + 1] = s[1];
+        mine[4 * c + 2] = s[2];
+        mine[4 * c + 3] = s[3];
+      }
+    }
+  }
+  __syncthreads();
+  const uint32_t e = e0 + threadIdx.x;
+  if (threadIdx.x >= a.ipc || e >= a.count) return;
   uint64_t s[25];
-  const uint8_t *msg = a.msg_ptrs ? a.msg_ptrs[e] : a.msgs + (size_t)e * a.stride;
-  sha3_256_global(msg + off, len, s);
-  uint64_t *dst = reinterpret_cast<uint64_t *>(a.leaves + 32 * (size_t)t);
-  dst[0] = s[0];
-  dst[1] = s[1];
-  dst[2] = s[2];
-  dst[3] = s[3];
-}
-
-__global__ void __launch_bounds__(128) k_tree_root(TreeRootArgs a) {
-  const uint32_t e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= a.count) return;
-  uint64_t s[25];
-  sha3_256_global(a.leaves + (size_t)e * 32 * a.m, 32 * a.m, s);
+  sha3_256_mem(reinterpret_cast<const uint8_t *>(sleaf + (size_t)threadIdx.x * words), 32 * a.m, s);
   if (a.mode == TREE_DIGEST) {
     sha3_digest(s, a.out + (size_t)e * a.out_stride);
     if (a.out2) sha3_digest(s, a.out2 + (size_t)e * a.out2_stride);
     return;
   }
-  // K = H(x || H(c)), x = K' (Encaps, or Decaps when c' = c) or z
+  // Encaps (Alg. 4): K = H(K' || H(c))
   uint64_t lanes[SHA3_RATE / 8];
   lanes_zero(lanes);
   const uint64_t *kp = reinterpret_cast<const uint64_t *>(a.kprime + 32 * (size_t)e);
-  if (a.mode == TREE_ENC_KEY) {
-    for (int i = 0; i < 4; i++) lanes[i] = kp[i];
-  } else {
-    // all-ones when the re-encryption matched (flag == 0), else zero
-    const uint32_t f = a.flags[e];
-    const uint64_t keep = (uint64_t)0 - (uint64_t)(((f | (0u - f)) >> 31) ^ 1u);
-    const uint64_t *z = reinterpret_cast<const uint64_t *>(a.z_ptrs ? a.z_ptrs[e] + a.z_off : a.z);
-    for (int i = 0; i < 4; i++) lanes[i] = (kp[i] & keep) | (z[i] & ~keep);
-  }
+  for (int i = 0; i < 4; i++) lanes[i] = kp[i];
   for (int i = 0; i < 4; i++) lanes[4 + i] = s[i];
   sha3_256_lanes(lanes, 64, s);
   sha3_digest(s, a.out + 32 * (size_t)e);
+}
+
+__global__ void __launch_bounds__(128) k_final_key(FinalKeyArgs a) {
+  const uint32_t e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= a.count) return;
+  // all-ones when the re-encryption matched (flag == 0), else zero
+  const uint32_t f = a.flags[e];
+  const uint64_t keep = (uint64_t)0 - (uint64_t)(((f | (0u - f)) >> 31) ^ 1u);
+  const uint64_t *kp = reinterpret_cast<const uint64_t *>(a.kprime + 32 * (size_t)e);
+  const uint64_t *z = reinterpret_cast<const uint64_t *>(a.z_ptrs ? a.z_ptrs[e] + a.z_off : a.z);
+  const uint64_t *hc = reinterpret_cast<const uint64_t *>(a.hc + 32 * (size_t)e);
+  uint64_t lanes[SHA3_RATE / 8];
+  lanes_zero(lanes);
+  for (int i = 0; i < 4; i++) lanes[i] = (kp[i] & keep) | (z[i] & ~keep);
+  for (int i = 0; i < 4; i++) lanes[4 + i] = hc[i];
+  uint64_t s[25];
+  sha3_256_lanes(lanes, 64, s);
+  sha3_digest(s, a.K + 32 * (size_t)e);
 }
 
 // ---------------------------------------------------------------------------
@@ -793,14 +814,28 @@ void launch_derive(const DeriveArgs &a, cudaStream_t st) {
   k_derive<<<(a.count + 63) / 64, 64, 0, st>>>(a);
 }
 
-void launch_tree_leaves(const TreeLeafArgs &a, cudaStream_t st) {
-  const uint32_t m = (a.len + LWE_TREE_CHUNK - 1) / LWE_TREE_CHUNK;
-  const uint64_t total = (uint64_t)a.count * m;
-  k_tree_leaves<<<(unsigned)((total + 127) / 128), 128, 0, st>>>(a);
+// One CTA per SM where the batch allows (the leaf work is one wave: CTAs of
+// equal size spread it evenly), at most TREE_MAX_THREADS threads and 48 KB
+// of digests per CTA.
+void launch_tree(TreeArgs &a, int num_sms, cudaStream_t st) {
+  a.m = (a.len + LWE_TREE_CHUNK - 1) / LWE_TREE_CHUNK;
+  uint32_t t = 1;
+  while (t < a.m && t < 256) t <<= 1;
+  a.tpi = t;
+  const uint32_t words = 4 * a.m + 1;
+  uint32_t cap = TREE_MAX_THREADS / t;
+  cap = std::min<uint32_t>(cap, (48u * 1024u) / (8u * words));
+  cap = std::max<uint32_t>(cap, 1u);
+  const uint32_t sms = num_sms > 0 ? (uint32_t)num_sms : 1u;
+  a.ipc = std::min<uint32_t>(cap, (a.count + sms - 1) / sms);
+  if (a.ipc == 0) a.ipc = 1;
+  const uint32_t threads = (a.ipc * t + 31) / 32 * 32;
+  const size_t smem = (size_t)a.ipc * words * 8;
+  k_tree<<<(a.count + a.ipc - 1) / a.ipc, threads, smem, st>>>(a);
 }
 
-void launch_tree_root(const TreeRootArgs &a, cudaStream_t st) {
-  k_tree_root<<<(a.count + 127) / 128, 128, 0, st>>>(a);
+void launch_final_key(const FinalKeyArgs &a, cudaStream_t st) {
+  k_final_key<<<(a.count + 127) / 128, 128, 0, st>>>(a);
 }
 
 void launch_gemm_limbs(const GemmLimbArgs &a, int num_sms, cudaStream_t st) {

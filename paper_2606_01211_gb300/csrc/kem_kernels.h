@@ -117,30 +117,40 @@ struct DeriveArgs {
   uint32_t count, mu_bytes;
 };
 
-struct TreeLeafArgs {
-  const uint8_t *msgs;   // item e at msgs + e * stride
-  const uint8_t *const *msg_ptrs;  // per-item messages (then msgs unused)
+enum { TREE_DIGEST = 0, TREE_ENC_KEY = 1 };
+#define TREE_MAX_THREADS 512
+
+// Tree hash of `count` messages of `len` bytes (item e at msgs + e*stride,
+// or msg_ptrs[e]): leaves and root in one kernel, the leaf digests kept in
+// shared memory.  DIGEST writes H to out + e*out_stride (and out2);
+// ENC_KEY writes K = H(K'_e || H) to out + 32 e.
+struct TreeArgs {
+  const uint8_t *msgs;
+  const uint8_t *const *msg_ptrs;
   uint64_t stride;
-  uint32_t len;          // bytes per item
-  uint32_t count;
-  uint8_t *leaves;       // [count][m][32]
-};
-
-enum { TREE_DIGEST = 0, TREE_ENC_KEY = 1, TREE_DEC_KEY = 2 };
-
-struct TreeRootArgs {
-  const uint8_t *leaves;
-  uint32_t m, count;
-  int mode, pad;
-  uint8_t *out;          // DIGEST: out + e*out_stride; keys: out + 32 e
+  uint32_t len, count;
+  uint32_t m;            // leaves per message
+  uint32_t tpi;          // threads per message (power of two <= 256)
+  uint32_t ipc;          // messages per CTA
+  int mode;
+  uint8_t *out;
   uint64_t out_stride;
   uint8_t *out2;
   uint64_t out2_stride;
   const uint8_t *kprime; // 32 per item
-  const uint8_t *z;      // Decaps: 32 bytes
-  const uint8_t *const *z_ptrs;  // per-item z at z_ptrs[e] + z_off
+};
+
+// Decaps' key selection (Alg. 5): K = H(K' || H(c)) when the re-encryption
+// matched (flag 0), else H(z || H(c)); branch-free.
+struct FinalKeyArgs {
+  const uint8_t *kprime; // 32 per item
+  const uint8_t *hc;     // 32 per item
+  const uint8_t *z;      // one key's z, or
+  const uint8_t *const *z_ptrs;  // per item at z_ptrs[e] + z_off
   uint64_t z_off;
-  const uint32_t *flags; // Decaps: mismatch flag per item
+  const uint32_t *flags;
+  uint8_t *K;
+  uint32_t count, pad;
 };
 
 cudaError_t lwe_upload_aes_table(const uint32_t T0[256]);
@@ -154,5 +164,5 @@ void launch_mul_sa(const MulSaArgs &a, uint32_t items, bool fused, bool cmp, cud
 void launch_v_encode(const VEncArgs &a, uint32_t count, bool cmp, cudaStream_t st);
 void launch_keygen_seeds(const KeygenSeedArgs &a, cudaStream_t st);
 void launch_derive(const DeriveArgs &a, cudaStream_t st);
-void launch_tree_leaves(const TreeLeafArgs &a, cudaStream_t st);
-void launch_tree_root(const TreeRootArgs &a, cudaStream_t st);
+void launch_tree(TreeArgs &a, int num_sms, cudaStream_t st);
+void launch_final_key(const FinalKeyArgs &a, cudaStream_t st);

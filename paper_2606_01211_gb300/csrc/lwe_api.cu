@@ -132,7 +132,7 @@ uint32_t mu_bytes(const lwe_params &p) { return 8 * p.B; }
 
 const char *kKernelNames[KID_COUNT] = {
     "k_expand_A", "k_noise",        "k_keygen_seeds", "k_mul_as",     "k_decrypt",
-    "k_mul_sa",   "k_mul_sa_fused", "k_v_encode",     "k_tree_leaves", "k_tree_root",
+    "k_mul_sa",   "k_mul_sa_fused", "k_v_encode",     "k_tree",        "k_final_key",
     "k_derive",   "k_limbs",        "k_gemm_tc"};
 
 }  // namespace
@@ -162,7 +162,8 @@ struct lwe_ctx {
   // workspace
   uint8_t *ws = nullptr;
   size_t ws_bytes = 0;
-  uint8_t *seeds = nullptr, *mu = nullptr, *kp = nullptr, *pkh = nullptr, *leaves = nullptr;
+  uint8_t *seeds = nullptr, *mu = nullptr, *kp = nullptr, *pkh = nullptr;
+  uint8_t *hc = nullptr;       // H(c) per item (Decaps)
   uint32_t *flags = nullptr, *dev_err = nullptr;
   uint32_t *rk = nullptr;     // 44 AES round-key words per item
   uint8_t *pkhs = nullptr;    // H(pk) per item (multi-key Encaps)
@@ -172,7 +173,6 @@ struct lwe_ctx {
   uint16_t *partial = nullptr; // K-split running sums, [8 max_batch][n + 8]
   uint32_t kchunk = 0;         // exact K per GEMM pass
   bool has_tensor = false;
-  uint32_t tree_m = 0;  // leaves per item
   // side stream for work independent of the re-encryption (Decaps' H(c))
   cudaStream_t side = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
@@ -408,46 +408,46 @@ int run_encrypt(lwe_ctx *c, const uint8_t *pk, const uint16_t *A, uint32_t count
   return check_launch();
 }
 
-void tree_leaves(lwe_ctx *c, const uint8_t *msgs, uint64_t stride, uint32_t len, uint32_t count,
-                 cudaStream_t st, const uint8_t *const *msg_ptrs = nullptr) {
-  TreeLeafArgs la;
-  memset(&la, 0, sizeof la);
-  la.msgs = msgs;
-  la.msg_ptrs = msg_ptrs;
-  la.stride = stride;
-  la.len = len;
-  la.count = count;
-  la.leaves = c->leaves;
-  LAUNCH(c, KID_TREE_LEAVES, st, launch_tree_leaves(la, st));
-}
-
-void tree_root(lwe_ctx *c, uint32_t len, uint32_t count, int mode, uint8_t *out,
-               uint64_t out_stride, uint8_t *out2, uint64_t out2_stride, const uint8_t *z,
-               cudaStream_t st, const uint8_t *const *z_ptrs = nullptr, uint64_t z_off = 0) {
-  TreeRootArgs ra;
-  memset(&ra, 0, sizeof ra);
-  ra.leaves = c->leaves;
-  ra.m = (len + LWE_TREE_CHUNK - 1) / LWE_TREE_CHUNK;
-  ra.count = count;
-  ra.mode = mode;
-  ra.out = out;
-  ra.out_stride = out_stride;
-  ra.out2 = out2;
-  ra.out2_stride = out2_stride;
-  ra.kprime = c->kp;
-  ra.z = z;
-  ra.z_ptrs = z_ptrs;
-  ra.z_off = z_off;
-  ra.flags = c->flags;
-  LAUNCH(c, KID_TREE_ROOT, st, launch_tree_root(ra, st));
+void tree_hash(lwe_ctx *c, const uint8_t *msgs, uint64_t stride, uint32_t len, uint32_t count,
+               int mode, uint8_t *out, uint64_t out_stride, uint8_t *out2, uint64_t out2_stride,
+               cudaStream_t st, const uint8_t *const *msg_ptrs = nullptr) {
+  TreeArgs ta;
+  memset(&ta, 0, sizeof ta);
+  ta.msgs = msgs;
+  ta.msg_ptrs = msg_ptrs;
+  ta.stride = stride;
+  ta.len = len;
+  ta.count = count;
+  ta.mode = mode;
+  ta.out = out;
+  ta.out_stride = out_stride;
+  ta.out2 = out2;
+  ta.out2_stride = out2_stride;
+  ta.kprime = c->kp;
+  LAUNCH(c, KID_TREE, st, launch_tree(ta, c->num_sms, st));
 }
 
 int hash_tree(lwe_ctx *c, const uint8_t *msgs, uint64_t stride, uint32_t len, uint32_t count,
               int mode, uint8_t *out, uint64_t out_stride, uint8_t *out2, uint64_t out2_stride,
-              const uint8_t *z, cudaStream_t st) {
-  tree_leaves(c, msgs, stride, len, count, st);
-  tree_root(c, len, count, mode, out, out_stride, out2, out2_stride, z, st);
+              cudaStream_t st) {
+  tree_hash(c, msgs, stride, len, count, mode, out, out_stride, out2, out2_stride, st);
   return check_launch();
+}
+
+// Decaps' final key from K', H(c) and the re-encryption flags
+void final_key(lwe_ctx *c, const uint8_t *z, const uint8_t *const *z_ptrs, uint64_t z_off,
+               uint32_t count, uint8_t *K, cudaStream_t st) {
+  FinalKeyArgs fa;
+  memset(&fa, 0, sizeof fa);
+  fa.kprime = c->kp;
+  fa.hc = c->hc;
+  fa.z = z;
+  fa.z_ptrs = z_ptrs;
+  fa.z_off = z_off;
+  fa.flags = c->flags;
+  fa.K = K;
+  fa.count = count;
+  LAUNCH(c, KID_FINAL_KEY, st, launch_final_key(fa, st));
 }
 
 int set_device_of(lwe_ctx *c) {
@@ -538,7 +538,6 @@ int lwe_ctx_create(const lwe_params *p, uint32_t max_batch, int device, lwe_ctx 
 
   const size_t n = p->n;
   const size_t Bm = max_batch;
-  c->tree_m = (uint32_t)((std::max(ct_bytes(*p), pk_bytes(*p)) + LWE_TREE_CHUNK - 1) / LWE_TREE_CHUNK);
   // tensor path workspaces (bf16 S', limbs, K-split sums) are sized for
   // batched use: always for n <= 8192, and for larger n when max_batch >= 64
   c->has_tensor = lwe_gemm_supported(p->n, p->logq, p->clip) && (p->n <= 8192 || max_batch >= 64);
@@ -553,7 +552,7 @@ int lwe_ctx_create(const lwe_params *p, uint32_t max_batch, int device, lwe_ctx 
   const size_t o_seeds = carve(32 * Bm), o_mu = carve(32 * Bm), o_kp = carve(32 * Bm);
   const size_t o_flags = carve(4 * Bm), o_err = carve(16), o_pkh = carve(32);
   const size_t o_rk = carve(176 * Bm), o_pkhs = carve(32 * Bm);
-  const size_t o_leaves = carve(32 * (size_t)c->tree_m * Bm);
+  const size_t o_hc = carve(32 * Bm);
   const size_t o_sp8 = carve(8 * n * Bm), o_ep8 = carve(8 * n * Bm), o_epp = carve(64 * Bm);
   size_t o_spbf = 0, o_limbs = 0;
   size_t o_partial = 0;
@@ -578,7 +577,7 @@ int lwe_ctx_create(const lwe_params *p, uint32_t max_batch, int device, lwe_ctx 
   c->rk = reinterpret_cast<uint32_t *>(c->ws + o_rk);
   c->pkhs = c->ws + o_pkhs;
   c->pkh = c->ws + o_pkh;
-  c->leaves = c->ws + o_leaves;
+  c->hc = c->ws + o_hc;
   c->sp8 = reinterpret_cast<int8_t *>(c->ws + o_sp8);
   c->ep8 = reinterpret_cast<int8_t *>(c->ws + o_ep8);
   c->epp = reinterpret_cast<int8_t *>(c->ws + o_epp);
@@ -711,7 +710,7 @@ int lwe_keygen(lwe_ctx *c, const uint8_t *seeds, uint32_t count, uint8_t *pk, ui
 
   // H(pk) into sk
   return hash_tree(c, pk, pkb, (uint32_t)pkb, count, TREE_DIGEST, sk + 8 * (size_t)n + 32, skb,
-                   nullptr, 0, nullptr, st);
+                   nullptr, 0, st);
 }
 
 int lwe_encaps(lwe_ctx *c, const uint8_t *pk, const uint16_t *A, const uint8_t *coins,
@@ -728,13 +727,13 @@ int lwe_encaps(lwe_ctx *c, const uint8_t *pk, const uint16_t *A, const uint8_t *
   const lwe_params &p = c->p;
   const size_t pkb = pk_bytes(p), ctb = ct_bytes(p);
 
-  rc = hash_tree(c, pk, pkb, (uint32_t)pkb, 1, TREE_DIGEST, c->pkh, 32, nullptr, 0, nullptr, st);
+  rc = hash_tree(c, pk, pkb, (uint32_t)pkb, 1, TREE_DIGEST, c->pkh, 32, nullptr, 0, st);
   if (rc) return rc;
   DeriveArgs da = derive_args(c, coins, c->pkh, count);
   LAUNCH(c, KID_DERIVE, st, launch_derive(da, st));
   rc = run_encrypt(c, pk, A, count, ct, false, st);
   if (rc) return rc;
-  return hash_tree(c, ct, ctb, (uint32_t)ctb, count, TREE_ENC_KEY, K, 32, nullptr, 0, nullptr, st);
+  return hash_tree(c, ct, ctb, (uint32_t)ctb, count, TREE_ENC_KEY, K, 32, nullptr, 0, st);
 }
 
 int lwe_decaps(lwe_ctx *c, const uint8_t *sk, const uint16_t *A, const uint8_t *ct,
@@ -756,11 +755,11 @@ int lwe_decaps(lwe_ctx *c, const uint8_t *sk, const uint16_t *A, const uint8_t *
   const uint8_t *pk = pkh + 32;
 
   CUDA_TRY(cudaMemsetAsync(c->flags, 0, 4 * (size_t)count, st));
-  // H(c) does not depend on the re-encryption: its leaves run on the side
-  // stream, overlapping the tensor-bound product, and join before the keys
+  // H(c) does not depend on the re-encryption: it runs on the side stream,
+  // overlapping the re-encryption, and joins before the key selection
   CUDA_TRY(cudaEventRecord(c->ev_fork, st));
   CUDA_TRY(cudaStreamWaitEvent(c->side, c->ev_fork, 0));
-  tree_leaves(c, ct, ctb, (uint32_t)ctb, count, c->side);
+  tree_hash(c, ct, ctb, (uint32_t)ctb, count, TREE_DIGEST, c->hc, 32, nullptr, 0, c->side);
   CUDA_TRY(cudaEventRecord(c->ev_join, c->side));
   DecryptArgs dca = decrypt_args(c, ct, reinterpret_cast<const int8_t *>(sk), nullptr);
   LAUNCH(c, KID_DECRYPT, st, launch_decrypt(dca, count, st));
@@ -769,7 +768,7 @@ int lwe_decaps(lwe_ctx *c, const uint8_t *sk, const uint16_t *A, const uint8_t *
   rc = run_encrypt(c, pk, A, count, const_cast<uint8_t *>(ct), true, st);
   if (rc) return rc;
   CUDA_TRY(cudaStreamWaitEvent(st, c->ev_join, 0));
-  tree_root(c, (uint32_t)ctb, count, TREE_DEC_KEY, K, 32, nullptr, 0, z, st);
+  final_key(c, z, nullptr, 0, count, K, st);
   return check_launch();
 }
 
@@ -792,8 +791,8 @@ int lwe_encaps_multi(lwe_ctx *c, const uint8_t *const *pk_ptrs, const uint8_t *c
   if (pkh_ptrs) {
     da.pkh_ptrs = pkh_ptrs;
   } else {  // H(pk) of every item's key
-    tree_leaves(c, nullptr, 0, (uint32_t)pkb, count, st, pk_ptrs);
-    tree_root(c, (uint32_t)pkb, count, TREE_DIGEST, c->pkhs, 32, nullptr, 0, nullptr, st);
+    tree_hash(c, nullptr, 0, (uint32_t)pkb, count, TREE_DIGEST, c->pkhs, 32, nullptr, 0, st,
+              pk_ptrs);
     da.pkh = c->pkhs;
     da.pkh_stride = 32;
   }
@@ -804,7 +803,7 @@ int lwe_encaps_multi(lwe_ctx *c, const uint8_t *const *pk_ptrs, const uint8_t *c
   ik.A_ptrs = A_ptrs;
   rc = run_encrypt(c, nullptr, nullptr, count, ct, false, st, &ik);
   if (rc) return rc;
-  return hash_tree(c, ct, ctb, (uint32_t)ctb, count, TREE_ENC_KEY, K, 32, nullptr, 0, nullptr, st);
+  return hash_tree(c, ct, ctb, (uint32_t)ctb, count, TREE_ENC_KEY, K, 32, nullptr, 0, st);
 }
 
 int lwe_decaps_multi(lwe_ctx *c, const uint8_t *const *sk_ptrs, const uint16_t *const *A_ptrs,
@@ -824,7 +823,7 @@ int lwe_decaps_multi(lwe_ctx *c, const uint8_t *const *sk_ptrs, const uint16_t *
   CUDA_TRY(cudaMemsetAsync(c->flags, 0, 4 * (size_t)count, st));
   CUDA_TRY(cudaEventRecord(c->ev_fork, st));
   CUDA_TRY(cudaStreamWaitEvent(c->side, c->ev_fork, 0));
-  tree_leaves(c, ct, ctb, (uint32_t)ctb, count, c->side);
+  tree_hash(c, ct, ctb, (uint32_t)ctb, count, TREE_DIGEST, c->hc, 32, nullptr, 0, c->side);
   CUDA_TRY(cudaEventRecord(c->ev_join, c->side));
   DecryptArgs dca = decrypt_args(c, ct, nullptr, sk_ptrs);
   LAUNCH(c, KID_DECRYPT, st, launch_decrypt(dca, count, st));
@@ -839,8 +838,7 @@ int lwe_decaps_multi(lwe_ctx *c, const uint8_t *const *sk_ptrs, const uint16_t *
   rc = run_encrypt(c, nullptr, nullptr, count, const_cast<uint8_t *>(ct), true, st, &ik);
   if (rc) return rc;
   CUDA_TRY(cudaStreamWaitEvent(st, c->ev_join, 0));
-  tree_root(c, (uint32_t)ctb, count, TREE_DEC_KEY, K, 32, nullptr, 0, nullptr, st, sk_ptrs,
-            8ull * n);
+  final_key(c, nullptr, sk_ptrs, 8ull * n, count, K, st);
   return check_launch();
 }
 
@@ -946,8 +944,6 @@ int lwe_encaps_noalloc(const lwe_params *p, const uint8_t *pk, const uint16_t *A
       !aligned16(K) || (A && !aligned16(A)))
     return LWE_EINVAL;
   const size_t n = p->n, Bm = count;
-  const uint32_t tree_m =
-      (uint32_t)((std::max(ct_bytes(*p), pk_bytes(*p)) + LWE_TREE_CHUNK - 1) / LWE_TREE_CHUNK);
   size_t off = 0;
   auto carve = [&](size_t bytes) {
     size_t o = off;
@@ -956,7 +952,6 @@ int lwe_encaps_noalloc(const lwe_params *p, const uint8_t *pk, const uint16_t *A
   };
   const size_t o_seeds = carve(32 * Bm), o_mu = carve(32 * Bm), o_kp = carve(32 * Bm);
   const size_t o_flags = carve(4 * Bm), o_pkh = carve(32), o_rk = carve(176 * Bm);
-  const size_t o_leaves = carve(32 * (size_t)tree_m * Bm);
   const size_t o_sp8 = carve(8 * n * Bm), o_ep8 = carve(8 * n * Bm), o_epp = carve(64 * Bm);
   if (off > LWE_NOALLOC_SCRATCH_BYTES) return LWE_ECAPACITY;
 
@@ -976,27 +971,25 @@ int lwe_encaps_noalloc(const lwe_params *p, const uint8_t *pk, const uint16_t *A
   c.max_batch = count;
   c.path = LWE_PATH_SKINNY;
   c.has_tensor = false;
-  c.tree_m = tree_m;
   c.seeds = ws + o_seeds;
   c.mu = ws + o_mu;
   c.kp = ws + o_kp;
   c.flags = reinterpret_cast<uint32_t *>(ws + o_flags);
   c.rk = reinterpret_cast<uint32_t *>(ws + o_rk);
   c.pkh = ws + o_pkh;
-  c.leaves = ws + o_leaves;
   c.sp8 = reinterpret_cast<int8_t *>(ws + o_sp8);
   c.ep8 = reinterpret_cast<int8_t *>(ws + o_ep8);
   c.epp = reinterpret_cast<int8_t *>(ws + o_epp);
 
   cudaStream_t st = (cudaStream_t)stream;
   const size_t pkb = pk_bytes(*p), ctb = ct_bytes(*p);
-  rc = hash_tree(&c, pk, pkb, (uint32_t)pkb, 1, TREE_DIGEST, c.pkh, 32, nullptr, 0, nullptr, st);
+  rc = hash_tree(&c, pk, pkb, (uint32_t)pkb, 1, TREE_DIGEST, c.pkh, 32, nullptr, 0, st);
   if (rc) return rc;
   DeriveArgs da = derive_args(&c, coins, c.pkh, count);
   LAUNCH(&c, KID_DERIVE, st, launch_derive(da, st));
   rc = run_encrypt(&c, pk, A, count, ct, false, st);
   if (rc) return rc;
-  return hash_tree(&c, ct, ctb, (uint32_t)ctb, count, TREE_ENC_KEY, K, 32, nullptr, 0, nullptr, st);
+  return hash_tree(&c, ct, ctb, (uint32_t)ctb, count, TREE_ENC_KEY, K, 32, nullptr, 0, st);
 }
 
 int lwe_selftest_bounded_wait(lwe_ctx *c, uint32_t limit_us, void *stream) {
