@@ -229,7 +229,8 @@ def run_ours(args, rank, world, local_rank):
 
     # the step: 4096 Encaps + 4096 Decaps against one key (direct launches,
     # CUDA events around every kernel on its launch stream)
-    kem = batch.BatchedKem(PRESET, COUNT, seed=key_seed, gemm_bn=tuned["gemm_bn"])
+    kem = batch.BatchedKem(PRESET, COUNT, seed=key_seed, gemm_bn=tuned["gemm_bn"],
+                           gemm_pair=tuned["gemm_pair"])
     for i in range(args.warmup):
         kem.coins.copy_(cs_all[i])
         kem.step()
@@ -387,7 +388,8 @@ def run_ours(args, rank, world, local_rank):
         "plain_path_value": plain,
         "batched_vs_plain": (value / world / plain) if plain else None,
         "kernels_ms_per_step": {k: v[1] / args.steps for k, v in stats.items()},
-        "autotune": {"gemm_bn": tuned["gemm_bn"], "tensor_min": tuned["tensor_min"]},
+        "autotune": {"gemm_pair": tuned["gemm_pair"], "gemm_bn": tuned["gemm_bn"],
+                     "tensor_min": tuned["tensor_min"]},
         "served": served,
         "latency_p640_us": latency,
         "as_gbs": as_sweep,

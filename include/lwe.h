@@ -133,9 +133,13 @@ enum {
   LWE_OPT_PATH = 0,          /* one of LWE_PATH_*                             */
   LWE_OPT_TENSOR_MIN = 1,    /* AUTO threshold (items per call), default 64   */
   LWE_OPT_TIMING = 2,        /* 1: time every launch with CUDA events          */
-  LWE_OPT_GEMM_BN = 3,       /* GEMM output-column tile: 64 or 128 (default)  */
-  LWE_OPT_GEMM_KCHUNK = 4    /* K per tensor-core pass: a multiple of 64 up to
+  LWE_OPT_GEMM_BN = 3,       /* single-CTA GEMM column tile: 64 or 128 (def.) */
+  LWE_OPT_GEMM_KCHUNK = 4,   /* K per tensor-core pass: a multiple of 64 up to
                                 the exact bound (2^24-1)/(128 c); 0 = bound   */
+  LWE_OPT_GEMM_PAIR = 5      /* 1 (default): the GEMM runs on CTA pairs (two
+                                SMs share a 256 x 128 tile, tcgen05
+                                cta_group::2; LWE_OPT_GEMM_BN is then
+                                ignored); 0: one CTA per 128 x BN tile        */
 };
 int lwe_ctx_set_option(lwe_ctx *ctx, int option, int64_t value);
 

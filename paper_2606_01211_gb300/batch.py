@@ -9,9 +9,10 @@ kernel launches.  Batching many encapsulations against one key is what
 turns S' A into one tensor-core contraction (the paper batches the 256
 per-bit encryptions of one Encaps into one launch, Sec. 3.2).
 
-autotune() times the candidate GEMM output-column tiles (64 / 128) and the
-items-per-call threshold above which the tensor path beats the CUDA-core
-path, for a given (n, batch), and caches the choice in a JSON file.
+autotune() times the candidate GEMM kernels (CTA pairs on 256 x 128 tiles,
+or one CTA on 128 x 64 / 128 x 128 tiles) and the items-per-call threshold
+above which the tensor path beats the CUDA-core path, for a given (n,
+batch), and caches the choice in a JSON file.
 """
 from __future__ import annotations
 
@@ -29,7 +30,8 @@ CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_autotune.json
 
 class BatchedKem:
     def __init__(self, name: str = "P976", count: int = 4096, seed: int = 1, device=None,
-                 path: int = lwe.PATH_TENSOR, gemm_bn: int | None = None):
+                 path: int = lwe.PATH_TENSOR, gemm_bn: int | None = None,
+                 gemm_pair: int | None = None):
         self.dev = torch.device("cuda", torch.cuda.current_device() if device is None else device)
         self.params = p = lwe.Params(**PRESETS[name])
         self.count = count
@@ -37,6 +39,8 @@ class BatchedKem:
         self.ctx.set_path(path)
         if gemm_bn:
             self.ctx.set_option(lwe.OPT_GEMM_BN, gemm_bn)
+        if gemm_pair is not None:
+            self.ctx.set_option(lwe.OPT_GEMM_PAIR, gemm_pair)
         self.pk, self.sk = self.ctx.empty_pk(1), self.ctx.empty_sk(1)
         self.A = torch.empty((p.n, p.n), dtype=torch.int16, device=self.dev)
         self.ctx.keygen(torch.from_numpy(master_seeds(1, seed=seed)).to(self.dev), self.pk, self.sk,
@@ -117,21 +121,26 @@ def autotune(name: str = "P976", count: int = 4096, cache: str | None = CACHE,
              refresh: bool = False) -> dict:
     """Pick the GEMM tile width and the tensor-path threshold for (n, batch).
 
-    Returns {"gemm_bn": 64|128, "tensor_min": items, "ms": {...}} and stores
-    it under the key "<name>/<count>" in the cache file."""
+    Returns {"gemm_pair": 0|1, "gemm_bn": 64|128, "tensor_min": items,
+    "ms": {...}} and stores it under the key "<name>/<count>" in the cache
+    file."""
     key = "%s/%d" % (name, count)
     table = {}
     if cache and os.path.exists(cache):
         with open(cache) as f:
             table = json.load(f)
-        if key in table and not refresh:
+        if key in table and not refresh and "gemm_pair" in table[key]:
             return table[key]
     kem = BatchedKem(name, count, path=lwe.PATH_TENSOR)
     ms = {}
-    for bn in (64, 128):
+    cands = {"tensor_pair": (1, 128), "tensor_bn128": (0, 128), "tensor_bn64": (0, 64)}
+    for label, (pair, bn) in cands.items():
+        kem.ctx.set_option(lwe.OPT_GEMM_PAIR, pair)
         kem.ctx.set_option(lwe.OPT_GEMM_BN, bn)
-        ms["tensor_bn%d" % bn] = _time(kem.step)
-    best_bn = 64 if ms["tensor_bn64"] < ms["tensor_bn128"] else 128
+        ms[label] = _time(kem.step)
+    best = min(cands, key=lambda k: ms[k])
+    best_pair, best_bn = cands[best]
+    kem.ctx.set_option(lwe.OPT_GEMM_PAIR, best_pair)
     kem.ctx.set_option(lwe.OPT_GEMM_BN, best_bn)
     # crossover: smallest batch at which the tensor path is faster per item
     tensor_min = count + 1
@@ -148,7 +157,7 @@ def autotune(name: str = "P976", count: int = 4096, cache: str | None = CACHE,
             tensor_min = b
             break
     kem.close()
-    res = {"gemm_bn": best_bn, "tensor_min": tensor_min, "ms": ms}
+    res = {"gemm_pair": best_pair, "gemm_bn": best_bn, "tensor_min": tensor_min, "ms": ms}
     if cache:
         table[key] = res
         tmp = cache + ".tmp"

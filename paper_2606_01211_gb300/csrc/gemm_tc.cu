@@ -20,6 +20,17 @@
 // C columns) and store -- or compare against a received ciphertext (Decaps).
 // Every mbarrier wait is bounded; a wait that runs out raises the context's
 // device error word and the CTA leaves cleanly.
+//
+// k_gemm_sa2 is the same product on CTA pairs (a cluster of two CTAs on one
+// TPC, tcgen05 cta_group::2): one tile is 256 rows x 128 columns; each CTA
+// loads its own 128 rows of S' and ONE limb tile (rank 0 the lo limbs, rank
+// 1 the hi limbs), and the leader's MMA (M = 256, N = 256) reads the B
+// operand from both CTAs' shared memory.  Per SM and k-block that is 32 KB
+// of operands instead of 48 KB for the same 128 x 256 products.  Both
+// CTAs' copies complete on the leader's full barrier; the leader's commits
+// are multicast to both CTAs' empty / accumulator-full barriers; each
+// epilogue warp of either CTA signals the leader's accumulator-empty
+// barrier.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
@@ -33,6 +44,7 @@ constexpr int BK = 64;  // bf16 elements = 128 bytes = one swizzle atom row
 constexpr int STAGES = 4;
 constexpr int NTHREADS = 192;
 constexpr uint64_t kTimeoutNs = 1000000000ull;  // 1 s per wait
+constexpr uint64_t kDrainNs = 2000000ull;       // 2 ms for copies in flight after an abort
 
 template <int BN>
 struct Cfg {
@@ -47,6 +59,22 @@ struct Cfg {
   static constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) |
                                     ((uint32_t)(2 * BN / 8) << 17) |
                                     ((uint32_t)(BM / 16) << 24);
+};
+
+// CTA-pair variant: per CTA 128 rows of S' and one limb tile of BN2
+// columns per stage; MMA M = 256 (the pair), N = 2 BN2 (lo | hi).
+constexpr int BN2 = 128;
+constexpr int STAGES2 = 6;
+struct Cfg2 {
+  static constexpr int A_BYTES = BM * BK * 2;        // 16 KB
+  static constexpr int B_BYTES = BN2 * BK * 2;       // 16 KB: one limb
+  static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
+  static constexpr int TMEM_COLS = 2 * (2 * BN2);    // two accumulators
+  static constexpr int BAR_OFF = STAGES2 * STAGE_BYTES;
+  static constexpr int SMEM = BAR_OFF + 256 + 1024;
+  static constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) |
+                                    ((uint32_t)(2 * BN2 / 8) << 17) |
+                                    ((uint32_t)(2 * BM / 16) << 24);
 };
 
 LWE_DEV uint32_t smem_u32(const void *p) {
@@ -100,6 +128,14 @@ LWE_DEV bool wait_bar(uint32_t bar, uint32_t parity, volatile uint32_t *abort_fl
   }
 }
 
+// The same decision for every lane of a warp (the epilogue's TMEM loads and
+// shuffles are warp-collective, so no lane may leave the loop alone).
+LWE_DEV bool wait_bar_warp(uint32_t bar, uint32_t parity, volatile uint32_t *abort_flag,
+                           uint32_t *dev_err) {
+  const bool ok = wait_bar(bar, parity, abort_flag, dev_err);
+  return __all_sync(0xffffffffu, ok);
+}
+
 LWE_DEV void tma_load_2d(uint32_t dst, const CUtensorMap *map, int c0, int c1, uint32_t bar) {
   asm volatile(
       "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
@@ -115,6 +151,48 @@ LWE_DEV void tma_load_3d(uint32_t dst, const CUtensorMap *map, int c0, int c1, i
       " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(dst),
       "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(bar)
       : "memory");
+}
+
+// The same copies for a CTA pair: the mbarrier may live in the peer CTA
+// (a shared::cluster address).
+LWE_DEV void tma_load_2d_pair(uint32_t dst, const CUtensorMap *map, int c0, int c1, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.cta_group::2.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(bar)
+      : "memory");
+}
+
+LWE_DEV void tma_load_3d_pair(uint32_t dst, const CUtensorMap *map, int c0, int c1, int c2,
+                              uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.cta_group::2.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(bar)
+      : "memory");
+}
+
+LWE_DEV uint32_t cluster_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+
+// shared::cluster address of this CTA's shared variable `a` in CTA `rank`
+LWE_DEV uint32_t peer_addr(uint32_t a, uint32_t rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
+  return r;
+}
+
+LWE_DEV void mbar_arrive_cluster(uint32_t cluster_addr) {
+  asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(cluster_addr)
+               : "memory");
+}
+
+LWE_DEV void cluster_sync() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::
+                   : "memory");
 }
 
 LWE_DEV void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
@@ -135,6 +213,26 @@ LWE_DEV void mma_bf16(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t i
       "setp.ne.b32 p, %4, 0;\n\t"
       "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(dtmem),
       "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+LWE_DEV void mma_bf16_pair(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                           uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(dtmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+// arrive on the barrier at this offset in every CTA of `mask` once the
+// pair's earlier MMAs have completed
+LWE_DEV void mma_commit_pair(uint32_t bar, uint16_t mask) {
+  asm volatile(
+      "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64"
+      " [%0], %1;" ::"r"(bar),
+      "h"(mask)
       : "memory");
 }
 
@@ -160,6 +258,118 @@ LWE_DEV uint32_t fold(uint32_t lo_bits, uint32_t hi_bits) {
   const int lo = __float2int_rn(__uint_as_float(lo_bits));
   const int hi = __float2int_rn(__uint_as_float(hi_bits));
   return (uint32_t)lo + ((uint32_t)hi << 8);
+}
+
+// One 128-row x BN-column output tile of this CTA from its TMEM
+// accumulator (lo limb products at column c, hi at BN + c): fold the limbs,
+// add the K-split running sum, E' (B' columns) or E'' + Enc(mu) (C
+// columns), then store, or compare with the received ciphertext and flag a
+// mismatch.  `row` is this thread's output row, tl its TMEM lane quarter.
+template <int BN>
+LWE_DEV void epilogue_tile(const GemmSaArgs &a, uint32_t row, uint32_t n0, uint32_t tl) {
+  const uint32_t D = a.logq, mask = (1u << D) - 1u;
+  const bool rv = row < a.rows;
+  const uint32_t e = row >> 3, kk = row & 7;
+  uint8_t *obase = a.out + (size_t)e * a.out_stride;
+  uint32_t diff = 0;
+  // global operands of the epilogue (E' and, for Decaps, the received
+  // B'), prefetched one 16-column chunk ahead of their use
+  uint4 e_cur = make_uint4(0, 0, 0, 0), o_cur0 = e_cur, o_cur1 = e_cur;
+  auto fetch = [&](uint32_t cc, uint4 &ev, uint4 &o0, uint4 &o1) {
+    const uint32_t c = n0 + 16 * cc;
+    if (rv && c < a.n) {
+      if (a.E) ev = __ldg(reinterpret_cast<const uint4 *>(a.E + (size_t)row * a.n + c));
+      if (a.cmp) {
+        const uint4 *o = reinterpret_cast<const uint4 *>(obase + 2 * ((size_t)kk * a.n + c));
+        o0 = __ldg(o);
+        o1 = __ldg(o + 1);
+      }
+    }
+  };
+  fetch(0, e_cur, o_cur0, o_cur1);
+#pragma unroll
+  for (uint32_t cc = 0; cc < BN / 16; cc++) {
+    const uint32_t c = n0 + 16 * cc;
+    uint32_t lo[16], hi[16];
+    tmem_ld16(tl + 16 * cc, lo);
+    tmem_ld16(tl + BN + 16 * cc, hi);
+    uint4 e_nxt = make_uint4(0, 0, 0, 0), o_nxt0 = e_nxt, o_nxt1 = e_nxt;
+    if (cc + 1 < BN / 16) fetch(cc + 1, e_nxt, o_nxt0, o_nxt1);
+    tmem_wait_ld();
+    if (rv && c < a.ncols) {
+      uint32_t v[16];
+#pragma unroll
+      for (int t = 0; t < 16; t++) v[t] = fold(lo[t], hi[t]);
+      const uint32_t nvalid = min(16u, a.ncols - c);
+      if (a.partial_in) {  // running sum of the earlier K passes
+        const uint16_t *pin = a.partial_in + (size_t)row * a.ncols + c;
+        if (nvalid == 16) {
+          const uint4 p0 = __ldg(reinterpret_cast<const uint4 *>(pin));
+          const uint4 p1 = __ldg(reinterpret_cast<const uint4 *>(pin) + 1);
+          const uint32_t pw[8] = {p0.x, p0.y, p0.z, p0.w, p1.x, p1.y, p1.z, p1.w};
+#pragma unroll
+          for (int t = 0; t < 16; t++) v[t] += (pw[t >> 1] >> (16 * (t & 1))) & 0xffffu;
+        } else {
+          for (uint32_t t = 0; t < nvalid; t++) v[t] += pin[t];
+        }
+      }
+      if (a.partial_out) {  // non-final pass: keep the running sum
+        uint16_t *pout = a.partial_out + (size_t)row * a.ncols + c;
+        if (nvalid == 16) {
+          uint32_t w[8];
+#pragma unroll
+          for (int t = 0; t < 8; t++) w[t] = (v[2 * t] & 0xffffu) | (v[2 * t + 1] << 16);
+          reinterpret_cast<uint4 *>(pout)[0] = make_uint4(w[0], w[1], w[2], w[3]);
+          reinterpret_cast<uint4 *>(pout)[1] = make_uint4(w[4], w[5], w[6], w[7]);
+        } else {
+          for (uint32_t t = 0; t < nvalid; t++) pout[t] = (uint16_t)v[t];
+        }
+      } else if (c < a.n) {  // B' columns: 16 at once (n is a multiple of 16)
+        if (a.E) {
+          const uint32_t ew[4] = {e_cur.x, e_cur.y, e_cur.z, e_cur.w};
+#pragma unroll
+          for (int t = 0; t < 16; t++) v[t] += (uint32_t)sext8(ew[t >> 2], t & 3);
+        }
+        uint32_t w[8];
+#pragma unroll
+        for (int t = 0; t < 8; t++) w[t] = (v[2 * t] & mask) | ((v[2 * t + 1] & mask) << 16);
+        if (a.cmp) {
+          diff |= (o_cur0.x ^ w[0]) | (o_cur0.y ^ w[1]) | (o_cur0.z ^ w[2]) |
+                  (o_cur0.w ^ w[3]) | (o_cur1.x ^ w[4]) | (o_cur1.y ^ w[5]) |
+                  (o_cur1.z ^ w[6]) | (o_cur1.w ^ w[7]);
+        } else {
+          uint4 *o = reinterpret_cast<uint4 *>(obase + 2 * ((size_t)kk * a.n + c));
+          o[0] = make_uint4(w[0], w[1], w[2], w[3]);
+          o[1] = make_uint4(w[4], w[5], w[6], w[7]);
+        }
+      } else {  // V columns n..n+7: C = V + E'' + Enc(mu)
+        const uint32_t Bb = a.B;
+        const uint8_t *mu = a.mu + 32 * (size_t)e + kk * Bb;
+        uint32_t bits = 0;
+        for (uint32_t t = 0; t < Bb; t++) bits |= (uint32_t)mu[t] << (8 * t);
+        const int8_t *epp = a.Epp + 64 * (size_t)e + 8 * kk;
+        uint16_t *co = reinterpret_cast<uint16_t *>(obase + 16 * (size_t)a.n) + 8 * kk;
+#pragma unroll
+        for (int t = 0; t < 8; t++) {
+          const uint32_t sym = (bits >> (t * Bb)) & ((1u << Bb) - 1u);
+          const uint32_t cv = (v[t] + (uint32_t)(int)epp[t] + (sym << (D - Bb))) & mask;
+          if (a.cmp)
+            diff |= cv ^ (uint32_t)co[t];
+          else
+            co[t] = (uint16_t)cv;
+        }
+      }
+    }
+    e_cur = e_nxt;
+    o_cur0 = o_nxt0;
+    o_cur1 = o_nxt1;
+  }
+  if (a.cmp) {
+    diff |= __shfl_xor_sync(0xffffffffu, diff, 1);
+    diff |= __shfl_xor_sync(0xffffffffu, diff, 2);
+    diff |= __shfl_xor_sync(0xffffffffu, diff, 4);
+    if (rv && kk == 0 && diff) atomicOr(a.flags + e, 1u);
+  }
 }
 
 template <int BN>
@@ -290,119 +500,15 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   } else if (warp >= 2) {
     // ---------------- epilogue ----------------
     const uint32_t q = warp & 3;  // TMEM lane quarter of this warp
-    const uint32_t D = a.logq, mask = (1u << D) - 1u;
     uint32_t it = 0;
     for (uint32_t tile = blockIdx.x; tile < num_tiles; tile += gridDim.x, ++it) {
       const uint32_t acc = it & 1, use = it >> 1;
-      if (!wait_bar(tfull(acc), use & 1, abort_flag, a.dev_err)) break;
+      if (!wait_bar_warp(tfull(acc), use & 1, abort_flag, a.dev_err)) break;
       tc_fence_after();
       const uint32_t m0 = (tile / num_n) * BM, n0 = (tile % num_n) * BN;
-      const uint32_t row = m0 + 32 * q + lane;
-      const bool rv = row < a.rows;
-      const uint32_t e = row >> 3, kk = row & 7;
-      uint8_t *obase = a.out + (size_t)e * a.out_stride;
-      const uint32_t tl = tmem_base + ((32 * q) << 16) + acc * (2 * BN);
-      uint32_t diff = 0;
-      // global operands of the epilogue (E' and, for Decaps, the received
-      // B'), prefetched one 16-column chunk ahead of their use
-      uint4 e_cur = make_uint4(0, 0, 0, 0), o_cur0 = e_cur, o_cur1 = e_cur;
-      auto fetch = [&](uint32_t cc, uint4 &ev, uint4 &o0, uint4 &o1) {
-        const uint32_t c = n0 + 16 * cc;
-        if (rv && c < a.n) {
-          if (a.E) ev = __ldg(reinterpret_cast<const uint4 *>(a.E + (size_t)row * a.n + c));
-          if (a.cmp) {
-            const uint4 *o = reinterpret_cast<const uint4 *>(obase + 2 * ((size_t)kk * a.n + c));
-            o0 = __ldg(o);
-            o1 = __ldg(o + 1);
-          }
-        }
-      };
-      fetch(0, e_cur, o_cur0, o_cur1);
-#pragma unroll
-      for (uint32_t cc = 0; cc < BN / 16; cc++) {
-        const uint32_t c = n0 + 16 * cc;
-        uint32_t lo[16], hi[16];
-        tmem_ld16(tl + 16 * cc, lo);
-        tmem_ld16(tl + BN + 16 * cc, hi);
-        uint4 e_nxt = make_uint4(0, 0, 0, 0), o_nxt0 = e_nxt, o_nxt1 = e_nxt;
-        if (cc + 1 < BN / 16) fetch(cc + 1, e_nxt, o_nxt0, o_nxt1);
-        tmem_wait_ld();
-        if (rv && c < a.ncols) {
-          uint32_t v[16];
-#pragma unroll
-          for (int t = 0; t < 16; t++) v[t] = fold(lo[t], hi[t]);
-          const uint32_t nvalid = min(16u, a.ncols - c);
-          if (a.partial_in) {  // running sum of the earlier K passes
-            const uint16_t *pin = a.partial_in + (size_t)row * a.ncols + c;
-            if (nvalid == 16) {
-              const uint4 p0 = __ldg(reinterpret_cast<const uint4 *>(pin));
-              const uint4 p1 = __ldg(reinterpret_cast<const uint4 *>(pin) + 1);
-              const uint32_t pw[8] = {p0.x, p0.y, p0.z, p0.w, p1.x, p1.y, p1.z, p1.w};
-#pragma unroll
-              for (int t = 0; t < 16; t++) v[t] += (pw[t >> 1] >> (16 * (t & 1))) & 0xffffu;
-            } else {
-              for (uint32_t t = 0; t < nvalid; t++) v[t] += pin[t];
-            }
-          }
-          if (a.partial_out) {  // non-final pass: keep the running sum
-            uint16_t *pout = a.partial_out + (size_t)row * a.ncols + c;
-            if (nvalid == 16) {
-              uint32_t w[8];
-#pragma unroll
-              for (int t = 0; t < 8; t++) w[t] = (v[2 * t] & 0xffffu) | (v[2 * t + 1] << 16);
-              reinterpret_cast<uint4 *>(pout)[0] = make_uint4(w[0], w[1], w[2], w[3]);
-              reinterpret_cast<uint4 *>(pout)[1] = make_uint4(w[4], w[5], w[6], w[7]);
-            } else {
-              for (uint32_t t = 0; t < nvalid; t++) pout[t] = (uint16_t)v[t];
-            }
-          } else if (c < a.n) {  // B' columns: 16 at once (n is a multiple of 16)
-            if (a.E) {
-              const uint32_t ew[4] = {e_cur.x, e_cur.y, e_cur.z, e_cur.w};
-#pragma unroll
-              for (int t = 0; t < 16; t++) v[t] += (uint32_t)sext8(ew[t >> 2], t & 3);
-            }
-            uint32_t w[8];
-#pragma unroll
-            for (int t = 0; t < 8; t++) w[t] = (v[2 * t] & mask) | ((v[2 * t + 1] & mask) << 16);
-            if (a.cmp) {
-              diff |= (o_cur0.x ^ w[0]) | (o_cur0.y ^ w[1]) | (o_cur0.z ^ w[2]) |
-                      (o_cur0.w ^ w[3]) | (o_cur1.x ^ w[4]) | (o_cur1.y ^ w[5]) |
-                      (o_cur1.z ^ w[6]) | (o_cur1.w ^ w[7]);
-            } else {
-              uint4 *o = reinterpret_cast<uint4 *>(obase + 2 * ((size_t)kk * a.n + c));
-              o[0] = make_uint4(w[0], w[1], w[2], w[3]);
-              o[1] = make_uint4(w[4], w[5], w[6], w[7]);
-            }
-          } else {  // V columns n..n+7: C = V + E'' + Enc(mu)
-            const uint32_t Bb = a.B;
-            const uint8_t *mu = a.mu + 32 * (size_t)e + kk * Bb;
-            uint32_t bits = 0;
-            for (uint32_t t = 0; t < Bb; t++) bits |= (uint32_t)mu[t] << (8 * t);
-            const int8_t *epp = a.Epp + 64 * (size_t)e + 8 * kk;
-            uint16_t *co = reinterpret_cast<uint16_t *>(obase + 16 * (size_t)a.n) + 8 * kk;
-#pragma unroll
-            for (int t = 0; t < 8; t++) {
-              const uint32_t sym = (bits >> (t * Bb)) & ((1u << Bb) - 1u);
-              const uint32_t cv = (v[t] + (uint32_t)(int)epp[t] + (sym << (D - Bb))) & mask;
-              if (a.cmp)
-                diff |= cv ^ (uint32_t)co[t];
-              else
-                co[t] = (uint16_t)cv;
-            }
-          }
-        }
-        e_cur = e_nxt;
-        o_cur0 = o_nxt0;
-        o_cur1 = o_nxt1;
-      }
+      epilogue_tile<BN>(a, m0 + 32 * q + lane, n0, tmem_base + ((32 * q) << 16) + acc * (2 * BN));
       tc_fence_before();
       mbar_arrive(tempty(acc));
-      if (a.cmp) {
-        diff |= __shfl_xor_sync(0xffffffffu, diff, 1);
-        diff |= __shfl_xor_sync(0xffffffffu, diff, 2);
-        diff |= __shfl_xor_sync(0xffffffffu, diff, 4);
-        if (rv && kk == 0 && diff) atomicOr(a.flags + e, 1u);
-      }
     }
   }
   tc_fence_before();
@@ -410,6 +516,179 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   if (warp == 1) {
     tc_fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base),
+                 "r"((uint32_t)C::TMEM_COLS)
+                 : "memory");
+  }
+}
+
+// CTA-pair kernel (see the file head).  Roles per CTA as in k_gemm_sa;
+// only the leader (rank 0) issues MMAs.  Tiles: 256 rows (rank r owns rows
+// 128 r .. 128 r + 127 of the tile) x BN2 columns, both CTAs of a cluster
+// walking the same tile sequence.
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHREADS, 1)
+    k_gemm_sa2(const __grid_constant__ CUtensorMap tmS, const __grid_constant__ CUtensorMap tmL,
+               const GemmSaArgs a) {
+  using C = Cfg2;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
+                                              ~(uintptr_t)1023);
+  uint64_t *bars = reinterpret_cast<uint64_t *>(smem + C::BAR_OFF);
+  // bars: full[STAGES2] (leader), empty[STAGES2], tfull[2], tempty[2]
+  // (leader), done (leader)
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * STAGES2 + 5);
+  volatile uint32_t *abort_flag = tmem_slot + 1;
+
+  const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t rank = cluster_rank();
+  const bool leader = rank == 0;
+  const uint32_t cluster = blockIdx.x >> 1, nclusters = gridDim.x >> 1;
+  const uint32_t num_m = (a.rows + 2 * BM - 1) / (2 * BM);
+  const uint32_t num_n = (a.ncols + BN2 - 1) / BN2;
+  const uint32_t num_tiles = num_m * num_n;
+  const uint32_t KB = a.kblocks;
+
+  auto bar = [&](int i) { return smem_u32(bars + i); };
+  auto full = [&](uint32_t s) { return bar(s); };
+  auto empty = [&](uint32_t s) { return bar(STAGES2 + s); };
+  auto tfull = [&](uint32_t x) { return bar(2 * STAGES2 + x); };
+  auto tempty = [&](uint32_t x) { return bar(2 * STAGES2 + 2 + x); };
+  const uint32_t done_bar = bar(2 * STAGES2 + 4);
+  auto sA = [&](uint32_t s) { return smem_u32(smem + s * C::STAGE_BYTES); };
+  auto sB = [&](uint32_t s) { return smem_u32(smem + s * C::STAGE_BYTES + C::A_BYTES); };
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES2; s++) {
+      mbar_init(full(s), 1);
+      mbar_init(empty(s), 1);
+    }
+    for (int x = 0; x < 2; x++) {
+      mbar_init(tfull(x), 1);
+      mbar_init(tempty(x), 2 * 4);  // one arrival per epilogue warp of each CTA
+    }
+    mbar_init(done_bar, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmS)) : "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmL)) : "memory");
+  }
+  if (warp == 1) {  // one warp of each CTA of the pair allocates together
+    asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_slot)),
+                 "r"((uint32_t)C::TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  cluster_sync();  // the peer's barriers exist before any copy or arrive targets them
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+
+  if (warp == 0 && lane == 0) {
+    // ---------------- TMA producer (both CTAs) ----------------
+    uint32_t stage = 0, phase = 0;
+    uint32_t armed = 0, last_phase = 0;  // leader: stages with a phase in flight
+    bool ok = true;
+    for (uint32_t tile = cluster; ok && tile < num_tiles; tile += nclusters) {
+      const uint32_t tm = tile / num_n;
+      const int m0 = (int)(tm * 2 * BM + rank * BM);
+      const int n0 = (int)((tile % num_n) * BN2);
+      // a tail tile whose second half has no rows: the peer loads no S'
+      // (its accumulator rows are never stored) but still its limb tile
+      const bool peer_rows = tm * 2 * BM + BM < a.rows;
+      const uint32_t tx = 2 * C::STAGE_BYTES - (peer_rows ? 0u : (uint32_t)C::A_BYTES);
+      for (uint32_t kb = 0; kb < KB; kb++) {
+        if (!wait_bar(empty(stage), phase ^ 1, abort_flag, a.dev_err)) {
+          ok = false;
+          break;
+        }
+        const uint32_t fb = peer_addr(full(stage), 0);
+        if (leader) {
+          mbar_arrive_expect_tx(full(stage), tx);
+          armed |= 1u << stage;
+          last_phase = (last_phase & ~(1u << stage)) | (phase << stage);
+        }
+        if (leader || peer_rows) tma_load_2d_pair(sA(stage), &tmS, (int)(a.k0 + kb * BK), m0, fb);
+        tma_load_3d_pair(sB(stage), &tmL, (int)(a.k0 + kb * BK), n0, (int)rank, fb);
+        if (++stage == STAGES2) {
+          stage = 0;
+          phase ^= 1;
+        }
+      }
+    }
+    if (!ok) {
+      // let the copies already issued land before the CTA leaves: the
+      // leader sees both CTAs' bytes on its full barriers; the peer cannot
+      // observe its own copies and waits out the drain time
+      const uint64_t t0 = gtime();
+      if (leader) {
+        for (uint32_t s = 0; s < STAGES2; s++) {
+          if (!(armed & (1u << s))) continue;
+          const uint32_t ph = (last_phase >> s) & 1u;
+          while (!mbar_try_wait(full(s), ph) && gtime() - t0 < kDrainNs) {
+          }
+        }
+      }
+      while (gtime() - t0 < kDrainNs) {
+      }
+    }
+  } else if (warp == 1 && lane == 0 && leader) {
+    // ---------------- MMA issuer (leader only) ----------------
+    uint32_t stage = 0, phase = 0, it = 0;
+    bool ok = true;
+    for (uint32_t tile = cluster; ok && tile < num_tiles; tile += nclusters, ++it) {
+      const uint32_t acc = it & 1, use = it >> 1;
+      if (!wait_bar(tempty(acc), (use & 1) ^ 1, abort_flag, a.dev_err)) {
+        ok = false;
+        break;
+      }
+      tc_fence_after();
+      const uint32_t d = tmem_base + acc * (2 * BN2);
+      for (uint32_t kb = 0; kb < KB; kb++) {
+        if (!wait_bar(full(stage), phase, abort_flag, a.dev_err)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const uint64_t ad = sdesc(sA(stage)), bd = sdesc(sB(stage));
+#pragma unroll
+        for (uint32_t kk = 0; kk < BK / 16; kk++)
+          mma_bf16_pair(d, ad + 2 * kk, bd + 2 * kk, C::IDESC, (kb | kk) != 0);
+        mma_commit_pair(empty(stage), 0x3);
+        if (++stage == STAGES2) {
+          stage = 0;
+          phase ^= 1;
+        }
+      }
+      if (ok) mma_commit_pair(tfull(acc), 0x3);
+    }
+    // all issued MMAs complete before either CTA releases TMEM or leaves
+    mma_commit_pair(done_bar, 0x1);
+    const uint64_t t0 = gtime();
+    while (!mbar_try_wait(done_bar, 0) && gtime() - t0 < kTimeoutNs) {
+    }
+  } else if (warp >= 2) {
+    // ---------------- epilogue (both CTAs) ----------------
+    const uint32_t q = warp & 3;  // TMEM lane quarter of this warp
+    uint32_t it = 0;
+    for (uint32_t tile = cluster; tile < num_tiles; tile += nclusters, ++it) {
+      const uint32_t acc = it & 1, use = it >> 1;
+      if (!wait_bar_warp(tfull(acc), use & 1, abort_flag, a.dev_err)) break;
+      tc_fence_after();
+      const uint32_t m0 = (tile / num_n) * 2 * BM + rank * BM, n0 = (tile % num_n) * BN2;
+      epilogue_tile<BN2>(a, m0 + 32 * q + lane, n0,
+                         tmem_base + ((32 * q) << 16) + acc * (2 * BN2));
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive_cluster(peer_addr(tempty(acc), 0));
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  cluster_sync();  // no MMA, copy or arrive of the pair is left when either CTA frees TMEM
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem_base),
                  "r"((uint32_t)C::TMEM_COLS)
                  : "memory");
   }
@@ -461,6 +740,23 @@ int launch_bn(const GemmSaArgs &a, int num_sms, cudaStream_t st) {
   return LWE_OK;
 }
 
+int launch_pair(const GemmSaArgs &a, int num_sms, cudaStream_t st) {
+  CUtensorMap tmS, tmL;
+  const cuuint64_t dS[2] = {a.n, a.rows};
+  const cuuint64_t sS[1] = {2ull * a.n};
+  const cuuint32_t bS[2] = {BK, BM};
+  const cuuint64_t dL[3] = {a.n, a.ncols, 2};
+  const cuuint64_t sL[2] = {2ull * a.n, 2ull * a.n * a.ncols};
+  const cuuint32_t bL[3] = {BK, BN2, 1};
+  if (!make_map(&tmS, a.S, 2, dS, sS, bS)) return LWE_ECUDA;
+  if (!make_map(&tmL, a.limbs, 3, dL, sL, bL)) return LWE_ECUDA;
+  const uint32_t tiles = ((a.rows + 2 * BM - 1) / (2 * BM)) * ((a.ncols + BN2 - 1) / BN2);
+  const uint32_t pairs = (uint32_t)(num_sms / 2);
+  const uint32_t clusters = tiles < pairs ? tiles : pairs;
+  k_gemm_sa2<<<2 * clusters, NTHREADS, Cfg2::SMEM, st>>>(tmS, tmL, a);
+  return LWE_OK;
+}
+
 }  // namespace
 
 cudaError_t lwe_gemm_setup() {
@@ -475,6 +771,8 @@ cudaError_t lwe_gemm_setup() {
   }
   cudaError_t e = cudaFuncSetAttribute(k_gemm_sa<128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        Cfg<128>::SMEM);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_gemm_sa2, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg2::SMEM);
   if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(k_gemm_sa<64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               Cfg<64>::SMEM);
@@ -510,7 +808,9 @@ int launch_gemm_sa(const GemmSaArgs &a, int num_sms, cudaStream_t st) {
     b.kblocks = (min(a.n, b.k0 + kc) - b.k0 + BK - 1) / BK;
     b.partial_in = p > 0 ? a.partial_out : nullptr;
     b.partial_out = p + 1 < passes ? a.partial_out : nullptr;
-    const int rc = a.bn == 64 ? launch_bn<64>(b, num_sms, st) : launch_bn<128>(b, num_sms, st);
+    const int rc = a.pair && num_sms >= 2 ? launch_pair(b, num_sms, st)
+                   : a.bn == 64           ? launch_bn<64>(b, num_sms, st)
+                                          : launch_bn<128>(b, num_sms, st);
     if (rc != LWE_OK) return rc;
   }
   return LWE_OK;

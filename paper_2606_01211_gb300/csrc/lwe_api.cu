@@ -152,6 +152,7 @@ struct lwe_ctx {
   int path = LWE_PATH_AUTO;
   int tensor_min = 64;
   int gemm_bn = 128;
+  int gemm_pair = 1;
   bool timing = false;
   uint64_t launches = 0;
   std::vector<TimedLaunch> pending;
@@ -356,6 +357,7 @@ int run_encrypt(lwe_ctx *c, const uint8_t *pk, const uint16_t *A, uint32_t count
     ga.B = c->p.B;
     ga.cmp = cmp ? 1 : 0;
     ga.bn = c->gemm_bn;
+    ga.pair = c->gemm_pair;
     ga.kchunk = c->kchunk;
     ga.partial_out = c->partial;
     int rc = LWE_OK;
@@ -647,6 +649,10 @@ int lwe_ctx_set_option(lwe_ctx *c, int option, int64_t value) {
       if (value != 64 && value != 128) return LWE_EINVAL;
       c->gemm_bn = (int)value;
       return LWE_OK;
+    case LWE_OPT_GEMM_PAIR:
+      if (value != 0 && value != 1) return LWE_EINVAL;
+      c->gemm_pair = (int)value;
+      return LWE_OK;
     case LWE_OPT_GEMM_KCHUNK:
       if (value == 0) {
         c->kchunk = lwe_gemm_kchunk(c->p.clip);
@@ -913,6 +919,7 @@ int lwe_matmul_modq(lwe_ctx *c, int side, const uint16_t *A, const uint8_t *seed
     ga.B = 0;
     ga.cmp = 0;
     ga.bn = c->gemm_bn;
+    ga.pair = c->gemm_pair;
     ga.kchunk = c->kchunk;
     ga.partial_out = c->partial;
     LAUNCH(c, KID_GEMM, st, rc = launch_gemm_sa(ga, c->num_sms, st));

@@ -24,6 +24,7 @@ def _sa_ctx(n, logq, items, bn=128, clip=12):
     p = lwe.Params(n=n, logq=logq, B=2, clip=clip, sigma=2.8 if clip == 12 else 2.3)
     ctx = lwe.Ctx(p, max_batch=items)
     ctx.set_path(lwe.PATH_TENSOR)
+    ctx.set_option(lwe.OPT_GEMM_PAIR, 0)  # the single-CTA kernel (the pair kernel: test_gpu_pair)
     ctx.set_option(lwe.OPT_GEMM_BN, bn)
     return ctx
 
@@ -64,12 +65,14 @@ def test_tensor_exact_at_worst_case_limbs(clip):
 
 @pytest.mark.parametrize("name,count", [("P640", 21), ("P976", 37), ("P1344", 19)])
 @pytest.mark.parametrize("stored", [True, False])
-def test_kem_tensor_path_matches_oracle(name, count, stored):
+@pytest.mark.parametrize("pair", [1, 0])
+def test_kem_tensor_path_matches_oracle(name, count, stored, pair):
     cfg = PRESETS[name]
     p, po = params(name)
     pk_o, sk_o, A_o, ms = oracle_keys(cfg_key(cfg), 21)
     ctx = lwe.Ctx(p, max_batch=count)
     ctx.set_path(lwe.PATH_TENSOR)
+    ctx.set_option(lwe.OPT_GEMM_PAIR, pair)
     pk, sk = ctx.empty_pk(1), ctx.empty_sk(1)
     A = torch.empty((p.n, p.n), dtype=torch.int16, device="cuda") if stored else None
     ctx.keygen(dev(ms[None, :]), pk, sk, A_out=A)
@@ -151,5 +154,5 @@ def test_graph_replay_equals_direct_calls():
 def test_autotune_returns_a_valid_choice():
     from paper_2606_01211_gb300 import batch
     res = batch.autotune("P640", 256, cache=None)
-    assert res["gemm_bn"] in (64, 128)
+    assert res["gemm_bn"] in (64, 128) and res["gemm_pair"] in (0, 1)
     assert 16 <= res["tensor_min"] <= 257
