@@ -65,6 +65,7 @@ struct Cfg {
 // columns per stage; MMA M = 256 (the pair), N = 2 BN2 (lo | hi).
 constexpr int BN2 = 128;
 constexpr int STAGES2 = 6;
+constexpr int NTHREADS2 = 64 + 8 * 32;  // producer, MMA, 8 epilogue warps
 struct Cfg2 {
   static constexpr int A_BYTES = BM * BK * 2;        // 16 KB
   static constexpr int B_BYTES = BN2 * BK * 2;       // 16 KB: one limb
@@ -260,46 +261,91 @@ LWE_DEV uint32_t fold(uint32_t lo_bits, uint32_t hi_bits) {
   return (uint32_t)lo + ((uint32_t)hi << 8);
 }
 
-// One 128-row x BN-column output tile of this CTA from its TMEM
-// accumulator (lo limb products at column c, hi at BN + c): fold the limbs,
-// add the K-split running sum, E' (B' columns) or E'' + Enc(mu) (C
-// columns), then store, or compare with the received ciphertext and flag a
-// mismatch.  `row` is this thread's output row, tl its TMEM lane quarter.
-template <int BN>
-LWE_DEV void epilogue_tile(const GemmSaArgs &a, uint32_t row, uint32_t n0, uint32_t tl) {
+// The same fold for |lo|, |hi| < 2^22: x + 1.5 * 2^23 is exact and its bit
+// pattern is 0x4B400000 + x, whose low 16 bits are x mod 2^16, so two
+// FP32 adds replace the two float-to-integer conversions.
+LWE_DEV uint32_t fold_small(uint32_t lo_bits, uint32_t hi_bits) {
+  const uint32_t lo = __float_as_uint(__fadd_rn(__uint_as_float(lo_bits), 12582912.0f));
+  const uint32_t hi = __float_as_uint(__fadd_rn(__uint_as_float(hi_bits), 12582912.0f));
+  return lo + (hi << 8);
+}
+
+// The global operands of CHUNKS 16-column chunks of this thread's row from
+// column n0 (zero where absent): E' and, for Decaps (ov != nullptr), the
+// received B'.  Issued ahead of the accumulator wait so that the load
+// latency overlaps the tile's MMAs.
+template <int CHUNKS>
+LWE_DEV void epilogue_prefetch(const GemmSaArgs &a, uint32_t row, uint32_t n0, uint4 *ev,
+                               uint4 *ov) {
+  const bool rv = row < a.rows;
+  const uint8_t *obase = a.out + (size_t)(row >> 3) * a.out_stride + 2 * (size_t)(row & 7) * a.n;
+#pragma unroll
+  for (int cc = 0; cc < CHUNKS; cc++) {
+    const uint32_t c = n0 + 16 * cc;
+    const bool in = rv && c < a.n;
+    ev[cc] = make_uint4(0, 0, 0, 0);
+    if (a.E && in) ev[cc] = __ldg(reinterpret_cast<const uint4 *>(a.E + (size_t)row * a.n + c));
+    if (ov) {
+      ov[2 * cc] = make_uint4(0, 0, 0, 0);
+      ov[2 * cc + 1] = ov[2 * cc];
+      if (a.cmp && in) {
+        const uint4 *o = reinterpret_cast<const uint4 *>(obase + 2 * (size_t)c);
+        ov[2 * cc] = __ldg(o);
+        ov[2 * cc + 1] = __ldg(o + 1);
+      }
+    }
+  }
+}
+
+// CHUNKS 16-column chunks of one output row of this CTA from its TMEM
+// accumulator (lo limb products at column tl + j, hi at tl + hi_off + j):
+// fold the limbs, add the K-split running sum, E' (B' columns) or E'' +
+// Enc(mu) (C columns), then store, or compare with the received ciphertext
+// and flag a mismatch.  `row` is this thread's output row, n0 the first
+// column, tl the TMEM address of the first lo column of its lane quarter.
+// The received B' comes from ov when given (prefetched with the E'), else
+// it is loaded here one chunk ahead of its use.
+template <int CHUNKS>
+LWE_DEV void epilogue_tile(const GemmSaArgs &a, uint32_t row, uint32_t n0, uint32_t tl,
+                           uint32_t hi_off, const uint4 *ev, const uint4 *ov) {
   const uint32_t D = a.logq, mask = (1u << D) - 1u;
   const bool rv = row < a.rows;
   const uint32_t e = row >> 3, kk = row & 7;
   uint8_t *obase = a.out + (size_t)e * a.out_stride;
   uint32_t diff = 0;
-  // global operands of the epilogue (E' and, for Decaps, the received
-  // B'), prefetched one 16-column chunk ahead of their use
-  uint4 e_cur = make_uint4(0, 0, 0, 0), o_cur0 = e_cur, o_cur1 = e_cur;
-  auto fetch = [&](uint32_t cc, uint4 &ev, uint4 &o0, uint4 &o1) {
+  uint4 o_cur0 = make_uint4(0, 0, 0, 0), o_cur1 = o_cur0;
+  auto fetch = [&](uint32_t cc, uint4 &o0, uint4 &o1) {
     const uint32_t c = n0 + 16 * cc;
-    if (rv && c < a.n) {
-      if (a.E) ev = __ldg(reinterpret_cast<const uint4 *>(a.E + (size_t)row * a.n + c));
-      if (a.cmp) {
-        const uint4 *o = reinterpret_cast<const uint4 *>(obase + 2 * ((size_t)kk * a.n + c));
-        o0 = __ldg(o);
-        o1 = __ldg(o + 1);
-      }
+    if (a.cmp && rv && c < a.n) {
+      const uint4 *o = reinterpret_cast<const uint4 *>(obase + 2 * ((size_t)kk * a.n + c));
+      o0 = __ldg(o);
+      o1 = __ldg(o + 1);
     }
   };
-  fetch(0, e_cur, o_cur0, o_cur1);
+  if (!ov) fetch(0, o_cur0, o_cur1);
 #pragma unroll
-  for (uint32_t cc = 0; cc < BN / 16; cc++) {
+  for (uint32_t cc = 0; cc < CHUNKS; cc++) {
     const uint32_t c = n0 + 16 * cc;
     uint32_t lo[16], hi[16];
     tmem_ld16(tl + 16 * cc, lo);
-    tmem_ld16(tl + BN + 16 * cc, hi);
-    uint4 e_nxt = make_uint4(0, 0, 0, 0), o_nxt0 = e_nxt, o_nxt1 = e_nxt;
-    if (cc + 1 < BN / 16) fetch(cc + 1, e_nxt, o_nxt0, o_nxt1);
+    tmem_ld16(tl + hi_off + 16 * cc, hi);
+    uint4 o_nxt0 = make_uint4(0, 0, 0, 0), o_nxt1 = o_nxt0;
+    if (ov) {
+      o_cur0 = ov[2 * cc];
+      o_cur1 = ov[2 * cc + 1];
+    } else if (cc + 1 < CHUNKS) {
+      fetch(cc + 1, o_nxt0, o_nxt1);
+    }
     tmem_wait_ld();
     if (rv && c < a.ncols) {
       uint32_t v[16];
+      if (a.fast_fold) {
 #pragma unroll
-      for (int t = 0; t < 16; t++) v[t] = fold(lo[t], hi[t]);
+        for (int t = 0; t < 16; t++) v[t] = fold_small(lo[t], hi[t]);
+      } else {
+#pragma unroll
+        for (int t = 0; t < 16; t++) v[t] = fold(lo[t], hi[t]);
+      }
       const uint32_t nvalid = min(16u, a.ncols - c);
       if (a.partial_in) {  // running sum of the earlier K passes
         const uint16_t *pin = a.partial_in + (size_t)row * a.ncols + c;
@@ -309,8 +355,10 @@ LWE_DEV void epilogue_tile(const GemmSaArgs &a, uint32_t row, uint32_t n0, uint3
           const uint32_t pw[8] = {p0.x, p0.y, p0.z, p0.w, p1.x, p1.y, p1.z, p1.w};
 #pragma unroll
           for (int t = 0; t < 16; t++) v[t] += (pw[t >> 1] >> (16 * (t & 1))) & 0xffffu;
-        } else {
-          for (uint32_t t = 0; t < nvalid; t++) v[t] += pin[t];
+        } else {  // ragged last columns; unrolled so that v stays in registers
+#pragma unroll
+          for (uint32_t t = 0; t < 16; t++)
+            if (t < nvalid) v[t] += pin[t];
         }
       }
       if (a.partial_out) {  // non-final pass: keep the running sum
@@ -322,11 +370,13 @@ LWE_DEV void epilogue_tile(const GemmSaArgs &a, uint32_t row, uint32_t n0, uint3
           reinterpret_cast<uint4 *>(pout)[0] = make_uint4(w[0], w[1], w[2], w[3]);
           reinterpret_cast<uint4 *>(pout)[1] = make_uint4(w[4], w[5], w[6], w[7]);
         } else {
-          for (uint32_t t = 0; t < nvalid; t++) pout[t] = (uint16_t)v[t];
+#pragma unroll
+          for (uint32_t t = 0; t < 16; t++)
+            if (t < nvalid) pout[t] = (uint16_t)v[t];
         }
       } else if (c < a.n) {  // B' columns: 16 at once (n is a multiple of 16)
         if (a.E) {
-          const uint32_t ew[4] = {e_cur.x, e_cur.y, e_cur.z, e_cur.w};
+          const uint32_t ew[4] = {ev[cc].x, ev[cc].y, ev[cc].z, ev[cc].w};
 #pragma unroll
           for (int t = 0; t < 16; t++) v[t] += (uint32_t)sext8(ew[t >> 2], t & 3);
         }
@@ -360,9 +410,10 @@ LWE_DEV void epilogue_tile(const GemmSaArgs &a, uint32_t row, uint32_t n0, uint3
         }
       }
     }
-    e_cur = e_nxt;
-    o_cur0 = o_nxt0;
-    o_cur1 = o_nxt1;
+    if (!ov) {
+      o_cur0 = o_nxt0;
+      o_cur1 = o_nxt1;
+    }
   }
   if (a.cmp) {
     diff |= __shfl_xor_sync(0xffffffffu, diff, 1);
@@ -503,10 +554,14 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     uint32_t it = 0;
     for (uint32_t tile = blockIdx.x; tile < num_tiles; tile += gridDim.x, ++it) {
       const uint32_t acc = it & 1, use = it >> 1;
+      const uint32_t m0 = (tile / num_n) * BM, n0 = (tile % num_n) * BN;
+      const uint32_t row = m0 + 32 * q + lane;
+      uint4 ev[BN / 16];
+      epilogue_prefetch<BN / 16>(a, row, n0, ev, nullptr);
       if (!wait_bar_warp(tfull(acc), use & 1, abort_flag, a.dev_err)) break;
       tc_fence_after();
-      const uint32_t m0 = (tile / num_n) * BM, n0 = (tile % num_n) * BN;
-      epilogue_tile<BN>(a, m0 + 32 * q + lane, n0, tmem_base + ((32 * q) << 16) + acc * (2 * BN));
+      epilogue_tile<BN / 16>(a, row, n0, tmem_base + ((32 * q) << 16) + acc * (2 * BN), BN, ev,
+                             nullptr);
       tc_fence_before();
       mbar_arrive(tempty(acc));
     }
@@ -525,7 +580,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 // only the leader (rank 0) issues MMAs.  Tiles: 256 rows (rank r owns rows
 // 128 r .. 128 r + 127 of the tile) x BN2 columns, both CTAs of a cluster
 // walking the same tile sequence.
-__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHREADS, 1)
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHREADS2, 1)
     k_gemm_sa2(const __grid_constant__ CUtensorMap tmS, const __grid_constant__ CUtensorMap tmL,
                const GemmSaArgs a) {
   using C = Cfg2;
@@ -563,7 +618,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHREADS, 1)
     }
     for (int x = 0; x < 2; x++) {
       mbar_init(tfull(x), 1);
-      mbar_init(tempty(x), 2 * 4);  // one arrival per epilogue warp of each CTA
+      mbar_init(tempty(x), 2 * 8);  // one arrival per epilogue warp of each CTA
     }
     mbar_init(done_bar, 1);
     *abort_flag = 0;
@@ -670,17 +725,26 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHREADS, 1)
   } else if (warp >= 2) {
     // ---------------- epilogue (both CTAs) ----------------
     const uint32_t q = warp & 3;  // TMEM lane quarter of this warp
+    const uint32_t half = (warp - 2) >> 2;  // which 64 of the tile's 128 columns
+    // this thread's row and first column in a tile
+    auto row_of = [&](uint32_t t) { return (t / num_n) * 2 * BM + rank * BM + 32 * q + lane; };
+    auto col_of = [&](uint32_t t) { return (t % num_n) * BN2 + half * (BN2 / 2); };
+    // the next tile's E' / received B' are loaded while this tile drains
+    uint4 ev[BN2 / 32], ov[BN2 / 16];
     uint32_t it = 0;
+    if (cluster < num_tiles) epilogue_prefetch<BN2 / 32>(a, row_of(cluster), col_of(cluster), ev, ov);
     for (uint32_t tile = cluster; tile < num_tiles; tile += nclusters, ++it) {
       const uint32_t acc = it & 1, use = it >> 1;
       if (!wait_bar_warp(tfull(acc), use & 1, abort_flag, a.dev_err)) break;
       tc_fence_after();
-      const uint32_t m0 = (tile / num_n) * 2 * BM + rank * BM, n0 = (tile % num_n) * BN2;
-      epilogue_tile<BN2>(a, m0 + 32 * q + lane, n0,
-                         tmem_base + ((32 * q) << 16) + acc * (2 * BN2));
+      epilogue_tile<BN2 / 32>(a, row_of(tile), col_of(tile),
+                              tmem_base + ((32 * q) << 16) + acc * (2 * BN2) + half * (BN2 / 2),
+                              BN2, ev, ov);
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive_cluster(peer_addr(tempty(acc), 0));
+      const uint32_t next = tile + nclusters;
+      if (next < num_tiles) epilogue_prefetch<BN2 / 32>(a, row_of(next), col_of(next), ev, ov);
     }
   }
   tc_fence_before();
@@ -753,7 +817,7 @@ int launch_pair(const GemmSaArgs &a, int num_sms, cudaStream_t st) {
   const uint32_t tiles = ((a.rows + 2 * BM - 1) / (2 * BM)) * ((a.ncols + BN2 - 1) / BN2);
   const uint32_t pairs = (uint32_t)(num_sms / 2);
   const uint32_t clusters = tiles < pairs ? tiles : pairs;
-  k_gemm_sa2<<<2 * clusters, NTHREADS, Cfg2::SMEM, st>>>(tmS, tmL, a);
+  k_gemm_sa2<<<2 * clusters, NTHREADS2, Cfg2::SMEM, st>>>(tmS, tmL, a);
   return LWE_OK;
 }
 
@@ -808,6 +872,8 @@ int launch_gemm_sa(const GemmSaArgs &a, int num_sms, cudaStream_t st) {
     b.kblocks = (min(a.n, b.k0 + kc) - b.k0 + BK - 1) / BK;
     b.partial_in = p > 0 ? a.partial_out : nullptr;
     b.partial_out = p + 1 < passes ? a.partial_out : nullptr;
+    // |partial sums| <= K c 128 (zero-filled K tail included)
+    b.fast_fold = (uint64_t)b.kblocks * BK * a.clip * 128u < (1u << 22) ? 1 : 0;
     const int rc = a.pair && num_sms >= 2 ? launch_pair(b, num_sms, st)
                    : a.bn == 64           ? launch_bn<64>(b, num_sms, st)
                                           : launch_bn<128>(b, num_sms, st);

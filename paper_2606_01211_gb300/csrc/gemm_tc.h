@@ -42,6 +42,8 @@ struct GemmSaArgs {
   const uint16_t *partial_in;
   uint16_t *partial_out;
   uint32_t kchunk;        // host: maximum exact K per pass (multiple of 64)
+  uint32_t clip;          // |S'| bound c
+  uint32_t fast_fold;     // set per pass: every partial sum is below 2^22
 };
 
 cudaError_t lwe_gemm_setup();

@@ -511,12 +511,36 @@ __global__ void __launch_bounds__(256) k_v_encode(VEncArgs a) {
 // Hashing: seeds (Alg. 1), derivation of K' and seedSE' (Alg. 4-5), tree
 // hash of pk / c, and the final keys.
 // ---------------------------------------------------------------------------
+// 32 bytes at any alignment as four little-endian words
+LWE_DEV void load32_le(const uint8_t *p, uint64_t w[4]) {
+  if ((reinterpret_cast<uintptr_t>(p) & 7) == 0) {
+    const uint64_t *q = reinterpret_cast<const uint64_t *>(p);
+#pragma unroll
+    for (int i = 0; i < 4; i++) w[i] = q[i];
+  } else {
+#pragma unroll
+    for (int i = 0; i < 4; i++) {
+      uint64_t v = 0;
+#pragma unroll
+      for (int b = 0; b < 8; b++) v |= (uint64_t)p[8 * i + b] << (8 * b);
+      w[i] = v;
+    }
+  }
+}
+
+// SHA3-256 of prefix || 32 bytes, built lane by lane (the 33-byte message
+// is the 32 bytes shifted up one byte; padding opens byte 1 of lane 4)
 LWE_DEV void sha3_prefixed32(uint8_t prefix, const uint8_t *msg32, uint64_t s[25]) {
-  uint64_t lanes[SHA3_RATE / 8];
-  lanes_zero(lanes);
-  lanes[0] = prefix;
-  lanes_put(lanes, 1, msg32, 32);
-  sha3_256_lanes(lanes, 33, s);
+  uint64_t w[4];
+  load32_le(msg32, w);
+  s[0] = (uint64_t)prefix | (w[0] << 8);
+#pragma unroll
+  for (int j = 1; j < 4; j++) s[j] = (w[j - 1] >> 56) | (w[j] << 8);
+  s[4] = (w[3] >> 56) | ((uint64_t)0x06 << 8);
+#pragma unroll
+  for (int j = 5; j < 25; j++) s[j] = 0;
+  s[SHA3_RATE / 8 - 1] ^= 0x8000000000000000ull;
+  keccak_f1600(s);
 }
 
 __global__ void k_keygen_seeds(KeygenSeedArgs a) {
@@ -546,34 +570,53 @@ __global__ void k_keygen_seeds(KeygenSeedArgs a) {
   sha3_digest(s, sk + a.sk_z_off);
 }
 
+// Alg. 4 / 5 seeds of the (re-)encryption.  mu is 8 B bytes (B <= 4), i.e.
+// whole 64-bit lanes, so both messages are built lane by lane with
+// compile-time state indices (nothing leaves the registers):
+//   Encaps: mu = H(0x4D || coins)[0 : 8 B]
+//   K' = H(pkh || mu),  seedSE' = H(0x01 || pkh || mu)[0 : 16]
 __global__ void k_derive(DeriveArgs a) {
   const uint32_t e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= a.count) return;
   uint64_t s[25];
-  uint8_t *mu = a.mu + 32 * (size_t)e;
-  const uint32_t mub = a.mu_bytes;
-  if (a.coins) {  // Encaps: mu = H(0x4D || coins)[0 : mub]
+  uint64_t *mu64 = reinterpret_cast<uint64_t *>(a.mu + 32 * (size_t)e);
+  const uint32_t nb = a.mu_bytes / 8;  // lanes of mu, 1..4
+  uint64_t x[8];                       // pkh (4 lanes) || mu (nb lanes) || zeros
+  if (a.coins) {
     sha3_prefixed32(0x4D, a.coins + 32 * (size_t)e, s);
-    uint8_t h[32];
-    sha3_digest(s, h);
-    for (uint32_t t = 0; t < 32; t++) mu[t] = t < mub ? h[t] : 0;
+#pragma unroll
+    for (int i = 0; i < 4; i++) {
+      x[4 + i] = (uint32_t)i < nb ? s[i] : 0;
+      mu64[i] = x[4 + i];
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < 4; i++) x[4 + i] = (uint32_t)i < nb ? mu64[i] : 0;
   }
-  uint8_t m[32];
-  for (uint32_t t = 0; t < mub; t++) m[t] = mu[t];
   const uint8_t *pkh = a.pkh_ptrs ? a.pkh_ptrs[e] + a.pkh_off : a.pkh + (size_t)e * a.pkh_stride;
-  // K' = H(pkh || mu)
-  uint64_t lanes[SHA3_RATE / 8];
-  lanes_zero(lanes);
-  lanes_put(lanes, 0, pkh, 32);
-  lanes_put(lanes, 32, m, mub);
-  sha3_256_lanes(lanes, 32 + mub, s);
+  load32_le(pkh, x);
+  // K' = H(pkh || mu): 32 + 8 nb bytes, padding opens lane 4 + nb
+  // (every lane is written unconditionally with a selected value: a
+  // conditional store to lane 4 + nb would become a dynamically indexed
+  // state, i.e. local memory)
+#pragma unroll
+  for (int i = 0; i < 25; i++) s[i] = i < 8 ? x[i] : 0;
+#pragma unroll
+  for (int i = 5; i < 9; i++) s[i] ^= (uint32_t)i == 4 + nb ? 0x06ull : 0ull;
+  s[SHA3_RATE / 8 - 1] ^= 0x8000000000000000ull;
+  keccak_f1600(s);
   sha3_digest(s, a.kprime + 32 * (size_t)e);
-  // seedSE' = H(0x01 || pkh || mu)[0:16]
-  lanes_zero(lanes);
-  lanes[0] = 0x01;
-  lanes_put(lanes, 1, pkh, 32);
-  lanes_put(lanes, 33, m, mub);
-  sha3_256_lanes(lanes, 33 + mub, s);
+  // seedSE' = H(0x01 || pkh || mu): the same lanes one byte later; the
+  // padding byte lands in byte 1 of lane 4 + nb
+  s[0] = 0x01 | (x[0] << 8);
+#pragma unroll
+  for (int j = 1; j < 9; j++) s[j] = (x[j - 1] >> 56) | (j < 8 ? x[j] << 8 : 0);
+#pragma unroll
+  for (int j = 9; j < 25; j++) s[j] = 0;
+#pragma unroll
+  for (int i = 5; i < 9; i++) s[i] ^= (uint32_t)i == 4 + nb ? 0x0600ull : 0ull;
+  s[SHA3_RATE / 8 - 1] ^= 0x8000000000000000ull;
+  keccak_f1600(s);
   sha3_digest16(s, a.seeds + 32 * (size_t)e);
   const uint32_t key[4] = {(uint32_t)s[0], (uint32_t)(s[0] >> 32), (uint32_t)s[1],
                            (uint32_t)(s[1] >> 32)};

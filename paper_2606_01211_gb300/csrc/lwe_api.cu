@@ -358,6 +358,7 @@ int run_encrypt(lwe_ctx *c, const uint8_t *pk, const uint16_t *A, uint32_t count
     ga.cmp = cmp ? 1 : 0;
     ga.bn = c->gemm_bn;
     ga.pair = c->gemm_pair;
+    ga.clip = c->p.clip;
     ga.kchunk = c->kchunk;
     ga.partial_out = c->partial;
     int rc = LWE_OK;
@@ -920,6 +921,7 @@ int lwe_matmul_modq(lwe_ctx *c, int side, const uint16_t *A, const uint8_t *seed
     ga.cmp = 0;
     ga.bn = c->gemm_bn;
     ga.pair = c->gemm_pair;
+    ga.clip = c->p.clip;
     ga.kchunk = c->kchunk;
     ga.partial_out = c->partial;
     LAUNCH(c, KID_GEMM, st, rc = launch_gemm_sa(ga, c->num_sms, st));

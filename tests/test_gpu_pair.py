@@ -46,13 +46,17 @@ def test_pair_matmul_SA_matches_oracle(n, logq, items, stored):
     assert ctx.device_error() == 0
 
 
-def test_pair_exact_at_worst_case_limbs():
-    n, logq, items, clip = 976, 16, 40, 10
+@pytest.mark.parametrize("n,items,clip,sigma,B", [(976, 40, 10, 2.3, 3), (4096, 16, 12, 2.8, 2)])
+def test_pair_exact_at_worst_case_limbs(n, items, clip, sigma, B):
+    """A = 0x8080 (limbs -128, -127) against S = +-c: the largest partial
+    sums, on the short-K fold (n = 976: below 2^22) and on the general one
+    (n = 4096: above 2^22)."""
+    logq = 16
     k = 8 * items
     A_o = np.full((n, n), 0x8080, dtype=np.uint16)
     S = np.full((k, n), clip, dtype=np.int8)
     S[1::2] = -clip
-    ctx = _pair_ctx(lwe.Params(n=n, logq=logq, B=3, clip=clip, sigma=2.3), items)
+    ctx = _pair_ctx(lwe.Params(n=n, logq=logq, B=B, clip=clip, sigma=sigma), items)
     out = torch.empty((k, n), dtype=torch.int16, device="cuda")
     lwe.matmul_modq(lwe.SIDE_SA, dev(S), out, n, logq, A=dev(A_o.view(np.int16)), ctx=ctx)
     assert np.array_equal(as_u16(out), O.mul_SA(S, A_o, None, logq))
