@@ -142,8 +142,9 @@ LWE_DEV void aes_load_key(const uint8_t *key, uint32_t k[4]) {
   }
 }
 
-// Key expansion from the plain 256-word table in global memory, for kernels
-// that do not hold the shared tables (one key per thread, off the hot loop).
+// Key expansion from a plain 256-word T0 table (global memory, or a copy in
+// shared memory), for kernels that do not hold the rotated shared tables
+// (one key per thread, off the hot loop).
 LWE_DEV void aes_key_expand_global(const uint32_t *T0g, const uint32_t key[4], uint32_t rk[44]) {
   rk[0] = key[0];
   rk[1] = key[1];

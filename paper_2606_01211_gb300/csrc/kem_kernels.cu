@@ -262,8 +262,22 @@ __global__ void __launch_bounds__(256) k_decrypt(DecryptArgs a) {
   const uint16_t *Brow = reinterpret_cast<const uint16_t *>(ct) + (size_t)r * n;
   const int8_t *St = a.sk_ptrs ? reinterpret_cast<const int8_t *>(a.sk_ptrs[e]) : a.St;
   int acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-  for (uint32_t jc = lane; jc < n / 8; jc += 32)
-    dot8_chunk(ld_nc_u4(Brow + 8 * (size_t)jc), St, n, 8 * jc, acc);
+  // up to four 16-byte chunks of the row per lane are requested together,
+  // so a warp waits for one memory latency per 2048 bytes, not per chunk
+  const uint32_t nch = n / 8;
+  for (uint32_t base = 0; base < nch; base += 128) {
+    uint4 x[4];
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+      const uint32_t jc = base + lane + 32 * k;
+      x[k] = jc < nch ? ld_nc_u4(Brow + 8 * (size_t)jc) : make_uint4(0, 0, 0, 0);
+    }
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+      const uint32_t jc = base + lane + 32 * k;
+      if (jc < nch) dot8_chunk(x[k], St, n, 8 * jc, acc);
+    }
+  }
   warp_allreduce8(acc);
   if (lane == 0) {
     const uint32_t D = a.logq, Bb = a.B, m = (1u << D) - 1u;
@@ -576,6 +590,9 @@ __global__ void k_keygen_seeds(KeygenSeedArgs a) {
 //   Encaps: mu = H(0x4D || coins)[0 : 8 B]
 //   K' = H(pkh || mu),  seedSE' = H(0x01 || pkh || mu)[0 : 16]
 __global__ void k_derive(DeriveArgs a) {
+  __shared__ uint32_t sT0[256];  // the key expansion's S-box lookups stay on chip
+  for (uint32_t i = threadIdx.x; i < 256; i += blockDim.x) sT0[i] = g_aes_T0[i];
+  __syncthreads();
   const uint32_t e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= a.count) return;
   uint64_t s[25];
@@ -621,7 +638,7 @@ __global__ void k_derive(DeriveArgs a) {
   const uint32_t key[4] = {(uint32_t)s[0], (uint32_t)(s[0] >> 32), (uint32_t)s[1],
                            (uint32_t)(s[1] >> 32)};
   uint32_t rk[44];
-  aes_key_expand_global(g_aes_T0, key, rk);
+  aes_key_expand_global(sT0, key, rk);
   uint4 *dst = reinterpret_cast<uint4 *>(a.rk + 44 * (size_t)e);
 #pragma unroll
   for (int i = 0; i < 11; i++) dst[i] = make_uint4(rk[4 * i], rk[4 * i + 1], rk[4 * i + 2], rk[4 * i + 3]);

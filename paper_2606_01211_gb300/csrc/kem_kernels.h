@@ -118,7 +118,7 @@ struct DeriveArgs {
 };
 
 enum { TREE_DIGEST = 0, TREE_ENC_KEY = 1 };
-#define TREE_MAX_THREADS 512
+#define TREE_MAX_THREADS 448  // 14 warps
 
 // Tree hash of `count` messages of `len` bytes (item e at msgs + e*stride,
 // or msg_ptrs[e]): leaves and root in one kernel, the leaf digests kept in
