@@ -181,6 +181,22 @@ AES_PEAK_GBS = 152 * 2.070e9 * 32 / 160 * 16 / 1e9
 KECCAK_PEAK_GPERMS = 152 * 2.070e9 * 64 / (190 * 24) / 1e9
 
 
+def algorithmic_bytes(p, count):
+    """Bytes each kernel must move through HBM in one step (summed over its
+    launches), to set against the measured DRAM traffic."""
+    n = p.n
+    ct_bytes, pk_bytes = 16 * n + 128, 16 + 16 * n
+    rows = 8 * count
+    return {
+        # H(pk) once, H(c) read in Encaps and in Decaps
+        "k_tree": float(pk_bytes + 2 * count * ct_bytes),
+        # per launch: S' (bf16) + limbs + E' read; ct written (Encaps) or read (Decaps)
+        "k_gemm_tc": 2.0 * (2 * rows * n + 2 * 2 * (n + 8) * n + rows * n + count * ct_bytes),
+        # per launch: S' (bf16), E' (int8), E'' written
+        "k_noise": 2.0 * count * (2 * 8 * n + 8 * n + 64),
+    }
+
+
 def algorithmic(p, count):
     """Algorithmic work of the kernels in one step (summed over launches)."""
     n = p.n
@@ -197,6 +213,62 @@ def algorithmic(p, count):
         "k_tree": ("alu", float(keccak_perms(pk_bytes) + 2 * count * keccak_perms(ct_bytes) + count),
                    "G Keccak-f/s", 1e9),
     }
+
+
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of a step's
+# launches of a kernel, from one ncu capture of this workload (the capture
+# and its command are summarised in the named profile).  Each entry carries a
+# fingerprint of the source it was measured on: once that source changes the
+# figure no longer describes the kernel and the bench reports null.
+CSRC = os.path.join(ROOT, "paper_2606_01211_gb300", "csrc")
+TRAFFIC = {
+    # kernel: (bytes per step, launches per step, [(file, function or None)], fingerprint, profile)
+    "k_tree": (129.588480e6, 3,
+               [("kem_kernels.cu", "k_tree"), ("kem_kernels.cu", "launch_tree"), ("keccak.cuh", None)],
+               "4f1363b566d02733", "profiles/k_tree_p976.md"),
+    "k_gemm_tc": (302.765056e6, 2, [("gemm_tc.cu", None)], "a0989a5c202077cc",
+                  "profiles/k_gemm_sa2_p976.md"),
+    "k_noise": (70.732800e6, 2,
+                [("kem_kernels.cu", "k_noise"), ("kem_kernels.cu", "noise_store"),
+                 ("kem_kernels.cu", "noise_fill_table"), ("kem_kernels.cu", "launch_noise"),
+                 ("aes.cuh", None)],
+                "43372c8896e2089c", "profiles/k_noise_p976.md"),
+}
+
+
+def _function_text(text: str, name: str) -> str:
+    """The source of the first function whose signature line names `name(`,
+    up to its closing brace in column 0."""
+    i = text.find(" %s(" % name)
+    if i < 0:
+        return ""
+    start = text.rfind("\n", 0, i) + 1
+    end = text.find("\n}\n", i)
+    return text[start:end + 3] if end >= 0 else text[start:]
+
+
+def source_fingerprint(parts) -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for fname, func in parts:
+        with open(os.path.join(CSRC, fname)) as f:
+            text = f.read()
+        h.update((_function_text(text, func) if func else text).encode())
+    return h.hexdigest()[:16]
+
+
+def traffic_per_launch(kernel: str):
+    """Measured DRAM bytes per launch, or None when unmeasured or stale."""
+    t = TRAFFIC.get(kernel)
+    if not t:
+        return None
+    bytes_step, launches, parts, fp, _profile = t
+    try:
+        if source_fingerprint(parts) != fp:
+            return None
+    except OSError:
+        return None
+    return bytes_step / launches
 
 
 def max_over_ranks(x: float, dist, device) -> float:
@@ -313,7 +385,9 @@ def run_ours(args, rank, world, local_rank):
             peak = KECCAK_PEAK_GPERMS
         roof = {"bound": bound, "achieved": ach, "peak": peak, "unit": unit, "frac": ach / peak,
                 "kernel": dom, "launches_per_step": nl / args.steps,
-                "share": kernel_total[dom] / sum(kernel_total.values()), "traffic": None}
+                "share": kernel_total[dom] / sum(kernel_total.values()),
+                "algorithmic_bytes": algorithmic_bytes(p, COUNT).get(dom, 0.0) / (nl / args.steps),
+                "traffic": traffic_per_launch(dom)}
 
     # end to end through the public API: coins from pinned host memory into
     # the step's input buffer, the replayed step, both key sets back to host

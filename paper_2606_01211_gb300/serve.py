@@ -1,13 +1,16 @@
 """Continuous-batching server for the plain-LWE KEM on one GPU.
 
 Requests (KeyGen for a dimension n, Encaps or Decaps against a resident key)
-arrive open-loop; the engine groups the waiting requests of the same
-(operation, n, key), and whenever one of its slots is free it launches the
-oldest group as ONE batched library call on that slot's stream -- without
-waiting for the batches already running on the other slots, so arrivals
-are admitted while earlier work is still on the device (continuous
-batching).  Completion is observed through CUDA events; latency is measured
-from a request's arrival to the moment its batch is seen complete.
+arrive open-loop and queue per (operation, n).  Whenever one of the
+engine's slots is free it takes the queue whose head is oldest and launches
+ONE batched library call on that slot's stream: all waiting requests of one
+key when that key has many (a single-key call, where the stacked S' can use
+the tensor-core product), else the oldest requests across keys (a
+multi-key call with per-item key pointers).  It does not wait for the
+batches already running on the other slots, so arrivals are admitted while
+earlier work is still on the device (continuous batching).  Completion is
+observed through CUDA events; latency is measured from a request's arrival
+to the moment its batch is seen complete.
 
 Keys (pk, sk) stay on the device.  The expanded matrix A of a key is kept
 in an LRU cache bounded by a byte budget (admission by device memory); a
