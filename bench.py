@@ -2,7 +2,8 @@
 
 Workload (one step): one P976 public key (n = 976, q = 2^16, sigma = 2.3,
 c = 10, B = 3), 4096 Encaps against it (stacked S' on the tensor-core path)
-followed by the 4096 matching Decaps.  Inputs (keys, expanded A, the coins of
+followed by the 4096 matching Decaps, captured once as a CUDA graph and
+replayed with each step's coins.  Inputs (keys, expanded A, the coins of
 every step) are resident in HBM before the timed region; L2 is flushed
 between timed steps.  value = Encaps+Decaps pairs per second over all ranks.
 
@@ -137,6 +138,8 @@ def run_reference(args, rank, world):
     steps = []
     total_pairs = 0
     threads = 1
+    if args.ref_step_s is None:
+        args.ref_step_s = min(8.0, 150.0 / (args.warmup + args.steps))
     for i in range(args.warmup + args.steps):
         rate, threads, pairs, el = cpu_oracle_rate(target_s=args.ref_step_s)
         if i >= args.warmup:
@@ -314,13 +317,12 @@ def run_ours(args, rank, world, local_rank):
         import torch.distributed as dist_
         dist = dist_
         dist.barrier()
+
+    # (1) direct launches with CUDA events around every kernel on its launch
+    # stream: the per-kernel times of the roofline
     torch.cuda.synchronize()
     kem.ctx.set_option(lwe.OPT_TIMING, 1)
     kem.ctx.reset_stats()
-    launches0 = kem.ctx.launches()
-    clk = ClockSampler(local_rank)
-    clk.start()
-    step_ms = []
     evs = []
     for i in range(args.warmup, nsteps):
         flush.fill_(i)  # L2 flush, outside the timed events
@@ -332,12 +334,41 @@ def run_ours(args, rank, world, local_rank):
         b.record(stream)
         evs.append((a, b))
     torch.cuda.synchronize()
-    clocks = clk.stop()
-    step_ms = [a.elapsed_time(b) for a, b in evs]
+    direct_ms = sum(a.elapsed_time(b) for a, b in evs)
     stats = kem.ctx.kernel_stats()
     kem.ctx.set_option(lwe.OPT_TIMING, 0)
-    launches = kem.ctx.launches() - launches0
-    tot_ms = sum(step_ms)
+    assert torch.equal(kem.K, kem.K2), "decapsulated keys differ from the encapsulated keys"
+    if dist is not None:
+        direct_ms = max_over_ranks(direct_ms, dist, dev)
+    direct_value = world * COUNT * args.steps / (direct_ms / 1e3)
+
+    # (2) the timed region: the step captured once as a CUDA graph (the
+    # workload is defined graph-captured) and replayed with each step's
+    # coins; W untimed replays, then K timed ones between barriers
+    kem.capture()
+    for i in range(args.warmup):
+        kem.replay(cs_all[i])
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    launches0 = kem.ctx.launches()
+    clk = ClockSampler(local_rank)
+    clk.start()
+    evs = []
+    for i in range(args.warmup, nsteps):
+        flush.fill_(i)  # L2 flush, outside the timed events
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        kem.replay(cs_all[i])
+        b.record(stream)
+        evs.append((a, b))
+    torch.cuda.synchronize()
+    clocks = clk.stop()
+    tot_ms = sum(a.elapsed_time(b) for a, b in evs)
+    # kernels launched by the replays (the graph's nodes, counted at capture)
+    launches = kem.launches_per_step * args.steps + (kem.ctx.launches() - launches0)
     if dist is not None:
         tot_ms = max_over_ranks(tot_ms, dist, dev)
         dist.barrier()
@@ -345,30 +376,37 @@ def run_ours(args, rank, world, local_rank):
     err = kem.ctx.device_error()
     value = world * COUNT * args.steps / (tot_ms / 1e3)
 
-    # the same step replayed from a CUDA graph (one launch per step)
-    graph_value = None
-    if not args.no_plain:
-        kem.capture()
+    # (3) end to end through the public API: each step's coins from pinned
+    # host memory into the graph's input buffer, the replayed step, both key
+    # sets back to pinned host memory, all inside the host-timed region
+    e2e = None
+    if not args.no_e2e:
+        hc = torch.from_numpy(coins(COUNT, seed=99)).pin_memory()
+        hK = torch.empty((COUNT, 32), dtype=torch.uint8).pin_memory()
+        hK2 = torch.empty_like(hK).pin_memory()
         ts = []
         for i in range(args.warmup + args.steps):
-            flush.fill_(i)
-            a = torch.cuda.Event(enable_timing=True)
-            b = torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            kem.replay(cs_all[i])
-            b.record(stream)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            kem.replay(hc)
+            hK.copy_(kem.K, non_blocking=True)
+            hK2.copy_(kem.K2, non_blocking=True)
             torch.cuda.synchronize()
             if i >= args.warmup:
-                ts.append(a.elapsed_time(b))
-        assert torch.equal(kem.K, kem.K2)
-        graph_value = world * COUNT * len(ts) / (sum(ts) / 1e3)
+                ts.append(time.perf_counter() - t0)
+        assert torch.equal(hK, hK2)
+        t_e2e = sum(ts)
+        if dist is not None:
+            t_e2e = max_over_ranks(t_e2e, dist, dev)
+        e2e = {"value": world * COUNT * len(ts) / t_e2e, "unit": UNIT,
+               "h2d_bytes_per_step": COUNT * 32, "d2h_bytes_per_step": 2 * COUNT * 32}
 
     if rank != 0:
         kem.close()
         return 0
 
-    # roofline of the dominant kernel (largest share of the timed region):
-    # algorithmic work of the timed steps / the kernel's summed event time
+    # roofline of the dominant kernel (largest share of the step): its
+    # algorithmic work over the direct-launch steps / its summed event time
     kernel_total = {k: v[1] for k, v in stats.items()}
     dom = max(kernel_total, key=kernel_total.get)
     alg = algorithmic(p, COUNT)
@@ -387,29 +425,8 @@ def run_ours(args, rank, world, local_rank):
                 "kernel": dom, "launches_per_step": nl / args.steps,
                 "share": kernel_total[dom] / sum(kernel_total.values()),
                 "algorithmic_bytes": algorithmic_bytes(p, COUNT).get(dom, 0.0) / (nl / args.steps),
-                "traffic": traffic_per_launch(dom)}
-
-    # end to end through the public API: coins from pinned host memory into
-    # the step's input buffer, the replayed step, both key sets back to host
-    e2e = None
-    if not args.no_e2e:
-        hc = torch.from_numpy(coins(COUNT, seed=99)).pin_memory()
-        hK = torch.empty((COUNT, 32), dtype=torch.uint8).pin_memory()
-        hK2 = torch.empty_like(hK).pin_memory()
-        ts = []
-        for i in range(args.warmup + args.steps):
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            kem.coins.copy_(hc, non_blocking=True)
-            kem.step()
-            hK.copy_(kem.K, non_blocking=True)
-            hK2.copy_(kem.K2, non_blocking=True)
-            torch.cuda.synchronize()
-            if i >= args.warmup:
-                ts.append(time.perf_counter() - t0)
-        assert torch.equal(hK, hK2)
-        e2e = {"value": COUNT / statistics.mean(ts), "unit": UNIT,
-               "h2d_bytes_per_step": COUNT * 32, "d2h_bytes_per_step": 2 * COUNT * 32}
+                "traffic": traffic_per_launch(dom),
+                "timing": "CUDA events around each launch of the direct-launch steps"}
 
     # the same step with direct launches (no graph), and on the plain
     # per-request path (CUDA cores, one item per row of CTAs)
@@ -450,7 +467,7 @@ def run_ours(args, rank, world, local_rank):
         "scaling": "weak", "vs_baseline": None, "dtype": "u16",
         "data": "synthetic (seeded random keys and coins)",
         "config": {"workload": WORKLOAD, "n": p.n, "batch": COUNT, "path": "tensor",
-                   "launch": "direct launches (graph replay reported as graph_value)",
+                   "launch": "CUDA graph replay of the captured step (direct launches: direct_value)",
                    "l2": "flushed between timed steps (256 MiB write), per-step CUDA events",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "gpu_launches": launches,
@@ -458,7 +475,7 @@ def run_ours(args, rank, world, local_rank):
         "cpu_baseline": cpu,
         "e2e": e2e,
         "clocks": clocks,
-        "graph_value": graph_value,
+        "direct_value": direct_value,
         "plain_path_value": plain,
         "batched_vs_plain": (value / world / plain) if plain else None,
         "kernels_ms_per_step": {k: v[1] / args.steps for k, v in stats.items()},
@@ -572,7 +589,8 @@ def main():
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-sweep", action="store_true")
     ap.add_argument("--cpu-s", type=float, default=12.0)
-    ap.add_argument("--ref-step-s", type=float, default=8.0)
+    ap.add_argument("--ref-step-s", type=float, default=None,
+                    help="CPU seconds per reference step (default: about 150 s in all)")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
