@@ -136,10 +136,15 @@ enum {
   LWE_OPT_GEMM_BN = 3,       /* single-CTA GEMM column tile: 64 or 128 (def.) */
   LWE_OPT_GEMM_KCHUNK = 4,   /* K per tensor-core pass: a multiple of 64 up to
                                 the exact bound (2^24-1)/(128 c); 0 = bound   */
-  LWE_OPT_GEMM_PAIR = 5      /* 1 (default): the GEMM runs on CTA pairs (two
+  LWE_OPT_GEMM_PAIR = 5,     /* 1 (default): the GEMM runs on CTA pairs (two
                                 SMs share a 256 x 128 tile, tcgen05
                                 cta_group::2; LWE_OPT_GEMM_BN is then
                                 ignored); 0: one CTA per 128 x BN tile        */
+  LWE_OPT_SERIAL = 6         /* 1: work that normally overlaps on the
+                                context's side stream (the tensor path's
+                                limbs, Decaps' H(c)) runs on the caller's
+                                stream, so that per-kernel timings measure
+                                each kernel alone; 0 (default): overlapped   */
 };
 int lwe_ctx_set_option(lwe_ctx *ctx, int option, int64_t value);
 

@@ -153,6 +153,7 @@ struct lwe_ctx {
   int tensor_min = 64;
   int gemm_bn = 128;
   int gemm_pair = 1;
+  bool serial = false;  // LWE_OPT_SERIAL: side-stream work on the caller's stream
   bool timing = false;
   uint64_t launches = 0;
   std::vector<TimedLaunch> pending;
@@ -176,7 +177,7 @@ struct lwe_ctx {
   bool has_tensor = false;
   // side stream for work independent of the re-encryption (Decaps' H(c))
   cudaStream_t side = nullptr;
-  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_limbs = nullptr;
 };
 
 namespace {
@@ -309,15 +310,39 @@ struct ItemKeys {
   const uint16_t *const *A_ptrs = nullptr;
 };
 
-int run_encrypt(lwe_ctx *c, const uint8_t *pk, const uint16_t *A, uint32_t count, uint8_t *ct,
-                bool cmp, cudaStream_t st, const ItemKeys *ik = nullptr) {
-  const uint32_t n = c->p.n;
+// The stream for work that does not depend on the main chain (the tensor
+// path's limbs, Decaps' H(c)): the context's side stream, or the caller's
+// stream when LWE_OPT_SERIAL is set.
+cudaStream_t side_stream(const lwe_ctx *c, cudaStream_t st) { return c->serial ? st : c->side; }
+
+// Whether a call of `count` items runs its product on the tensor cores.
+bool use_tensor(const lwe_ctx *c, uint32_t count, const ItemKeys *ik) {
   bool tensor = false;
   if (c->path == LWE_PATH_TENSOR)
     tensor = true;
   else if (c->path == LWE_PATH_AUTO)
     tensor = (int)count >= c->tensor_min;
-  tensor = tensor && c->has_tensor && !ik;  // one GEMM needs one shared A
+  return tensor && c->has_tensor && !ik;  // one GEMM needs one shared A
+}
+
+// The GEMM's B operand: limbs of the columns of [A | B] (A stored, or
+// regenerated from seedA = pk[0:16]).  Depends on the key only.
+void launch_limbs(lwe_ctx *c, const uint8_t *pk, const uint16_t *A, cudaStream_t st) {
+  GemmLimbArgs la;
+  la.A = A;
+  la.seedA = pk;
+  la.B = pk + 16;
+  la.n = c->p.n;
+  la.logq = c->p.logq;
+  la.limbs = c->limbs;
+  LAUNCH(c, KID_LIMBS, st, launch_gemm_limbs(la, c->num_sms, st));
+}
+
+int run_encrypt(lwe_ctx *c, const uint8_t *pk, const uint16_t *A, uint32_t count, uint8_t *ct,
+                bool cmp, cudaStream_t st, const ItemKeys *ik = nullptr,
+                bool limbs_on_side = false) {
+  const uint32_t n = c->p.n;
+  const bool tensor = use_tensor(c, count, ik);
 
   NoiseArgs na = noise_args(c, count);
   na.nout = 3;
@@ -331,14 +356,10 @@ int run_encrypt(lwe_ctx *c, const uint8_t *pk, const uint16_t *A, uint32_t count
   LAUNCH(c, KID_NOISE, st, launch_noise(na, c->num_sms, st));
 
   if (tensor) {
-    GemmLimbArgs la;
-    la.A = A;
-    la.seedA = pk;
-    la.B = pk + 16;
-    la.n = n;
-    la.logq = c->p.logq;
-    la.limbs = c->limbs;
-    LAUNCH(c, KID_LIMBS, st, launch_gemm_limbs(la, c->num_sms, st));
+    if (limbs_on_side)  // made on the side stream by the caller
+      CUDA_TRY(cudaStreamWaitEvent(st, c->ev_limbs, 0));
+    else
+      launch_limbs(c, pk, A, st);
     GemmSaArgs ga;
     memset(&ga, 0, sizeof ga);
     ga.S = c->spbf;
@@ -592,12 +613,14 @@ int lwe_ctx_create(const lwe_params *p, uint32_t max_batch, int device, lwe_ctx 
   e = cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_limbs, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaMemset(c->ws, 0, c->ws_bytes);
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
   cudaSetDevice(prev);
   if (e != cudaSuccess) {
     if (c->ev_fork) cudaEventDestroy(c->ev_fork);
     if (c->ev_join) cudaEventDestroy(c->ev_join);
+    if (c->ev_limbs) cudaEventDestroy(c->ev_limbs);
     if (c->side) cudaStreamDestroy(c->side);
     cudaFree(c->ws);
     delete c;
@@ -624,6 +647,7 @@ int lwe_ctx_destroy(lwe_ctx *c) {
   for (auto e : c->free_events) cudaEventDestroy(e);
   if (c->ev_fork) cudaEventDestroy(c->ev_fork);
   if (c->ev_join) cudaEventDestroy(c->ev_join);
+  if (c->ev_limbs) cudaEventDestroy(c->ev_limbs);
   if (c->side) cudaStreamDestroy(c->side);
   cudaFree(c->ws);
   cudaSetDevice(prev);
@@ -649,6 +673,9 @@ int lwe_ctx_set_option(lwe_ctx *c, int option, int64_t value) {
     case LWE_OPT_GEMM_BN:
       if (value != 64 && value != 128) return LWE_EINVAL;
       c->gemm_bn = (int)value;
+      return LWE_OK;
+    case LWE_OPT_SERIAL:
+      c->serial = value != 0;
       return LWE_OK;
     case LWE_OPT_GEMM_PAIR:
       if (value != 0 && value != 1) return LWE_EINVAL;
@@ -734,11 +761,21 @@ int lwe_encaps(lwe_ctx *c, const uint8_t *pk, const uint16_t *A, const uint8_t *
   const lwe_params &p = c->p;
   const size_t pkb = pk_bytes(p), ctb = ct_bytes(p);
 
+  // tensor path: the limbs of [A | B] are made on the side stream while
+  // the main stream hashes pk (one message: a latency-bound launch)
+  const bool side = use_tensor(c, count, nullptr);
+  if (side) {
+    cudaStream_t ss = side_stream(c, st);
+    CUDA_TRY(cudaEventRecord(c->ev_fork, st));
+    CUDA_TRY(cudaStreamWaitEvent(ss, c->ev_fork, 0));
+    launch_limbs(c, pk, A, ss);
+    CUDA_TRY(cudaEventRecord(c->ev_limbs, ss));
+  }
   rc = hash_tree(c, pk, pkb, (uint32_t)pkb, 1, TREE_DIGEST, c->pkh, 32, nullptr, 0, st);
   if (rc) return rc;
   DeriveArgs da = derive_args(c, coins, c->pkh, count);
   LAUNCH(c, KID_DERIVE, st, launch_derive(da, st));
-  rc = run_encrypt(c, pk, A, count, ct, false, st);
+  rc = run_encrypt(c, pk, A, count, ct, false, st, nullptr, side);
   if (rc) return rc;
   return hash_tree(c, ct, ctb, (uint32_t)ctb, count, TREE_ENC_KEY, K, 32, nullptr, 0, st);
 }
@@ -763,16 +800,23 @@ int lwe_decaps(lwe_ctx *c, const uint8_t *sk, const uint16_t *A, const uint8_t *
 
   CUDA_TRY(cudaMemsetAsync(c->flags, 0, 4 * (size_t)count, st));
   // H(c) does not depend on the re-encryption: it runs on the side stream,
-  // overlapping the re-encryption, and joins before the key selection
+  // overlapping the re-encryption, and joins before the key selection (the
+  // tensor path's limbs go first on that stream)
+  cudaStream_t ss = side_stream(c, st);
   CUDA_TRY(cudaEventRecord(c->ev_fork, st));
-  CUDA_TRY(cudaStreamWaitEvent(c->side, c->ev_fork, 0));
-  tree_hash(c, ct, ctb, (uint32_t)ctb, count, TREE_DIGEST, c->hc, 32, nullptr, 0, c->side);
-  CUDA_TRY(cudaEventRecord(c->ev_join, c->side));
+  CUDA_TRY(cudaStreamWaitEvent(ss, c->ev_fork, 0));
+  const bool side = use_tensor(c, count, nullptr);
+  if (side) {
+    launch_limbs(c, pk, A, ss);
+    CUDA_TRY(cudaEventRecord(c->ev_limbs, ss));
+  }
+  tree_hash(c, ct, ctb, (uint32_t)ctb, count, TREE_DIGEST, c->hc, 32, nullptr, 0, ss);
+  CUDA_TRY(cudaEventRecord(c->ev_join, ss));
   DecryptArgs dca = decrypt_args(c, ct, reinterpret_cast<const int8_t *>(sk), nullptr);
   LAUNCH(c, KID_DECRYPT, st, launch_decrypt(dca, count, st));
   DeriveArgs da = derive_args(c, nullptr, pkh, count);
   LAUNCH(c, KID_DERIVE, st, launch_derive(da, st));
-  rc = run_encrypt(c, pk, A, count, const_cast<uint8_t *>(ct), true, st);
+  rc = run_encrypt(c, pk, A, count, const_cast<uint8_t *>(ct), true, st, nullptr, side);
   if (rc) return rc;
   CUDA_TRY(cudaStreamWaitEvent(st, c->ev_join, 0));
   final_key(c, z, nullptr, 0, count, K, st);
@@ -829,9 +873,10 @@ int lwe_decaps_multi(lwe_ctx *c, const uint8_t *const *sk_ptrs, const uint16_t *
   const size_t ctb = ct_bytes(p);
   CUDA_TRY(cudaMemsetAsync(c->flags, 0, 4 * (size_t)count, st));
   CUDA_TRY(cudaEventRecord(c->ev_fork, st));
-  CUDA_TRY(cudaStreamWaitEvent(c->side, c->ev_fork, 0));
-  tree_hash(c, ct, ctb, (uint32_t)ctb, count, TREE_DIGEST, c->hc, 32, nullptr, 0, c->side);
-  CUDA_TRY(cudaEventRecord(c->ev_join, c->side));
+  cudaStream_t ss = side_stream(c, st);
+  CUDA_TRY(cudaStreamWaitEvent(ss, c->ev_fork, 0));
+  tree_hash(c, ct, ctb, (uint32_t)ctb, count, TREE_DIGEST, c->hc, 32, nullptr, 0, ss);
+  CUDA_TRY(cudaEventRecord(c->ev_join, ss));
   DecryptArgs dca = decrypt_args(c, ct, nullptr, sk_ptrs);
   LAUNCH(c, KID_DECRYPT, st, launch_decrypt(dca, count, st));
   DeriveArgs da = derive_args(c, nullptr, nullptr, count);

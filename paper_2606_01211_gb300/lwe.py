@@ -26,7 +26,8 @@ LWE_EUNSUPPORTED = -5
 LWE_ECAPACITY = -6
 
 PATH_AUTO, PATH_SKINNY, PATH_TENSOR = 0, 1, 2
-OPT_PATH, OPT_TENSOR_MIN, OPT_TIMING, OPT_GEMM_BN, OPT_GEMM_KCHUNK, OPT_GEMM_PAIR = 0, 1, 2, 3, 4, 5
+(OPT_PATH, OPT_TENSOR_MIN, OPT_TIMING, OPT_GEMM_BN, OPT_GEMM_KCHUNK, OPT_GEMM_PAIR,
+ OPT_SERIAL) = 0, 1, 2, 3, 4, 5, 6
 SIDE_AS, SIDE_SA = 0, 1
 PRESET_IDS = {"P640": 0, "P976": 1, "P1344": 2, "P4096": 3, "P16384": 4, "P32768": 5}
 

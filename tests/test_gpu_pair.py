@@ -139,3 +139,27 @@ def test_pair_batched_4096_equals_single_cta_and_oracle_samples():
         assert np.array_equal(res[1][0][i], ct_o), i
         assert np.array_equal(res[1][1][i], K_o), i
     assert ctx.device_error() == 0
+
+
+def test_serial_option_gives_the_same_results():
+    """LWE_OPT_SERIAL (side-stream work on the caller's stream) changes the
+    schedule only."""
+    name, count = "P976", 40
+    p, _ = params(name)
+    ctx = lwe.Ctx(p, max_batch=count)
+    ctx.set_path(lwe.PATH_TENSOR)
+    pk, sk = ctx.empty_pk(1), ctx.empty_sk(1)
+    ctx.keygen(dev(master_seeds(1, seed=3)), pk, sk)
+    cs = dev(coins(count, seed=33))
+    out = []
+    for serial in (0, 1):
+        ctx.set_option(lwe.OPT_SERIAL, serial)
+        ct = ctx.empty_ct(count)
+        K = torch.empty((count, 32), dtype=torch.uint8, device="cuda")
+        ctx.encaps(pk, cs, ct, K)
+        K2 = torch.empty_like(K)
+        ctx.decaps(sk, ct, K2)
+        out.append((host(ct), host(K), host(K2)))
+    for a, b in zip(*out):
+        assert np.array_equal(a, b)
+    assert np.array_equal(out[0][1], out[0][2])
