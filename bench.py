@@ -457,7 +457,8 @@ def run_ours(args, rank, world, local_rank):
 
     served = None if args.no_serve else serve_measure(torch)
     latency = None if args.no_latency else single_request_latency(lwe, torch, dev)
-    as_sweep = None if args.no_sweep else as_gbs_sweep(lwe, torch, dev, flush)
+    sweep = None if args.no_sweep else kernel_sweep(lwe, torch, dev, flush)
+    large = None if args.no_large else large_n(lwe, torch, dev)
 
     cpu = None
     if not args.no_cpu:
@@ -487,7 +488,9 @@ def run_ours(args, rank, world, local_rank):
                      "tensor_min": tuned["tensor_min"]},
         "served": served,
         "latency_p640_us": latency,
-        "as_gbs": as_sweep,
+        "as_gbs": sweep["AS_stored"] if sweep else None,
+        "kernel_sweep": sweep,
+        "large_n": large,
         "correct": bool(ok) and err == 0,
     }
     print(json.dumps(line))
@@ -553,31 +556,96 @@ def single_request_latency(lwe, torch, dev, reps: int = 300):
             for k, v in t.items()}
 
 
-def as_gbs_sweep(lwe, torch, dev, flush, sizes=(1344, 2048, 4096, 8192), reps: int = 5):
-    """lwe_matmul_modq A S (stored A, n x 8 secret): bytes of A read per
-    second, L2 flushed before every timed call."""
-    out = {}
+def _event_ms(torch, stream, fn, flush=None, reps: int = 5) -> float:
+    """Median CUDA-event time of fn() on the stream (after one untimed
+    call); L2 flushed before every call when a flush buffer is given."""
+    ts = []
+    for r in range(reps + 1):
+        if flush is not None:
+            flush.fill_(r)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        if r:
+            ts.append(a.elapsed_time(b))
+    return statistics.median(ts)
+
+
+def kernel_sweep(lwe, torch, dev, flush, sizes=(1344, 2048, 4096, 8192)):
+    """Standalone hot kernels over n (L2 flushed before every timed call):
+    lwe_expand_A (bytes of A written per second), and lwe_matmul_modq A S
+    and S A for one n x 8 secret with A stored (bytes of A read per second)
+    or regenerated inside the kernel (bytes of A's keystream per second)."""
+    out = {k: {} for k in ("expand_A", "AS_stored", "AS_fused", "SA_stored", "SA_fused")}
     stream = torch.cuda.current_stream()
     for n in sizes:
         A = torch.empty((n, n), dtype=torch.int16, device=dev)
         seed = torch.arange(16, dtype=torch.uint8, device=dev)
-        lwe.expand_A(seed, n, 16, A)
         St = torch.randint(-6, 7, (8, n), dtype=torch.int8, device=dev)
-        o = torch.empty((n, 8), dtype=torch.int16, device=dev)
-        ts = []
-        for r in range(reps + 1):
-            flush.fill_(r)
-            a = torch.cuda.Event(enable_timing=True)
-            b = torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            lwe.matmul_modq(lwe.SIDE_AS, St, o, n, 16, A=A)
-            b.record(stream)
-            torch.cuda.synchronize()
-            if r:
-                ts.append(a.elapsed_time(b) / 1e3)
-        out[str(n)] = 2.0 * n * n / statistics.median(ts) / 1e9
+        o_as = torch.empty((n, 8), dtype=torch.int16, device=dev)
+        o_sa = torch.empty((8, n), dtype=torch.int16, device=dev)
+        gb = 2.0 * n * n / 1e9
+        out["expand_A"][str(n)] = gb / (_event_ms(torch, stream, lambda: lwe.expand_A(seed, n, 16, A),
+                                                  flush) / 1e3)
+        out["AS_stored"][str(n)] = gb / (_event_ms(
+            torch, stream, lambda: lwe.matmul_modq(lwe.SIDE_AS, St, o_as, n, 16, A=A), flush) / 1e3)
+        out["AS_fused"][str(n)] = gb / (_event_ms(
+            torch, stream, lambda: lwe.matmul_modq(lwe.SIDE_AS, St, o_as, n, 16, seedA=seed), flush) / 1e3)
+        out["SA_stored"][str(n)] = gb / (_event_ms(
+            torch, stream, lambda: lwe.matmul_modq(lwe.SIDE_SA, St, o_sa, n, 16, A=A), flush) / 1e3)
+        out["SA_fused"][str(n)] = gb / (_event_ms(
+            torch, stream, lambda: lwe.matmul_modq(lwe.SIDE_SA, St, o_sa, n, 16, seedA=seed), flush) / 1e3)
         del A
+    out["unit"] = "GB/s (bytes of A written, read or generated)"
     return out
+
+
+def large_n(lwe, torch, dev, batch: int = 1024):
+    """n = 16384 and 32768 (A = 0.5 / 2 GiB): one KeyGen, Encaps and Decaps
+    per call with A stored in HBM vs regenerated tile by tile inside the
+    kernels (CUDA-core path), and Encaps of `batch` items against one key
+    on the tensor path (K split into exact passes).  CUDA-event ms per call
+    (median of 3); the batched figure also as Encaps/s."""
+    stream = torch.cuda.current_stream()
+    res = {}
+    for name in ("P16384", "P32768"):
+        p = lwe.Params(**PRESETS[name])
+        n = p.n
+        ctx = lwe.Ctx(p, max_batch=batch, device=dev.index)
+        ms = torch.from_numpy(master_seeds(1, seed=3)).to(dev)
+        cs = torch.from_numpy(coins(batch, seed=3)).to(dev)
+        pk, sk = ctx.empty_pk(1), ctx.empty_sk(1)
+        A = torch.empty((n, n), dtype=torch.int16, device=dev)
+        ct = ctx.empty_ct(batch)
+        K = torch.empty((batch, 32), dtype=torch.uint8, device=dev)
+        K2 = torch.empty_like(K)
+        r = {}
+        ctx.set_path(lwe.PATH_SKINNY)
+        for mode, Ak in (("stored", A), ("fused", None)):
+            r["keygen_" + mode] = _event_ms(torch, stream, lambda: ctx.keygen(ms, pk, sk, A_out=Ak),
+                                            reps=3)
+            r["encaps_" + mode] = _event_ms(torch, stream, lambda: ctx.encaps(pk, cs[:1], ct[:1], K[:1],
+                                                                               A=Ak), reps=3)
+            r["decaps_" + mode] = _event_ms(torch, stream, lambda: ctx.decaps(sk, ct[:1], K2[:1], A=Ak),
+                                            reps=3)
+            assert torch.equal(K[:1], K2[:1])
+        ctx.keygen(ms, pk, sk, A_out=A)
+        ctx.set_path(lwe.PATH_TENSOR)
+        t = _event_ms(torch, stream, lambda: ctx.encaps(pk, cs, ct, K, A=A), reps=3)
+        r["encaps_batched_%d_stored" % batch] = t
+        r["encaps_batched_per_s"] = batch / (t / 1e3)
+        ctx.decaps(sk, ct, K2, A=A)
+        torch.cuda.synchronize()
+        assert torch.equal(K, K2)
+        res[name] = r
+        ctx.close()
+        del A
+        torch.cuda.empty_cache()
+    res["unit"] = "ms per call"
+    return res
 
 
 def main():
@@ -592,6 +660,7 @@ def main():
     ap.add_argument("--no-latency", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-sweep", action="store_true")
+    ap.add_argument("--no-large", action="store_true")
     ap.add_argument("--cpu-s", type=float, default=12.0)
     ap.add_argument("--ref-step-s", type=float, default=None,
                     help="CPU seconds per reference step (default: about 150 s in all)")

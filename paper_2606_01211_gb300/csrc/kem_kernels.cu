@@ -7,9 +7,9 @@
 //                   counter streams.
 //   k_mul_as        B = A S + E of Alg. 1 (A stored or regenerated).
 //   k_decrypt       M = C - B' S and mu' = Dec(M) of Alg. 3.
-//   k_mul_sa        B' = S' A + E' of Alg. 2, one encryption per CTA row,
-//                   stored A; with a compare epilogue for Alg. 5.
-//   k_mul_sa_fused  the same with A regenerated from its seed in-CTA.
+//   k_sa            B' = S' A + E' of Alg. 2 on the CUDA cores (A stored or
+//                   regenerated from its seed in-CTA), with a compare
+//                   epilogue for Alg. 5.
 //   k_v_encode      V = S' B + E'', C = V + Enc(mu) of Alg. 2 (or compare).
 //   k_keygen_seeds, k_derive, k_tree, k_final_key: the hashing of
 //                   Alg. 4-5 (SHA3-256) and the Fujisaki-Okamoto selection.
@@ -252,6 +252,90 @@ __global__ void __launch_bounds__(256) k_mul_as(MulAsArgs a) {
   }
 }
 
+// A S + E with stored A (KeyGen, Alg. 1).  A warp computes AS_ROWS rows of
+// A together, so every 64-byte chunk of S^T it loads serves AS_ROWS rows,
+// and keeps two 16-byte chunks of each row in flight per lane (A streams
+// past L1; S^T stays there).  The 8 AS_ROWS partial sums of a lane are
+// reduced across the warp by recursive halving, which leaves lane L with
+// output L = (row L / 8, column L % 8) for one coalesced store.
+#define AS_ROWS 4
+
+LWE_DEV uint4 ld_stream_u4(const void *p) {
+  uint4 v;
+  asm("ld.global.nc.L1::no_allocate.v4.u32 {%0, %1, %2, %3}, [%4];"
+      : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+      : "l"(p));
+  return v;
+}
+
+LWE_DEV void dot8_rows(const uint4 *x, const int8_t *__restrict__ St, uint32_t n, uint32_t j,
+                       int acc[AS_ROWS][8]) {
+#pragma unroll
+  for (int l = 0; l < 8; l++) {
+    const uint2 s = ld_nc_u2(St + (size_t)l * n + j);
+#pragma unroll
+    for (int r = 0; r < AS_ROWS; r++) {
+      acc[r][l] = __dp2a_lo((int)x[r].x, (int)s.x, acc[r][l]);
+      acc[r][l] = __dp2a_hi((int)x[r].y, (int)s.x, acc[r][l]);
+      acc[r][l] = __dp2a_lo((int)x[r].z, (int)s.y, acc[r][l]);
+      acc[r][l] = __dp2a_hi((int)x[r].w, (int)s.y, acc[r][l]);
+    }
+  }
+}
+
+// Row groups (tasks) are dealt out task = CTA + grid * (warp + 8 k), so
+// that with a grid of two CTAs per SM every SM streams the same share of A.
+__global__ void __launch_bounds__(256) k_mul_as_rows(MulAsArgs a) {
+  const uint32_t e = blockIdx.y;
+  const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t n = a.n, nch = n / 8;
+  const uint32_t tasks = n / AS_ROWS;  // n is a multiple of AS_ROWS
+  const int8_t *St = a.St + (size_t)e * a.st_stride;
+  for (uint32_t task = blockIdx.x + gridDim.x * warp; task < tasks; task += gridDim.x * 8) {
+  const uint32_t i0 = task * AS_ROWS;
+  const uint16_t *A0 = a.A + (size_t)e * a.a_stride + (size_t)i0 * n;
+  int acc[AS_ROWS][8];
+#pragma unroll
+  for (int r = 0; r < AS_ROWS; r++)
+#pragma unroll
+    for (int l = 0; l < 8; l++) acc[r][l] = 0;
+  for (uint32_t jc = lane; jc < nch; jc += 64) {
+    const bool two = jc + 32 < nch;
+    uint4 x0[AS_ROWS], x1[AS_ROWS];
+#pragma unroll
+    for (int r = 0; r < AS_ROWS; r++) x0[r] = ld_stream_u4(A0 + (size_t)r * n + 8 * (size_t)jc);
+#pragma unroll
+    for (int r = 0; r < AS_ROWS; r++)
+      x1[r] = two ? ld_stream_u4(A0 + (size_t)r * n + 8 * (size_t)(jc + 32)) : make_uint4(0, 0, 0, 0);
+    dot8_rows(x0, St, n, 8 * jc, acc);
+    if (two) dot8_rows(x1, St, n, 8 * (jc + 32), acc);
+  }
+  // recursive halving: at offset o a lane keeps the half of its values
+  // selected by lane bit o and adds the partner's copy of that half
+  int v[32];
+#pragma unroll
+  for (int r = 0; r < AS_ROWS; r++)
+#pragma unroll
+    for (int l = 0; l < 8; l++) v[8 * r + l] = acc[r][l];
+#pragma unroll
+  for (int o = 16; o >= 1; o >>= 1) {
+    const bool up = (lane & o) != 0;
+#pragma unroll
+    for (int j = 0; j < o; j++) {
+      const int send = up ? v[j] : v[j + o];
+      const int keep = up ? v[j + o] : v[j];
+      v[j] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+    }
+  }
+  const uint32_t r = lane >> 3, l = lane & 7, i = i0 + r;
+  const uint32_t m = (1u << a.logq) - 1u;
+  const int ev = a.E ? (int)a.E[(size_t)e * a.e_stride + (size_t)i * 8 + l] : 0;
+  const uint16_t val = (uint16_t)((uint32_t)(v[0] + ev) & m);
+  reinterpret_cast<uint16_t *>(a.out + (size_t)e * a.out_stride + 16 * (size_t)i)[l] = val;
+  if (a.out2) reinterpret_cast<uint16_t *>(a.out2 + (size_t)e * a.out2_stride + 16 * (size_t)i)[l] = val;
+  }
+}
+
 // Decrypt (Alg. 3): warp r of CTA e computes row r of M = C - B' S and the
 // B message bits of its eight coefficients.
 __global__ void __launch_bounds__(256) k_decrypt(DecryptArgs a) {
@@ -294,186 +378,158 @@ __global__ void __launch_bounds__(256) k_decrypt(DecryptArgs a) {
   }
 }
 
-// ---------------------------------------------------------------------------
-// S' A (+ E') with stored A.  CTA (column block of 64, item e); warp w takes
-// rows i = w (mod 8); lane l takes columns j0 + 2l, j0 + 2l + 1.
-// ---------------------------------------------------------------------------
-#define SA_CH 512
+// S' A (+ E') for one or more items on the CUDA cores (Alg. 2), A stored
+// (LDG.128 of 8 columns per row) or regenerated (one AES block per row and
+// 8 columns, the counter layout of A).  CTA = (256-column block, row
+// split, item): lane l owns columns 8 l .. 8 l + 7 of the block, warp w the
+// row pairs (2p, 2p + 1) with p = w (mod 8); the pair's S' bytes are staged
+// in shared memory so that one dp2a multiplies two rows.  The warps' sums
+// meet in shared memory; when a call has few items the rows are split over
+// a cluster of R CTAs whose partial sums are added through distributed
+// shared memory, so no global workspace is needed.  Then E' is added and
+// the row stored, or (CMP) compared with the received ciphertext.
+#define SA_PAIRS 512  // row pairs of S' staged at a time (8 KB)
 
-template <bool CMP>
-__global__ void __launch_bounds__(256) k_mul_sa(MulSaArgs a) {
-  __shared__ int4 sS[SA_CH][2];  // S'[0..7][i] for a chunk of rows
-  const uint32_t e = blockIdx.y, j0 = blockIdx.x * 64;
-  const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const uint32_t n = a.n;
-  const int8_t *S = a.S + (size_t)e * a.s_stride;
-  const uint16_t *Aitem = a.A_ptrs ? a.A_ptrs[e] : a.A;
-  const uint32_t j = j0 + 2 * lane;
-  const bool jvalid = j < n;
-  int acc[8][2];
-#pragma unroll
-  for (int k = 0; k < 8; k++) acc[k][0] = acc[k][1] = 0;
-  for (uint32_t i0 = 0; i0 < n; i0 += SA_CH) {
-    __syncthreads();
-    for (uint32_t idx = threadIdx.x; idx < SA_CH * 8; idx += blockDim.x) {
-      const uint32_t k = idx / SA_CH, ii = idx % SA_CH;
-      const int v = (i0 + ii < n) ? (int)S[(size_t)k * n + i0 + ii] : 0;
-      reinterpret_cast<int *>(&sS[ii][0])[k] = v;
-    }
-    __syncthreads();
-    const uint32_t rows = min((uint32_t)SA_CH, n - i0);
-    for (uint32_t ii = warp; ii < rows; ii += 8) {
-      uint32_t av = 0;
-      if (jvalid) av = __ldg(reinterpret_cast<const uint32_t *>(Aitem + (size_t)(i0 + ii) * n + j));
-      const int x0 = (int)(av & 0xffffu), x1 = (int)(av >> 16);
-      const int4 s0 = sS[ii][0], s1 = sS[ii][1];
-      const int s[8] = {s0.x, s0.y, s0.z, s0.w, s1.x, s1.y, s1.z, s1.w};
-#pragma unroll
-      for (int k = 0; k < 8; k++) {
-        acc[k][0] += s[k] * x0;
-        acc[k][1] += s[k] * x1;
-      }
-    }
-  }
-  // reduce the 8 warps' partial sums
-  __syncthreads();
-  int *red = reinterpret_cast<int *>(&sS[0][0]);  // [8 warps][16][32 lanes]
-#pragma unroll
-  for (int k = 0; k < 8; k++) {
-    red[(warp * 16 + 2 * k + 0) * 32 + lane] = acc[k][0];
-    red[(warp * 16 + 2 * k + 1) * 32 + lane] = acc[k][1];
-  }
-  __syncthreads();
-  {
-    const uint32_t k = warp;  // thread (k, lane) finishes row k, columns j, j+1
-    int v0 = 0, v1 = 0;
-#pragma unroll
-    for (int w = 0; w < 8; w++) {
-      v0 += red[(w * 16 + 2 * k + 0) * 32 + lane];
-      v1 += red[(w * 16 + 2 * k + 1) * 32 + lane];
-    }
-    const uint32_t m = (1u << a.logq) - 1u;
-    uint32_t diff = 0;
-    if (jvalid) {
-      if (a.E) {
-        const int8_t *E = a.E + (size_t)e * a.e_stride + (size_t)k * n + j;
-        v0 += E[0];
-        v1 += E[1];
-      }
-      const uint32_t packed = ((uint32_t)v0 & m) | (((uint32_t)v1 & m) << 16);
-      uint32_t *o = reinterpret_cast<uint32_t *>(a.out + (size_t)e * a.out_stride +
-                                                 2 * ((size_t)k * n + j));
-      if (CMP)
-        diff = packed ^ *o;
-      else
-        *o = packed;
-    }
-    if (CMP) {
-      diff = __reduce_or_sync(0xffffffffu, diff);
-      if (lane == 0 && diff) atomicOr(a.flags + e, 1u);
-    }
-  }
+LWE_DEV uint32_t cluster_map(const void *p, uint32_t rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;"
+               : "=r"(r)
+               : "r"((uint32_t)__cvta_generic_to_shared(p)), "r"(rank));
+  return r;
+}
+LWE_DEV int ld_cluster_s32(uint32_t addr) {
+  int v;
+  asm volatile("ld.shared::cluster.s32 %0, [%1];" : "=r"(v) : "r"(addr) : "memory");
+  return v;
+}
+LWE_DEV void cluster_barrier() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::
+                   : "memory");
 }
 
-// S' A (+ E') with A regenerated: thread (column block cb of 8 columns,
-// row slice rs of 32) generates A[i][j0+8cb .. +7] with one AES block per row.
-template <bool CMP>
-__global__ void __launch_bounds__(256) k_mul_sa_fused(MulSaArgs a) {
-  extern __shared__ uint32_t smem[];
-  uint32_t *sT = smem;                                           // 32 KB
-  int4 *sS = reinterpret_cast<int4 *>(smem + AES_TABLE_WORDS);  // [SA_CH][2]
-  aes_fill_smem(sT, g_aes_T0);
-  __syncthreads();
-  const AesTab tab = aes_tab(sT);
-  const uint32_t e = blockIdx.y, j0 = blockIdx.x * 64;
-  uint32_t key[4], rk[44];
-  aes_load_key(a.seed_ptrs ? a.seed_ptrs[e] + a.seed_off : a.seedA, key);
-  aes_key_expand(tab, key, rk);
-
-  const uint32_t cb = threadIdx.x & 7, rs = threadIdx.x >> 3;
+template <bool FUSED, bool CMP>
+__global__ void __launch_bounds__(256) k_sa(MulSaArgs a) {
+  extern __shared__ uint4 sm4[];
+  uint8_t *base = reinterpret_cast<uint8_t *>(sm4);
+  uint4 *sP = reinterpret_cast<uint4 *>(base + (FUSED ? AES_SMEM_BYTES : 0));
+  int *red = reinterpret_cast<int *>(base + (FUSED ? AES_SMEM_BYTES : 0) + SA_PAIRS * 16);
+  const uint32_t cb = blockIdx.x, rsplit = blockIdx.y, R = gridDim.y, e = blockIdx.z;
+  const uint32_t tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const uint32_t n = a.n;
+  const uint32_t j0 = cb * 256 + 8 * lane;
+  const bool jv = j0 < n;  // n and j0 are multiples of 8: a chunk is all in or all out
+  for (uint32_t i = tid; i < 2048; i += 256) red[i] = 0;
+  AesTab tab;
+  uint32_t rk[44];
+  if (FUSED) {
+    uint32_t *sT = reinterpret_cast<uint32_t *>(base);
+    aes_fill_smem(sT, g_aes_T0);
+    __syncthreads();
+    tab = aes_tab(sT);
+    uint32_t key[4];
+    aes_load_key(a.seed_ptrs ? a.seed_ptrs[e] + a.seed_off : a.seedA, key);
+    aes_key_expand(tab, key, rk);
+  }
   const uint32_t mq = (1u << a.logq) - 1u, mm = mq | (mq << 16);
   const int8_t *S = a.S + (size_t)e * a.s_stride;
-  const uint32_t jb = j0 + 8 * cb;
-  const bool jvalid = jb < n;
+  const uint16_t *Aitem = FUSED ? nullptr : (a.A_ptrs ? a.A_ptrs[e] : a.A);
+  const uint32_t npairs = n / 2;
+  const uint32_t per = (npairs + R - 1) / R;
+  const uint32_t pb = min(npairs, rsplit * per), pe = min(npairs, pb + per);
   int acc[8][8];
 #pragma unroll
   for (int k = 0; k < 8; k++)
 #pragma unroll
     for (int c = 0; c < 8; c++) acc[k][c] = 0;
-  for (uint32_t i0 = 0; i0 < n; i0 += SA_CH) {
-    __syncthreads();
-    for (uint32_t idx = threadIdx.x; idx < SA_CH * 8; idx += blockDim.x) {
-      const uint32_t k = idx / SA_CH, ii = idx % SA_CH;
-      const int v = (i0 + ii < n) ? (int)S[(size_t)k * n + i0 + ii] : 0;
-      reinterpret_cast<int *>(&sS[2 * ii])[k] = v;
+  auto row_chunk = [&](uint32_t i) -> uint4 {
+    if (FUSED) {
+      uint4 v = aes_ctr_block(tab, rk, 0, (uint64_t)i * (n / 8) + j0 / 8);
+      v.x &= mm;
+      v.y &= mm;
+      v.z &= mm;
+      v.w &= mm;
+      return v;
     }
-    __syncthreads();
-    const uint32_t rows = min((uint32_t)SA_CH, n - i0);
-    if (jvalid) {
-      for (uint32_t ii = rs; ii < rows; ii += 32) {
-        const uint4 v = aes_ctr_block(tab, rk, 0, (uint64_t)(i0 + ii) * (n / 8) + jb / 8);
-        const uint32_t w[4] = {v.x & mm, v.y & mm, v.z & mm, v.w & mm};
-        const int4 s0 = sS[2 * ii], s1 = sS[2 * ii + 1];
-        const int s[8] = {s0.x, s0.y, s0.z, s0.w, s1.x, s1.y, s1.z, s1.w};
+    return jv ? ld_nc_u4(Aitem + (size_t)i * n + j0) : make_uint4(0, 0, 0, 0);
+  };
+  auto mac_pair = [&](const uint4 x0, const uint4 x1, const uint4 sp) {
+    const uint32_t w0[4] = {x0.x, x0.y, x0.z, x0.w}, w1[4] = {x1.x, x1.y, x1.z, x1.w};
+    const uint32_t sw[4] = {sp.x, sp.y, sp.z, sp.w};
 #pragma unroll
-        for (int c = 0; c < 8; c++) {
-          const int x = (int)((w[c >> 1] >> (16 * (c & 1))) & 0xffffu);
+    for (int c = 0; c < 8; c++) {
+      // column c of both rows as two 16-bit halves (signed: same residues)
+      const int pk = (int)__byte_perm(w0[c >> 1], w1[c >> 1], (c & 1) ? 0x7632 : 0x5410);
 #pragma unroll
-          for (int k = 0; k < 8; k++) acc[k][c] += s[k] * x;
-        }
+      for (int q = 0; q < 4; q++) {
+        acc[2 * q][c] = __dp2a_lo(pk, (int)sw[q], acc[2 * q][c]);
+        acc[2 * q + 1][c] = __dp2a_hi(pk, (int)sw[q], acc[2 * q + 1][c]);
       }
     }
+  };
+  for (uint32_t c0 = pb; c0 < pe; c0 += SA_PAIRS) {
+    const uint32_t cn = min((uint32_t)SA_PAIRS, pe - c0);
+    __syncthreads();
+    // word q of pair p: S'[2q][2p], S'[2q][2p+1], S'[2q+1][2p], S'[2q+1][2p+1]
+    for (uint32_t q = tid; q < cn; q += 256) {
+      const uint32_t i = 2 * (c0 + q);
+      uint32_t w[4];
+#pragma unroll
+      for (int kk = 0; kk < 4; kk++) {
+        const uint32_t lo = *reinterpret_cast<const uint16_t *>(S + (size_t)(2 * kk) * n + i);
+        const uint32_t hi = *reinterpret_cast<const uint16_t *>(S + (size_t)(2 * kk + 1) * n + i);
+        w[kk] = lo | (hi << 16);
+      }
+      sP[q] = make_uint4(w[0], w[1], w[2], w[3]);
+    }
+    __syncthreads();
+    uint32_t q = warp;
+    for (; q + 8 < cn; q += 16) {  // two pairs in flight
+      const uint32_t i = 2 * (c0 + q), i2 = i + 16;
+      const uint4 x0 = row_chunk(i), x1 = row_chunk(i + 1);
+      const uint4 y0 = row_chunk(i2), y1 = row_chunk(i2 + 1);
+      mac_pair(x0, x1, sP[q]);
+      mac_pair(y0, y1, sP[q + 8]);
+    }
+    if (q < cn) {
+      const uint32_t i = 2 * (c0 + q);
+      mac_pair(row_chunk(i), row_chunk(i + 1), sP[q]);
+    }
   }
-  // reduce over the 4 row slices inside a warp (lanes l, l^8, l^16, l^24)
+  // the CTA's sum: red[k][c][lane] (column 8 lane + c)
 #pragma unroll
   for (int k = 0; k < 8; k++)
 #pragma unroll
-    for (int c = 0; c < 8; c++) {
-      acc[k][c] += __shfl_xor_sync(0xffffffffu, acc[k][c], 8);
-      acc[k][c] += __shfl_xor_sync(0xffffffffu, acc[k][c], 16);
-    }
+    for (int c = 0; c < 8; c++) atomicAdd(&red[k * 256 + c * 32 + lane], acc[k][c]);
   __syncthreads();
-  int *red = reinterpret_cast<int *>(sS);  // [8 warps][8 cb][64]
-  const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  if (lane < 8) {
-#pragma unroll
-    for (int k = 0; k < 8; k++)
-#pragma unroll
-      for (int c = 0; c < 8; c++) red[(warp * 8 + lane) * 64 + k * 8 + c] = acc[k][c];
-  }
-  __syncthreads();
-  {
-    // thread (k = warp, lane) finishes row k, columns j0 + 2 lane, +1
-    const uint32_t k = warp;
-    const uint32_t j = j0 + 2 * lane;
-    const uint32_t cbj = (2 * lane) / 8, c0 = (2 * lane) % 8;
-    int v0 = 0, v1 = 0;
-#pragma unroll
-    for (int w = 0; w < 8; w++) {
-      v0 += red[(w * 8 + cbj) * 64 + k * 8 + c0];
-      v1 += red[(w * 8 + cbj) * 64 + k * 8 + c0 + 1];
+  if (R > 1) cluster_barrier();  // every CTA of the cluster has its partial sum
+  // this CTA finishes values v = k * 256 + column, a 1/R share of them
+  const uint32_t share = 2048 / R;
+  uint32_t diff = 0;
+  for (uint32_t v = rsplit * share + tid; v < (rsplit + 1) * share; v += 256) {
+    const uint32_t k = v >> 8, col = v & 255;
+    const uint32_t idx = k * 256 + (col & 7) * 32 + (col >> 3);
+    int sum = 0;
+    if (R > 1) {
+      for (uint32_t r = 0; r < R; r++) sum += ld_cluster_s32(cluster_map(red + idx, r));
+    } else {
+      sum = red[idx];
     }
-    uint32_t diff = 0;
+    const uint32_t j = cb * 256 + col;
     if (j < n) {
-      if (a.E) {
-        const int8_t *E = a.E + (size_t)e * a.e_stride + (size_t)k * n + j;
-        v0 += E[0];
-        v1 += E[1];
-      }
-      const uint32_t packed = ((uint32_t)v0 & mq) | (((uint32_t)v1 & mq) << 16);
-      uint32_t *o = reinterpret_cast<uint32_t *>(a.out + (size_t)e * a.out_stride +
-                                                 2 * ((size_t)k * n + j));
+      if (a.E) sum += a.E[(size_t)e * a.e_stride + (size_t)k * n + j];
+      const uint32_t val = (uint32_t)sum & mq;
+      uint16_t *o = reinterpret_cast<uint16_t *>(a.out + (size_t)e * a.out_stride) + (size_t)k * n + j;
       if (CMP)
-        diff = packed ^ *o;
+        diff |= val ^ (uint32_t)*o;
       else
-        *o = packed;
-    }
-    if (CMP) {
-      diff = __reduce_or_sync(0xffffffffu, diff);
-      if (lane == 0 && diff) atomicOr(a.flags + e, 1u);
+        *o = (uint16_t)val;
     }
   }
+  if (CMP) {
+    diff = __reduce_or_sync(0xffffffffu, diff);
+    if (lane == 0 && diff) atomicOr(a.flags + e, 1u);
+  }
+  if (R > 1) cluster_barrier();  // no CTA leaves while others read its shared memory
 }
 
 // ---------------------------------------------------------------------------
@@ -810,10 +866,10 @@ cudaError_t lwe_kernel_smem_setup() {
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_mul_as<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, AES_SMEM_BYTES);
   if (e != cudaSuccess) return e;
-  const int fused_smem = AES_SMEM_BYTES + SA_CH * 32;
-  e = cudaFuncSetAttribute(k_mul_sa_fused<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, fused_smem);
+  const int fused_smem = AES_SMEM_BYTES + SA_PAIRS * 16 + 2048 * 4;
+  e = cudaFuncSetAttribute(k_sa<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, fused_smem);
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_mul_sa_fused<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, fused_smem);
+  e = cudaFuncSetAttribute(k_sa<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, fused_smem);
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_limbs, cudaFuncAttributeMaxDynamicSharedMemorySize, AES_SMEM_BYTES);
   return e;
@@ -831,31 +887,53 @@ void launch_noise(const NoiseArgs &a, int num_sms, cudaStream_t st) {
   k_noise<<<g, 512, NOISE_SMEM_BYTES, st>>>(a);
 }
 
-void launch_mul_as(const MulAsArgs &a, uint32_t count, bool fused, cudaStream_t st) {
-  dim3 grid((a.n + 7) / 8, count);
-  if (fused)
+void launch_mul_as(const MulAsArgs &a, uint32_t count, bool fused, int num_sms, cudaStream_t st) {
+  if (fused) {
+    dim3 grid((a.n + 7) / 8, count);
     k_mul_as<true><<<grid, 256, AES_SMEM_BYTES, st>>>(a);
-  else
-    k_mul_as<false><<<grid, 256, 0, st>>>(a);
+  } else {
+    // two CTAs per SM in all, spread over the items
+    const uint32_t want = (a.n / AS_ROWS + 7) / 8;
+    const uint32_t share = std::max<uint32_t>(1u, 2u * (uint32_t)std::max(num_sms, 1) / count);
+    dim3 grid(std::min(want, share), count);
+    k_mul_as_rows<<<grid, 256, 0, st>>>(a);
+  }
 }
 
 void launch_decrypt(const DecryptArgs &a, uint32_t count, cudaStream_t st) {
   k_decrypt<<<count, 256, 0, st>>>(a);
 }
 
-void launch_mul_sa(const MulSaArgs &a, uint32_t items, bool fused, bool cmp, cudaStream_t st) {
-  dim3 grid((a.n + 63) / 64, items);
+void launch_mul_sa(const MulSaArgs &a, uint32_t items, bool fused, bool cmp, int num_sms,
+                   cudaStream_t st) {
+  // rows split over a cluster of R CTAs (R a power of two <= 8) until the
+  // grid holds about two CTAs per SM (one with the AES tables)
+  const uint32_t cbs = (a.n + 255) / 256;
+  const uint32_t target = (fused ? 1u : 2u) * (uint32_t)std::max(num_sms, 1);
+  uint32_t R = 1;
+  while (R < 8 && (uint64_t)cbs * items * R < target && a.n / 2 / (2 * R) >= 64) R <<= 1;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(cbs, R, items);
+  cfg.blockDim = dim3(256, 1, 1);
+  cfg.dynamicSmemBytes = (fused ? AES_SMEM_BYTES : 0) + SA_PAIRS * 16 + 2048 * 4;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = 1;
+  attr[0].val.clusterDim.y = R;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = R > 1 ? 1 : 0;
   if (fused) {
-    const int smem = AES_SMEM_BYTES + SA_CH * 32;
     if (cmp)
-      k_mul_sa_fused<true><<<grid, 256, smem, st>>>(a);
+      cudaLaunchKernelEx(&cfg, k_sa<true, true>, a);
     else
-      k_mul_sa_fused<false><<<grid, 256, smem, st>>>(a);
+      cudaLaunchKernelEx(&cfg, k_sa<true, false>, a);
   } else {
     if (cmp)
-      k_mul_sa<true><<<grid, 256, 0, st>>>(a);
+      cudaLaunchKernelEx(&cfg, k_sa<false, true>, a);
     else
-      k_mul_sa<false><<<grid, 256, 0, st>>>(a);
+      cudaLaunchKernelEx(&cfg, k_sa<false, false>, a);
   }
 }
 

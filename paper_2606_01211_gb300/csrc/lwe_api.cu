@@ -408,7 +408,7 @@ int run_encrypt(lwe_ctx *c, const uint8_t *pk, const uint16_t *A, uint32_t count
     sa.seed_off = ik->pk_off;
     fused = ik->A_ptrs == nullptr;
   }
-  LAUNCH(c, fused ? KID_MUL_SA_FUSED : KID_MUL_SA, st, launch_mul_sa(sa, count, fused, cmp, st));
+  LAUNCH(c, fused ? KID_MUL_SA_FUSED : KID_MUL_SA, st, launch_mul_sa(sa, count, fused, cmp, c->num_sms, st));
 
   VEncArgs va;
   memset(&va, 0, sizeof va);
@@ -740,7 +740,7 @@ int lwe_keygen(lwe_ctx *c, const uint8_t *seeds, uint32_t count, uint8_t *pk, ui
   ma.out_stride = pkb;
   ma.out2 = sk + 8 * (size_t)n + 64 + 16;
   ma.out2_stride = skb;
-  LAUNCH(c, KID_MUL_AS, st, launch_mul_as(ma, count, A_out == nullptr, st));
+  LAUNCH(c, KID_MUL_AS, st, launch_mul_as(ma, count, A_out == nullptr, c->num_sms, st));
 
   // H(pk) into sk
   return hash_tree(c, pk, pkb, (uint32_t)pkb, count, TREE_DIGEST, sk + 8 * (size_t)n + 32, skb,
@@ -930,7 +930,7 @@ int lwe_matmul_modq(lwe_ctx *c, int side, const uint16_t *A, const uint8_t *seed
     ma.St = S;
     ma.E = E;
     ma.out = reinterpret_cast<uint8_t *>(out);
-    LAUNCH(c, KID_MUL_AS, st, launch_mul_as(ma, 1, A == nullptr, st));
+    LAUNCH(c, KID_MUL_AS, st, launch_mul_as(ma, 1, A == nullptr, sms, st));
     return check_launch();
   }
   if (side != LWE_SIDE_SA || k == 0 || (k % 8)) return LWE_EINVAL;
@@ -985,7 +985,7 @@ int lwe_matmul_modq(lwe_ctx *c, int side, const uint16_t *A, const uint8_t *seed
   sa.e_stride = 8ull * n;
   sa.out = reinterpret_cast<uint8_t *>(out);
   sa.out_stride = 16ull * n;
-  LAUNCH(c, A ? KID_MUL_SA : KID_MUL_SA_FUSED, st, launch_mul_sa(sa, items, A == nullptr, false, st));
+  LAUNCH(c, A ? KID_MUL_SA : KID_MUL_SA_FUSED, st, launch_mul_sa(sa, items, A == nullptr, false, sms, st));
   return check_launch();
 }
 
