@@ -5,7 +5,8 @@
 //   k_noise         the error/secret distributions of Alg. 1-2 (Tab. 1:
 //                   rounded Gaussian) by CDF-table inverse sampling of AES
 //                   counter streams.
-//   k_mul_as        B = A S + E of Alg. 1 (A stored or regenerated).
+//   k_mul_as_rows, k_mul_as_fused: B = A S + E of Alg. 1 (A stored, or
+//                   regenerated from its seed in-CTA).
 //   k_decrypt       M = C - B' S and mu' = Dec(M) of Alg. 3.
 //   k_sa            B' = S' A + E' of Alg. 2 on the CUDA cores (A stored or
 //                   regenerated from its seed in-CTA), with a compare
@@ -201,54 +202,44 @@ LWE_DEV void warp_allreduce8(int acc[8]) {
   }
 }
 
-template <bool FUSED>
-__global__ void __launch_bounds__(256) k_mul_as(MulAsArgs a) {
+// A S + E with A regenerated (KeyGen, Alg. 1, fused): persistent CTAs of
+// 16 warps fill the AES tables once and walk the rows (warp per row, lane
+// per 16-byte chunk = one AES block of A's counter layout).
+__global__ void __launch_bounds__(512, 1) k_mul_as_fused(MulAsArgs a) {
   extern __shared__ uint32_t sT[];
-  AesTab tab;
-  uint32_t rk[44];
+  aes_fill_smem(sT, g_aes_T0);
+  __syncthreads();
+  const AesTab tab = aes_tab(sT);
   const uint32_t e = blockIdx.y;
-  if (FUSED) {
-    aes_fill_smem(sT, g_aes_T0);
-    __syncthreads();
-    tab = aes_tab(sT);
-    uint32_t key[4];
-    aes_load_key(a.seeds + (size_t)e * a.seed_stride, key);
-    aes_key_expand(tab, key, rk);
-  }
+  uint32_t key[4], rk[44];
+  aes_load_key(a.seeds + (size_t)e * a.seed_stride, key);
+  aes_key_expand(tab, key, rk);
   const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const uint32_t i = blockIdx.x * 8 + warp;
-  if (i >= a.n) return;
   const uint32_t n = a.n;
+  const uint32_t m = (1u << a.logq) - 1u, mm = m | (m << 16);
   const int8_t *St = a.St + (size_t)e * a.st_stride;
-  int acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-  const uint16_t *Arow = FUSED ? nullptr : a.A + (size_t)e * a.a_stride + (size_t)i * n;
-  for (uint32_t jc = lane; jc < n / 8; jc += 32) {
-    uint4 x;
-    if (FUSED)
-      x = aes_ctr_block(tab, rk, 0, (uint64_t)i * (n / 8) + jc);
-    else
-      x = ld_nc_u4(Arow + 8 * (size_t)jc);
-    if (FUSED) {
-      const uint32_t m = (1u << a.logq) - 1u, mm = m | (m << 16);
+  for (uint32_t i = blockIdx.x * 16 + warp; i < n; i += gridDim.x * 16) {
+    int acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (uint32_t jc = lane; jc < n / 8; jc += 32) {
+      uint4 x = aes_ctr_block(tab, rk, 0, (uint64_t)i * (n / 8) + jc);
       x.x &= mm;
       x.y &= mm;
       x.z &= mm;
       x.w &= mm;
+      dot8_chunk(x, St, n, 8 * jc, acc);
     }
-    dot8_chunk(x, St, n, 8 * jc, acc);
-  }
-  warp_allreduce8(acc);
-  if (lane == 0) {
-    const uint32_t m = (1u << a.logq) - 1u;
-    uint32_t v[8];
-    const int8_t *E = a.E ? a.E + (size_t)e * a.e_stride + (size_t)i * 8 : nullptr;
+    warp_allreduce8(acc);
+    if (lane == 0) {
+      uint32_t v[8];
+      const int8_t *E = a.E ? a.E + (size_t)e * a.e_stride + (size_t)i * 8 : nullptr;
 #pragma unroll
-    for (int l = 0; l < 8; l++) v[l] = (uint32_t)(acc[l] + (E ? (int)E[l] : 0)) & m;
-    const uint4 pk = make_uint4(v[0] | (v[1] << 16), v[2] | (v[3] << 16), v[4] | (v[5] << 16),
-                                v[6] | (v[7] << 16));
-    *reinterpret_cast<uint4 *>(a.out + (size_t)e * a.out_stride + 16 * (size_t)i) = pk;
-    if (a.out2)
-      *reinterpret_cast<uint4 *>(a.out2 + (size_t)e * a.out2_stride + 16 * (size_t)i) = pk;
+      for (int l = 0; l < 8; l++) v[l] = (uint32_t)(acc[l] + (E ? (int)E[l] : 0)) & m;
+      const uint4 pk = make_uint4(v[0] | (v[1] << 16), v[2] | (v[3] << 16), v[4] | (v[5] << 16),
+                                  v[6] | (v[7] << 16));
+      *reinterpret_cast<uint4 *>(a.out + (size_t)e * a.out_stride + 16 * (size_t)i) = pk;
+      if (a.out2)
+        *reinterpret_cast<uint4 *>(a.out2 + (size_t)e * a.out2_stride + 16 * (size_t)i) = pk;
+    }
   }
 }
 
@@ -407,105 +398,42 @@ LWE_DEV void cluster_barrier() {
                    : "memory");
 }
 
-template <bool FUSED, bool CMP>
-__global__ void __launch_bounds__(256) k_sa(MulSaArgs a) {
-  extern __shared__ uint4 sm4[];
-  uint8_t *base = reinterpret_cast<uint8_t *>(sm4);
-  uint4 *sP = reinterpret_cast<uint4 *>(base + (FUSED ? AES_SMEM_BYTES : 0));
-  int *red = reinterpret_cast<int *>(base + (FUSED ? AES_SMEM_BYTES : 0) + SA_PAIRS * 16);
-  const uint32_t cb = blockIdx.x, rsplit = blockIdx.y, R = gridDim.y, e = blockIdx.z;
-  const uint32_t tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const uint32_t n = a.n;
-  const uint32_t j0 = cb * 256 + 8 * lane;
-  const bool jv = j0 < n;  // n and j0 are multiples of 8: a chunk is all in or all out
-  for (uint32_t i = tid; i < 2048; i += 256) red[i] = 0;
-  AesTab tab;
-  uint32_t rk[44];
-  if (FUSED) {
-    uint32_t *sT = reinterpret_cast<uint32_t *>(base);
-    aes_fill_smem(sT, g_aes_T0);
-    __syncthreads();
-    tab = aes_tab(sT);
-    uint32_t key[4];
-    aes_load_key(a.seed_ptrs ? a.seed_ptrs[e] + a.seed_off : a.seedA, key);
-    aes_key_expand(tab, key, rk);
+// word q of pair p: S'[2q][2p], S'[2q][2p+1], S'[2q+1][2p], S'[2q+1][2p+1]
+LWE_DEV void sa_stage(const int8_t *S, uint32_t n, uint32_t c0, uint32_t cn, uint4 *sP,
+                      uint32_t tid, uint32_t nt) {
+  for (uint32_t q = tid; q < cn; q += nt) {
+    const uint32_t i = 2 * (c0 + q);
+    uint32_t w[4];
+#pragma unroll
+    for (int kk = 0; kk < 4; kk++) {
+      const uint32_t lo = *reinterpret_cast<const uint16_t *>(S + (size_t)(2 * kk) * n + i);
+      const uint32_t hi = *reinterpret_cast<const uint16_t *>(S + (size_t)(2 * kk + 1) * n + i);
+      w[kk] = lo | (hi << 16);
+    }
+    sP[q] = make_uint4(w[0], w[1], w[2], w[3]);
   }
-  const uint32_t mq = (1u << a.logq) - 1u, mm = mq | (mq << 16);
-  const int8_t *S = a.S + (size_t)e * a.s_stride;
-  const uint16_t *Aitem = FUSED ? nullptr : (a.A_ptrs ? a.A_ptrs[e] : a.A);
-  const uint32_t npairs = n / 2;
-  const uint32_t per = (npairs + R - 1) / R;
-  const uint32_t pb = min(npairs, rsplit * per), pe = min(npairs, pb + per);
-  int acc[8][8];
+}
+
+// One column c of both rows of a pair as two 16-bit halves, times the pair's
+// S' bytes for all 8 rows k: acc[k] += S'[k][2p] A[2p][c] + S'[k][2p+1] A[2p+1][c]
+LWE_DEV void sa_mac_col(int pk, const uint4 sp, int *acc_c /* [8] stride */, int stride) {
+  const uint32_t sw[4] = {sp.x, sp.y, sp.z, sp.w};
 #pragma unroll
-  for (int k = 0; k < 8; k++)
-#pragma unroll
-    for (int c = 0; c < 8; c++) acc[k][c] = 0;
-  auto row_chunk = [&](uint32_t i) -> uint4 {
-    if (FUSED) {
-      uint4 v = aes_ctr_block(tab, rk, 0, (uint64_t)i * (n / 8) + j0 / 8);
-      v.x &= mm;
-      v.y &= mm;
-      v.z &= mm;
-      v.w &= mm;
-      return v;
-    }
-    return jv ? ld_nc_u4(Aitem + (size_t)i * n + j0) : make_uint4(0, 0, 0, 0);
-  };
-  auto mac_pair = [&](const uint4 x0, const uint4 x1, const uint4 sp) {
-    const uint32_t w0[4] = {x0.x, x0.y, x0.z, x0.w}, w1[4] = {x1.x, x1.y, x1.z, x1.w};
-    const uint32_t sw[4] = {sp.x, sp.y, sp.z, sp.w};
-#pragma unroll
-    for (int c = 0; c < 8; c++) {
-      // column c of both rows as two 16-bit halves (signed: same residues)
-      const int pk = (int)__byte_perm(w0[c >> 1], w1[c >> 1], (c & 1) ? 0x7632 : 0x5410);
-#pragma unroll
-      for (int q = 0; q < 4; q++) {
-        acc[2 * q][c] = __dp2a_lo(pk, (int)sw[q], acc[2 * q][c]);
-        acc[2 * q + 1][c] = __dp2a_hi(pk, (int)sw[q], acc[2 * q + 1][c]);
-      }
-    }
-  };
-  for (uint32_t c0 = pb; c0 < pe; c0 += SA_PAIRS) {
-    const uint32_t cn = min((uint32_t)SA_PAIRS, pe - c0);
-    __syncthreads();
-    // word q of pair p: S'[2q][2p], S'[2q][2p+1], S'[2q+1][2p], S'[2q+1][2p+1]
-    for (uint32_t q = tid; q < cn; q += 256) {
-      const uint32_t i = 2 * (c0 + q);
-      uint32_t w[4];
-#pragma unroll
-      for (int kk = 0; kk < 4; kk++) {
-        const uint32_t lo = *reinterpret_cast<const uint16_t *>(S + (size_t)(2 * kk) * n + i);
-        const uint32_t hi = *reinterpret_cast<const uint16_t *>(S + (size_t)(2 * kk + 1) * n + i);
-        w[kk] = lo | (hi << 16);
-      }
-      sP[q] = make_uint4(w[0], w[1], w[2], w[3]);
-    }
-    __syncthreads();
-    uint32_t q = warp;
-    for (; q + 8 < cn; q += 16) {  // two pairs in flight
-      const uint32_t i = 2 * (c0 + q), i2 = i + 16;
-      const uint4 x0 = row_chunk(i), x1 = row_chunk(i + 1);
-      const uint4 y0 = row_chunk(i2), y1 = row_chunk(i2 + 1);
-      mac_pair(x0, x1, sP[q]);
-      mac_pair(y0, y1, sP[q + 8]);
-    }
-    if (q < cn) {
-      const uint32_t i = 2 * (c0 + q);
-      mac_pair(row_chunk(i), row_chunk(i + 1), sP[q]);
-    }
+  for (int q = 0; q < 4; q++) {
+    acc_c[(2 * q) * stride] = __dp2a_lo(pk, (int)sw[q], acc_c[(2 * q) * stride]);
+    acc_c[(2 * q + 1) * stride] = __dp2a_hi(pk, (int)sw[q], acc_c[(2 * q + 1) * stride]);
   }
-  // the CTA's sum: red[k][c][lane] (column 8 lane + c)
-#pragma unroll
-  for (int k = 0; k < 8; k++)
-#pragma unroll
-    for (int c = 0; c < 8; c++) atomicAdd(&red[k * 256 + c * 32 + lane], acc[k][c]);
-  __syncthreads();
-  if (R > 1) cluster_barrier();  // every CTA of the cluster has its partial sum
-  // this CTA finishes values v = k * 256 + column, a 1/R share of them
+}
+
+// The CTA's (and with R > 1 the cluster's) sums red[k][c][32] (column
+// 8 lane + c of the block) are finished: + E', mod q, store or compare.
+template <bool CMP>
+LWE_DEV void sa_epilogue(const MulSaArgs &a, int *red, uint32_t cb, uint32_t rsplit, uint32_t R,
+                         uint32_t e, uint32_t tid, uint32_t nt) {
+  const uint32_t n = a.n, mq = (1u << a.logq) - 1u;
   const uint32_t share = 2048 / R;
   uint32_t diff = 0;
-  for (uint32_t v = rsplit * share + tid; v < (rsplit + 1) * share; v += 256) {
+  for (uint32_t v = rsplit * share + tid; v < (rsplit + 1) * share; v += nt) {
     const uint32_t k = v >> 8, col = v & 255;
     const uint32_t idx = k * 256 + (col & 7) * 32 + (col >> 3);
     int sum = 0;
@@ -527,9 +455,149 @@ __global__ void __launch_bounds__(256) k_sa(MulSaArgs a) {
   }
   if (CMP) {
     diff = __reduce_or_sync(0xffffffffu, diff);
-    if (lane == 0 && diff) atomicOr(a.flags + e, 1u);
+    if ((tid & 31) == 0 && diff) atomicOr(a.flags + e, 1u);
   }
+}
+
+template <bool CMP>
+__global__ void __launch_bounds__(256) k_sa(MulSaArgs a) {
+  extern __shared__ uint4 sm4[];
+  uint4 *sP = sm4;
+  int *red = reinterpret_cast<int *>(sm4 + SA_PAIRS);
+  const uint32_t cb = blockIdx.x, rsplit = blockIdx.y, R = gridDim.y, e = blockIdx.z;
+  const uint32_t tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const uint32_t n = a.n;
+  const uint32_t j0 = cb * 256 + 8 * lane;
+  const bool jv = j0 < n;  // n and j0 are multiples of 8: a chunk is all in or all out
+  for (uint32_t i = tid; i < 2048; i += 256) red[i] = 0;
+  const int8_t *S = a.S + (size_t)e * a.s_stride;
+  const uint16_t *Aitem = a.A_ptrs ? a.A_ptrs[e] : a.A;
+  const uint32_t npairs = n / 2;
+  const uint32_t per = (npairs + R - 1) / R;
+  const uint32_t pb = min(npairs, rsplit * per), pe = min(npairs, pb + per);
+  int acc[8][8];
+#pragma unroll
+  for (int k = 0; k < 8; k++)
+#pragma unroll
+    for (int c = 0; c < 8; c++) acc[k][c] = 0;
+  auto row_chunk = [&](uint32_t i) -> uint4 {
+    return jv ? ld_nc_u4(Aitem + (size_t)i * n + j0) : make_uint4(0, 0, 0, 0);
+  };
+  auto mac_pair = [&](const uint4 x0, const uint4 x1, const uint4 sp) {
+    const uint32_t w0[4] = {x0.x, x0.y, x0.z, x0.w}, w1[4] = {x1.x, x1.y, x1.z, x1.w};
+#pragma unroll
+    for (int c = 0; c < 8; c++) {
+      // column c of both rows as two 16-bit halves (signed: same residues)
+      const int pk = (int)__byte_perm(w0[c >> 1], w1[c >> 1], (c & 1) ? 0x7632 : 0x5410);
+      sa_mac_col(pk, sp, &acc[0][c], 8);
+    }
+  };
+  for (uint32_t c0 = pb; c0 < pe; c0 += SA_PAIRS) {
+    const uint32_t cn = min((uint32_t)SA_PAIRS, pe - c0);
+    __syncthreads();
+    sa_stage(S, n, c0, cn, sP, tid, 256);
+    __syncthreads();
+    uint32_t q = warp;
+    for (; q + 8 < cn; q += 16) {  // two pairs in flight
+      const uint32_t i = 2 * (c0 + q), i2 = i + 16;
+      const uint4 x0 = row_chunk(i), x1 = row_chunk(i + 1);
+      const uint4 y0 = row_chunk(i2), y1 = row_chunk(i2 + 1);
+      mac_pair(x0, x1, sP[q]);
+      mac_pair(y0, y1, sP[q + 8]);
+    }
+    if (q < cn) {
+      const uint32_t i = 2 * (c0 + q);
+      mac_pair(row_chunk(i), row_chunk(i + 1), sP[q]);
+    }
+  }
+  // the CTA's sum: red[k][c][lane] (column 8 lane + c)
+#pragma unroll
+  for (int k = 0; k < 8; k++)
+#pragma unroll
+    for (int c = 0; c < 8; c++) atomicAdd(&red[k * 256 + c * 32 + lane], acc[k][c]);
+  __syncthreads();
+  if (R > 1) cluster_barrier();  // every CTA of the cluster has its partial sum
+  sa_epilogue<CMP>(a, red, cb, rsplit, R, e, tid, 256);
   if (R > 1) cluster_barrier();  // no CTA leaves while others read its shared memory
+}
+
+// The same product with A regenerated (the AES tables in shared memory): 16
+// warps; a lane pair shares one 8-column chunk, lane s of the pair
+// encrypting row 2p + s of each row pair and the two swapping half blocks,
+// so each lane holds 4 columns of both rows (32 sums, room for 16 warps).
+// Warps 0-7 take columns 0-127 of the CTA's block, warps 8-15 columns
+// 128-255.
+template <bool CMP>
+__global__ void __launch_bounds__(512, 1) k_sa_fused(MulSaArgs a) {
+  extern __shared__ uint4 sm4[];
+  uint8_t *base = reinterpret_cast<uint8_t *>(sm4);
+  uint4 *sP = reinterpret_cast<uint4 *>(base + AES_SMEM_BYTES);
+  int *red = reinterpret_cast<int *>(base + AES_SMEM_BYTES + SA_PAIRS * 16);
+  const uint32_t cb = blockIdx.x, rsplit = blockIdx.y, R = gridDim.y, e = blockIdx.z;
+  const uint32_t tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const uint32_t rw = warp & 7, half = warp >> 3, s = lane & 1;
+  const uint32_t n = a.n;
+  const uint32_t chunk = cb * 32 + half * 16 + (lane >> 1);  // 8-column chunk index
+  const uint32_t j0 = 8 * chunk;
+  const bool jv = j0 < n;
+  for (uint32_t i = tid; i < 2048; i += 512) red[i] = 0;
+  uint32_t *sT = reinterpret_cast<uint32_t *>(base);
+  aes_fill_smem(sT, g_aes_T0);
+  __syncthreads();
+  const AesTab tab = aes_tab(sT);
+  uint32_t key[4], rk[44];
+  aes_load_key(a.seed_ptrs ? a.seed_ptrs[e] + a.seed_off : a.seedA, key);
+  aes_key_expand(tab, key, rk);
+  const uint32_t mq = (1u << a.logq) - 1u, mm = mq | (mq << 16);
+  const int8_t *S = a.S + (size_t)e * a.s_stride;
+  const uint32_t npairs = n / 2;
+  const uint32_t per = (npairs + R - 1) / R;
+  const uint32_t pb = min(npairs, rsplit * per), pe = min(npairs, pb + per);
+  int acc[8][4];
+#pragma unroll
+  for (int k = 0; k < 8; k++)
+#pragma unroll
+    for (int c = 0; c < 4; c++) acc[k][c] = 0;
+  for (uint32_t c0 = pb; c0 < pe; c0 += SA_PAIRS) {
+    const uint32_t cn = min((uint32_t)SA_PAIRS, pe - c0);
+    __syncthreads();
+    sa_stage(S, n, c0, cn, sP, tid, 512);
+    __syncthreads();
+    for (uint32_t q = rw; q < cn; q += 8) {
+      const uint32_t i = 2 * (c0 + q) + s;  // this lane's row of the pair
+      uint4 x = make_uint4(0, 0, 0, 0);
+      if (jv) {
+        x = aes_ctr_block(tab, rk, 0, (uint64_t)i * (n / 8) + chunk);
+        x.x &= mm;
+        x.y &= mm;
+        x.z &= mm;
+        x.w &= mm;
+      }
+      // lane 0 of the pair keeps columns 0-3 of its row and takes columns
+      // 0-3 of row 2p+1; lane 1 keeps columns 4-7 of row 2p+1 and takes 4-7
+      // of row 2p
+      const uint32_t g0 = s ? x.x : x.z, g1 = s ? x.y : x.w;
+      const uint32_t r0 = __shfl_xor_sync(0xffffffffu, g0, 1);
+      const uint32_t r1 = __shfl_xor_sync(0xffffffffu, g1, 1);
+      const uint32_t a0 = s ? r0 : x.x, a1 = s ? r1 : x.y;  // row 2p, my 4 columns
+      const uint32_t b0 = s ? x.z : r0, b1 = s ? x.w : r1;  // row 2p+1
+      const uint4 sp = sP[q];
+      sa_mac_col((int)__byte_perm(a0, b0, 0x5410), sp, &acc[0][0], 4);
+      sa_mac_col((int)__byte_perm(a0, b0, 0x7632), sp, &acc[0][1], 4);
+      sa_mac_col((int)__byte_perm(a1, b1, 0x5410), sp, &acc[0][2], 4);
+      sa_mac_col((int)__byte_perm(a1, b1, 0x7632), sp, &acc[0][3], 4);
+    }
+  }
+  // column of the block owned by (half, lane): 128 half + 8 (lane / 2) + 4 s + c
+  const uint32_t cl = half * 16 + (lane >> 1);  // chunk within the block (0..31)
+#pragma unroll
+  for (int k = 0; k < 8; k++)
+#pragma unroll
+    for (int c = 0; c < 4; c++) atomicAdd(&red[k * 256 + (4 * s + c) * 32 + cl], acc[k][c]);
+  __syncthreads();
+  if (R > 1) cluster_barrier();
+  sa_epilogue<CMP>(a, red, cb, rsplit, R, e, tid, 512);
+  if (R > 1) cluster_barrier();
 }
 
 // ---------------------------------------------------------------------------
@@ -864,12 +932,12 @@ cudaError_t lwe_kernel_smem_setup() {
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_noise, cudaFuncAttributeMaxDynamicSharedMemorySize, NOISE_SMEM_BYTES);
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_mul_as<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, AES_SMEM_BYTES);
+  e = cudaFuncSetAttribute(k_mul_as_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, AES_SMEM_BYTES);
   if (e != cudaSuccess) return e;
   const int fused_smem = AES_SMEM_BYTES + SA_PAIRS * 16 + 2048 * 4;
-  e = cudaFuncSetAttribute(k_sa<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, fused_smem);
+  e = cudaFuncSetAttribute(k_sa_fused<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, fused_smem);
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_sa<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, fused_smem);
+  e = cudaFuncSetAttribute(k_sa_fused<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, fused_smem);
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_limbs, cudaFuncAttributeMaxDynamicSharedMemorySize, AES_SMEM_BYTES);
   return e;
@@ -889,8 +957,9 @@ void launch_noise(const NoiseArgs &a, int num_sms, cudaStream_t st) {
 
 void launch_mul_as(const MulAsArgs &a, uint32_t count, bool fused, int num_sms, cudaStream_t st) {
   if (fused) {
-    dim3 grid((a.n + 7) / 8, count);
-    k_mul_as<true><<<grid, 256, AES_SMEM_BYTES, st>>>(a);
+    const uint32_t per_item = std::max<uint32_t>(1u, (uint32_t)std::max(num_sms, 1) / count);
+    dim3 grid(std::min((a.n + 15) / 16, per_item), count);
+    k_mul_as_fused<<<grid, 512, AES_SMEM_BYTES, st>>>(a);
   } else {
     // two CTAs per SM in all, spread over the items
     const uint32_t want = (a.n / AS_ROWS + 7) / 8;
@@ -914,8 +983,8 @@ void launch_mul_sa(const MulSaArgs &a, uint32_t items, bool fused, bool cmp, int
   while (R < 8 && (uint64_t)cbs * items * R < target && a.n / 2 / (2 * R) >= 64) R <<= 1;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(cbs, R, items);
-  cfg.blockDim = dim3(256, 1, 1);
   cfg.dynamicSmemBytes = (fused ? AES_SMEM_BYTES : 0) + SA_PAIRS * 16 + 2048 * 4;
+  cfg.blockDim = dim3(fused ? 512 : 256, 1, 1);
   cfg.stream = st;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -926,14 +995,14 @@ void launch_mul_sa(const MulSaArgs &a, uint32_t items, bool fused, bool cmp, int
   cfg.numAttrs = R > 1 ? 1 : 0;
   if (fused) {
     if (cmp)
-      cudaLaunchKernelEx(&cfg, k_sa<true, true>, a);
+      cudaLaunchKernelEx(&cfg, k_sa_fused<true>, a);
     else
-      cudaLaunchKernelEx(&cfg, k_sa<true, false>, a);
+      cudaLaunchKernelEx(&cfg, k_sa_fused<false>, a);
   } else {
     if (cmp)
-      cudaLaunchKernelEx(&cfg, k_sa<false, true>, a);
+      cudaLaunchKernelEx(&cfg, k_sa<true>, a);
     else
-      cudaLaunchKernelEx(&cfg, k_sa<false, false>, a);
+      cudaLaunchKernelEx(&cfg, k_sa<false>, a);
   }
 }
 
