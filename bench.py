@@ -497,25 +497,31 @@ def run_ours(args, rank, world, local_rank):
     return 0
 
 
-def serve_measure(torch, rate: float = 1e5, requests: int = 20000):
+def serve_measure(torch, rates=(1e3, 1e4, 1e5, 1e6), requests: int = 20000):
     """The served mix (KeyGen/Encaps/Decaps 10/70/20 over n in {640, 976,
-    1344, 4096}, 10 000 resident keys, Zipf 1.1) at one open-loop arrival
-    rate, continuous batching versus one launch per request."""
+    1344, 4096}, 10 000 resident keys, Zipf 1.1) over open-loop arrival
+    rates, continuous batching versus one launch per request (each run about
+    two seconds of arrivals at the low rates, at most `requests`)."""
     from paper_2606_01211_gb300 import serve
-    cfg = serve.ServeConfig(rate=rate, requests=requests)
-    store = serve.KeyStore(cfg, torch.device("cuda", torch.cuda.current_device()))
-    out = {}
-    for plain in (False, True):
-        c = serve.ServeConfig(**{**cfg.__dict__, "plain": plain,
-                                 "requests": requests if not plain else 8000})
-        eng = serve.Engine(c, store=store)
-        eng.warmup()
-        st = eng.run()
-        out["plain" if plain else "batched"] = {k: st[k] for k in
-                                               ("ops_per_s", "p50_ms", "p99_ms", "mean_batch",
-                                                "requests")}
-    out["rate"] = rate
-    out["served_vs_plain"] = out["batched"]["ops_per_s"] / out["plain"]["ops_per_s"]
+    base = serve.ServeConfig(requests=requests)
+    store = serve.KeyStore(base, torch.device("cuda", torch.cuda.current_device()))
+    sweep = []
+    for rate in rates:
+        row = {"rate": rate}
+        for plain in (False, True):
+            cap = 8000 if plain else requests
+            c = serve.ServeConfig(**{**base.__dict__, "rate": rate, "plain": plain,
+                                     "requests": min(cap, max(2000, int(rate * 2)))})
+            eng = serve.Engine(c, store=store)
+            eng.warmup()
+            st = eng.run()
+            row["plain" if plain else "batched"] = {k: st[k] for k in
+                                                   ("ops_per_s", "p50_ms", "p99_ms", "mean_batch",
+                                                    "requests")}
+        row["served_vs_plain"] = row["batched"]["ops_per_s"] / row["plain"]["ops_per_s"]
+        sweep.append(row)
+    out = dict(next(r for r in sweep if r["rate"] == 1e5)) if 1e5 in rates else dict(sweep[-1])
+    out["rate_sweep"] = sweep
     return out
 
 
