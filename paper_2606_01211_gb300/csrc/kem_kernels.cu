@@ -498,6 +498,17 @@ __global__ void __launch_bounds__(256) k_sa(MulSaArgs a) {
     sa_stage(S, n, c0, cn, sP, tid, 256);
     __syncthreads();
     uint32_t q = warp;
+    for (; q + 24 < cn; q += 32) {  // four pairs (eight rows) in flight
+      const uint32_t i = 2 * (c0 + q);
+      uint4 x[8];
+#pragma unroll
+      for (int u = 0; u < 4; u++) {
+        x[2 * u] = row_chunk(i + 16 * u);
+        x[2 * u + 1] = row_chunk(i + 16 * u + 1);
+      }
+#pragma unroll
+      for (int u = 0; u < 4; u++) mac_pair(x[2 * u], x[2 * u + 1], sP[q + 8 * u]);
+    }
     for (; q + 8 < cn; q += 16) {  // two pairs in flight
       const uint32_t i = 2 * (c0 + q), i2 = i + 16;
       const uint4 x0 = row_chunk(i), x1 = row_chunk(i + 1);
