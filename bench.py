@@ -667,10 +667,21 @@ def main():
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-sweep", action="store_true")
     ap.add_argument("--no-large", action="store_true")
+    ap.add_argument("--sweep-only", type=str, default=None, metavar="N[,N...]",
+                    help="only the standalone kernel sweep at these n (prints its JSON, not the bench line)")
     ap.add_argument("--cpu-s", type=float, default=12.0)
     ap.add_argument("--ref-step-s", type=float, default=None,
                     help="CPU seconds per reference step (default: about 150 s in all)")
     args = ap.parse_args()
+    if args.sweep_only:
+        import torch
+        from paper_2606_01211_gb300 import lwe
+        dev = torch.device("cuda", 0)
+        torch.cuda.set_device(dev)
+        flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.int32, device=dev)
+        sizes = tuple(int(x) for x in args.sweep_only.split(","))
+        print(json.dumps(kernel_sweep(lwe, torch, dev, flush, sizes=sizes)))
+        return 0
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
