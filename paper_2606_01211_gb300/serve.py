@@ -45,7 +45,7 @@ class ServeConfig:
     requests: int = 20000
     max_batch: int = 512
     slots: int = 4
-    a_budget_bytes: int = 32 << 30
+    a_budget_bytes: int | None = None          # None: half the free device memory
     seed: int = 1
     plain: bool = False                        # per-request launches (baseline)
 
@@ -68,9 +68,11 @@ def zipf_keys(count: int, n_keys: int, s: float, r: np.random.Generator) -> np.n
 class KeyStore:
     """Resident key pairs per dimension and an LRU cache of expanded A.
 
-    The cache is an arena allocated once (the budget split evenly over the
-    dimensions, one fixed slot of 2 n^2 bytes per cached A), so admitting a
-    key never allocates device memory while serving.  A slot that is
+    The cache is an arena allocated once, one fixed slot of 2 n^2 bytes per
+    cached A, so admitting a key never allocates device memory while
+    serving.  Its budget (by default half the device memory free at start)
+    is water-filled over the dimensions: each gets what all its keys need
+    or an equal share of what is left, smallest need first.  A slot that is
     reused waits, on the stream that refills it, for the last batch that
     read it.  The most popular keys are expanded up front."""
 
@@ -81,8 +83,22 @@ class KeyStore:
         self.hits = self.misses = self.fills = 0
         self.arena, self.slot_of, self.lru, self.free, self.last_use = {}, {}, {}, {}, {}
         self.ready = {}
-        share = cfg.a_budget_bytes // max(1, len(cfg.presets))
+        budget = cfg.a_budget_bytes
+        if budget is None:
+            free, _total = torch.cuda.mem_get_info(device)
+            budget = free // 2
+        need = {}
+        for name in cfg.presets:
+            n = PRESETS[name]["n"]
+            need[name] = cfg.keys_per_n * 2 * n * n
+        share_of, left = {}, budget
+        order = sorted(cfg.presets, key=lambda nm: need[nm])
+        for k, name in enumerate(order):
+            share_of[name] = min(need[name], left // (len(order) - k))
+            left -= share_of[name]
+        self.budget = budget
         for i, name in enumerate(cfg.presets):
+            share = share_of[name]
             p = lwe.Params(**PRESETS[name])
             n = p.n
             self.params[n] = p
@@ -442,13 +458,15 @@ def main():
     ap.add_argument("--keys-per-n", type=int, default=2500)
     ap.add_argument("--max-batch", type=int, default=512)
     ap.add_argument("--slots", type=int, default=4)
-    ap.add_argument("--a-budget-gb", type=float, default=32.0)
+    ap.add_argument("--a-budget-gb", type=float, default=None,
+                    help="A cache budget (default: half the free device memory)")
     ap.add_argument("--no-plain", action="store_true")
     args = ap.parse_args()
     torch.cuda.set_device(0)
     base = ServeConfig(keys_per_n=args.keys_per_n, requests=args.requests,
                        max_batch=args.max_batch, slots=args.slots,
-                       a_budget_bytes=int(args.a_budget_gb * (1 << 30)))
+                       a_budget_bytes=None if args.a_budget_gb is None
+                       else int(args.a_budget_gb * (1 << 30)))
     store = KeyStore(base, torch.device("cuda", 0))
     for rate in [float(x) for x in args.rates.split(",")]:
         for plain in ([False] if args.no_plain else [False, True]):
