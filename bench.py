@@ -54,8 +54,9 @@ def peaks():
 class ClockSampler:
     """nvidia-smi clock / throttle sampling during the timed region."""
 
-    def __init__(self, index: int):
+    def __init__(self, index: int, period_ms: int = 200):
         self.index = index
+        self.period_ms = period_ms
         self.proc = None
         self.lines = []
 
@@ -66,7 +67,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + q,
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", str(self.period_ms)],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             threading.Thread(target=self._read, daemon=True).start()
         except Exception:
@@ -85,7 +86,7 @@ class ClockSampler:
             self.proc.wait(timeout=2)
         except Exception:
             self.proc.kill()
-        sm, smax, reasons = [], None, set()
+        sm, smax, reasons, watts = [], None, set(), []
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for ln in self.lines:
             f = [x.strip() for x in ln.split(",")]
@@ -96,9 +97,14 @@ class ClockSampler:
                 smax = float(f[2])
             except ValueError:
                 continue
+            try:
+                watts.append(float(f[3]))
+            except ValueError:
+                pass
             for nm, v in zip(names, f[5:9]):
                 if v.lower() == "active":
                     reasons.add(nm)
+        self.watts = watts
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
                 "reasons": sorted(reasons), "samples": len(sm)}
 
@@ -432,6 +438,8 @@ def run_ours(args, rank, world, local_rank):
                 "traffic": traffic_per_launch(dom),
                 "timing": "CUDA events around each launch of direct-launch steps, one stream"}
 
+    energy = None if args.no_energy else energy_measure(kem, torch, stream, local_rank)
+
     # the same step with direct launches (no graph), and on the plain
     # per-request path (CUDA cores, one item per row of CTAs)
     def direct_rate(path):
@@ -486,6 +494,7 @@ def run_ours(args, rank, world, local_rank):
         "kernels_ms_per_step": {k: v[1] / args.steps for k, v in stats.items()},
         "autotune": {"gemm_pair": tuned["gemm_pair"], "gemm_bn": tuned["gemm_bn"],
                      "tensor_min": tuned["tensor_min"]},
+        "energy": energy,
         "served": served,
         "latency_p640_us": latency,
         "as_gbs": sweep["AS_stored"] if sweep else None,
@@ -495,6 +504,40 @@ def run_ours(args, rank, world, local_rank):
     }
     print(json.dumps(line))
     return 0
+
+
+def energy_measure(kem, torch, stream, local_rank: int, seconds: float = 3.0):
+    """Energy to solution of the step: the captured graph replayed back to
+    back for a few seconds while nvidia-smi samples board power every 100 ms;
+    energy = mean power x elapsed time (the samples integrated at a uniform
+    period), reported per step and as pairs per joule."""
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    for _ in range(20):
+        kem.replay()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    steps = 0
+    clk = ClockSampler(local_rank, period_ms=100)
+    clk.start()
+    a.record(stream)
+    while time.perf_counter() - t0 < seconds:
+        for _ in range(100):
+            kem.replay()
+        steps += 100
+        torch.cuda.synchronize()
+    b.record(stream)
+    torch.cuda.synchronize()
+    info = clk.stop()
+    watts = getattr(clk, "watts", [])
+    if not watts:
+        return None
+    el = a.elapsed_time(b) / 1e3
+    p_avg = statistics.mean(watts)
+    pairs = steps * kem.count
+    return {"mean_board_w": p_avg, "samples": len(watts), "seconds": el, "steps": steps,
+            "joules_per_step": p_avg * el / steps, "pairs_per_joule": pairs / (p_avg * el),
+            "sm_mhz": info.get("sm_mhz"), "reasons": info.get("reasons")}
 
 
 def serve_measure(torch, rates=(1e3, 1e4, 1e5, 1e6), requests: int = 20000):
@@ -667,6 +710,7 @@ def main():
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-sweep", action="store_true")
     ap.add_argument("--no-large", action="store_true")
+    ap.add_argument("--no-energy", action="store_true")
     ap.add_argument("--sweep-only", type=str, default=None, metavar="N[,N...]",
                     help="only the standalone kernel sweep at these n (prints its JSON, not the bench line)")
     ap.add_argument("--cpu-s", type=float, default=12.0)
