@@ -131,9 +131,9 @@ size_t ct_bytes(const lwe_params &p) { return 16 * (size_t)p.n + 128; }
 uint32_t mu_bytes(const lwe_params &p) { return 8 * p.B; }
 
 const char *kKernelNames[KID_COUNT] = {
-    "k_expand_A", "k_noise",        "k_keygen_seeds", "k_mul_as",     "k_decrypt",
-    "k_mul_sa",   "k_mul_sa_fused", "k_v_encode",     "k_tree",        "k_final_key",
-    "k_derive",   "k_limbs",        "k_gemm_tc"};
+    "k_expand_A", "k_noise",    "k_keygen_seeds", "k_mul_as", "k_decrypt",
+    "k_sa",       "k_sa_fused", "k_v_encode",     "k_tree",   "k_final_key",
+    "k_derive",   "k_limbs",    "k_gemm_tc"};
 
 }  // namespace
 
