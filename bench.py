@@ -438,7 +438,11 @@ def run_ours(args, rank, world, local_rank):
                 "traffic": traffic_per_launch(dom),
                 "timing": "CUDA events around each launch of direct-launch steps, one stream"}
 
-    energy = None if args.no_energy else energy_measure(kem, torch, stream, local_rank)
+    # the per-GPU extras (energy, plain path, serving, latency, sweeps, the
+    # CPU baseline) are measured at N = 1; a multi-GPU run reports the
+    # replicas' throughput only, so the other GPUs are not held meanwhile
+    extras = world == 1
+    energy = energy_measure(kem, torch, stream, local_rank) if extras and not args.no_energy else None
 
     # the same step with direct launches (no graph), and on the plain
     # per-request path (CUDA cores, one item per row of CTAs)
@@ -460,16 +464,16 @@ def run_ours(args, rank, world, local_rank):
         kem.ctx.set_path(lwe.PATH_TENSOR)
         return COUNT / (statistics.median(ts) / 1e3)
 
-    plain = None if args.no_plain else direct_rate(lwe.PATH_SKINNY)
+    plain = direct_rate(lwe.PATH_SKINNY) if extras and not args.no_plain else None
     kem.close()
 
-    served = None if args.no_serve else serve_measure(torch)
-    latency = None if args.no_latency else single_request_latency(lwe, torch, dev)
-    sweep = None if args.no_sweep else kernel_sweep(lwe, torch, dev, flush)
-    large = None if args.no_large else large_n(lwe, torch, dev)
+    served = serve_measure(torch) if extras and not args.no_serve else None
+    latency = single_request_latency(lwe, torch, dev) if extras and not args.no_latency else None
+    sweep = kernel_sweep(lwe, torch, dev, flush) if extras and not args.no_sweep else None
+    large = large_n(lwe, torch, dev) if extras and not args.no_large else None
 
     cpu = None
-    if not args.no_cpu:
+    if extras and not args.no_cpu:
         rate, threads, pairs, el = cpu_oracle_rate(target_s=args.cpu_s)
         cpu = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
                "sample": "%d Encaps+Decaps pairs of the P976 workload (A given), %.1f s" % (pairs, el)}
