@@ -724,11 +724,16 @@ __global__ void k_keygen_seeds(KeygenSeedArgs a) {
 // compile-time state indices (nothing leaves the registers):
 //   Encaps: mu = H(0x4D || coins)[0 : 8 B]
 //   K' = H(pkh || mu),  seedSE' = H(0x01 || pkh || mu)[0 : 16]
-__global__ void k_derive(DeriveArgs a) {
+// K' and seedSE' do not depend on each other: a CTA of two warps takes 32
+// items, warp 0 computing K' and warp 1 seedSE' and its key schedule (both
+// warps hash mu themselves), so each item waits for two permutations in
+// Encaps and one in Decaps instead of three and two.
+__global__ void __launch_bounds__(64) k_derive(DeriveArgs a) {
   __shared__ uint32_t sT0[256];  // the key expansion's S-box lookups stay on chip
   for (uint32_t i = threadIdx.x; i < 256; i += blockDim.x) sT0[i] = g_aes_T0[i];
   __syncthreads();
-  const uint32_t e = blockIdx.x * blockDim.x + threadIdx.x;
+  const uint32_t w = threadIdx.x >> 5;
+  const uint32_t e = blockIdx.x * 32 + (threadIdx.x & 31);
   if (e >= a.count) return;
   uint64_t s[25];
   uint64_t *mu64 = reinterpret_cast<uint64_t *>(a.mu + 32 * (size_t)e);
@@ -739,7 +744,7 @@ __global__ void k_derive(DeriveArgs a) {
 #pragma unroll
     for (int i = 0; i < 4; i++) {
       x[4 + i] = (uint32_t)i < nb ? s[i] : 0;
-      mu64[i] = x[4 + i];
+      if (w == 0) mu64[i] = x[4 + i];
     }
   } else {
 #pragma unroll
@@ -747,17 +752,20 @@ __global__ void k_derive(DeriveArgs a) {
   }
   const uint8_t *pkh = a.pkh_ptrs ? a.pkh_ptrs[e] + a.pkh_off : a.pkh + (size_t)e * a.pkh_stride;
   load32_le(pkh, x);
-  // K' = H(pkh || mu): 32 + 8 nb bytes, padding opens lane 4 + nb
   // (every lane is written unconditionally with a selected value: a
   // conditional store to lane 4 + nb would become a dynamically indexed
   // state, i.e. local memory)
+  if (w == 0) {
+    // K' = H(pkh || mu): 32 + 8 nb bytes, padding opens lane 4 + nb
 #pragma unroll
-  for (int i = 0; i < 25; i++) s[i] = i < 8 ? x[i] : 0;
+    for (int i = 0; i < 25; i++) s[i] = i < 8 ? x[i] : 0;
 #pragma unroll
-  for (int i = 5; i < 9; i++) s[i] ^= (uint32_t)i == 4 + nb ? 0x06ull : 0ull;
-  s[SHA3_RATE / 8 - 1] ^= 0x8000000000000000ull;
-  keccak_f1600(s);
-  sha3_digest(s, a.kprime + 32 * (size_t)e);
+    for (int i = 5; i < 9; i++) s[i] ^= (uint32_t)i == 4 + nb ? 0x06ull : 0ull;
+    s[SHA3_RATE / 8 - 1] ^= 0x8000000000000000ull;
+    keccak_f1600(s);
+    sha3_digest(s, a.kprime + 32 * (size_t)e);
+    return;
+  }
   // seedSE' = H(0x01 || pkh || mu): the same lanes one byte later; the
   // padding byte lands in byte 1 of lane 4 + nb
   s[0] = 0x01 | (x[0] << 8);
@@ -1029,7 +1037,7 @@ void launch_keygen_seeds(const KeygenSeedArgs &a, cudaStream_t st) {
 }
 
 void launch_derive(const DeriveArgs &a, cudaStream_t st) {
-  k_derive<<<(a.count + 63) / 64, 64, 0, st>>>(a);
+  k_derive<<<(a.count + 31) / 32, 64, 0, st>>>(a);
 }
 
 // One CTA per SM where the batch allows (the leaf work is one wave: CTAs of
