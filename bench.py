@@ -431,7 +431,15 @@ def run_ours(args, rank, world, local_rank):
             peak = AES_PEAK_GBS
         else:
             peak = KECCAK_PEAK_GPERMS
+        probe = probe_peaks(torch, stream) if bound == "alu" else None
+        if probe is not None:
+            mp = probe["aes_gbs"] if dom == "k_noise" else probe["keccak_gperms"]
+            probe = {"peak": mp, "frac": ach / mp, "unit": unit,
+                     "how": "lwe_probe: the kernel's instruction sequence without memory traffic, "
+                            "best of 3 launches; 'peak' is the figure derived from unit counts "
+                            "at the maximum SM clock"}
         roof = {"bound": bound, "achieved": ach, "peak": peak, "unit": unit, "frac": ach / peak,
+                "measured_peak": probe,
                 "kernel": dom, "launches_per_step": nl / args.steps,
                 "share": kernel_total[dom] / sum(kernel_total.values()),
                 "algorithmic_bytes": algorithmic_bytes(p, COUNT).get(dom, 0.0) / (nl / args.steps),
@@ -508,6 +516,32 @@ def run_ours(args, rank, world, local_rank):
     }
     print(json.dumps(line))
     return 0
+
+
+def probe_peaks(torch, stream):
+    """Practical peaks of the two integer-bound instruction sequences on
+    this GPU: Keccak-f[1600] in registers (k_tree's permutation) and AES
+    counter blocks with the shared-memory round tables (k_noise's
+    generator), no memory traffic (lwe_probe).  Best of three launches."""
+    from paper_2606_01211_gb300 import lwe
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    out = {}
+    for kind, ctas, threads, iters, scale, key in (
+            (lwe.PROBE_KECCAK, 3 * sms, 256, 512, 1e9, "keccak_gperms"),
+            (lwe.PROBE_AES, sms, 512, 16384, 1e9 / 16, "aes_gbs")):
+        sink = torch.empty(ctas * 512, dtype=torch.int32, device="cuda")
+        lwe.probe(kind, ctas, iters, sink, stream)
+        ts = []
+        for _ in range(3):
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            lwe.probe(kind, ctas, iters, sink, stream)
+            b.record(stream)
+            b.synchronize()
+            ts.append(a.elapsed_time(b) / 1e3)
+        out[key] = ctas * threads * iters / min(ts) / scale
+    return out
 
 
 def energy_measure(kem, torch, stream, local_rank: int, seconds: float = 3.0):

@@ -281,6 +281,21 @@ uint64_t lwe_ctx_launches(const lwe_ctx *ctx);
  * the next lwe_ctx_device_error() returns LWE_ETIMEOUT (and clears it). */
 int lwe_selftest_bounded_wait(lwe_ctx *ctx, uint32_t limit_us, void *stream);
 
+/* Measurement probes (no counterpart in the paper): the instruction
+ * sequences of the two integer-bound kernels without memory traffic, to
+ * measure their practical peak on the current device.
+ *   LWE_PROBE_KECCAK: `ctas` CTAs of 256 threads; each thread applies
+ *     Keccak-f[1600] `iters` times to a state held in registers (the
+ *     permutation of k_tree).  Work: ctas * 256 * iters permutations.
+ *   LWE_PROBE_AES: `ctas` CTAs of 512 threads with the AES round tables in
+ *     shared memory; each thread encrypts `iters` (even) counter blocks, two
+ *     at a time (the generator of k_noise).  Work: ctas * 512 * iters blocks.
+ * One word per thread is written to sink (device, >= ctas * 512 words) so
+ * that the work is kept.  Asynchronous on `stream`; time it with CUDA events
+ * there.  LWE_EINVAL for an unknown kind, ctas = 0, or an odd iters for AES. */
+enum { LWE_PROBE_KECCAK = 0, LWE_PROBE_AES = 1 };
+int lwe_probe(int kind, uint32_t ctas, uint32_t iters, uint32_t *sink, void *stream);
+
 /* Per-kernel event timing (needs LWE_OPT_TIMING = 1; synchronises). */
 int lwe_ctx_kernel_stats(lwe_ctx *ctx, int kernel_id, uint64_t *launches,
                          double *total_ms);

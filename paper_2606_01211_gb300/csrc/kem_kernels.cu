@@ -934,6 +934,49 @@ __global__ void k_s_to_bf16(const int8_t *__restrict__ S, uint64_t count, uint16
 // ---------------------------------------------------------------------------
 // Host-side launch wrappers (called from lwe_api.cu)
 // ---------------------------------------------------------------------------
+// ---------------------------------------------------------------------------
+// Measurement probes: the instruction sequences of the two integer-bound
+// kernels without memory traffic, for their practical peak on this GPU.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_probe_keccak(uint32_t iters, uint32_t *sink) {
+  const uint32_t gid = blockIdx.x * blockDim.x + threadIdx.x;
+  uint64_t s[25];
+#pragma unroll
+  for (int i = 0; i < 25; i++) s[i] = ((uint64_t)gid << 32) ^ (uint64_t)(i * 0x9E3779B9u);
+  for (uint32_t it = 0; it < iters; it++) keccak_f1600(s);
+  sink[gid] = (uint32_t)(s[0] ^ s[7] ^ s[24]);
+}
+
+__global__ void __launch_bounds__(512, 1) k_probe_aes(uint32_t iters, uint32_t *sink) {
+  extern __shared__ uint32_t sT[];
+  aes_fill_smem(sT, g_aes_T0);
+  __syncthreads();
+  const AesTab tab = aes_tab(sT);
+  const uint32_t gid = blockIdx.x * blockDim.x + threadIdx.x;
+  uint32_t key[4] = {gid, gid * 0x9E3779B9u, ~gid, gid ^ 0x5A5A5A5Au}, rk[44];
+  aes_key_expand(tab, key, rk);
+  uint32_t acc = 0;
+  const uint64_t base = (uint64_t)gid * iters;
+  for (uint32_t b = 0; b < iters; b += 2) {  // two blocks in flight, as in k_noise
+    const uint4 v = aes_ctr_block(tab, rk, 3, base + b);
+    const uint4 w = aes_ctr_block(tab, rk, 3, base + b + 1);
+    acc ^= v.x ^ v.y ^ v.z ^ v.w ^ w.x ^ w.y ^ w.z ^ w.w;
+  }
+  sink[gid] = acc;
+}
+
+int launch_probe(int kind, uint32_t ctas, uint32_t iters, uint32_t *sink, cudaStream_t st) {
+  if (kind == 0) {
+    k_probe_keccak<<<ctas, 256, 0, st>>>(iters, sink);
+    return 0;
+  }
+  if (kind == 1) {
+    k_probe_aes<<<ctas, 512, AES_SMEM_BYTES, st>>>(iters, sink);
+    return 0;
+  }
+  return -1;
+}
+
 static int grid_for(uint64_t work, int per_cta, int max_ctas) {
   uint64_t g = (work + per_cta - 1) / per_cta;
   if (g > (uint64_t)max_ctas) g = max_ctas;
@@ -957,6 +1000,8 @@ cudaError_t lwe_kernel_smem_setup() {
   e = cudaFuncSetAttribute(k_sa_fused<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, fused_smem);
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_sa_fused<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, fused_smem);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_probe_aes, cudaFuncAttributeMaxDynamicSharedMemorySize, AES_SMEM_BYTES);
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_limbs, cudaFuncAttributeMaxDynamicSharedMemorySize, AES_SMEM_BYTES);
   return e;

@@ -1046,6 +1046,16 @@ int lwe_encaps_noalloc(const lwe_params *p, const uint8_t *pk, const uint16_t *A
   return hash_tree(&c, ct, ctb, (uint32_t)ctb, count, TREE_ENC_KEY, K, 32, nullptr, 0, st);
 }
 
+int lwe_probe(int kind, uint32_t ctas, uint32_t iters, uint32_t *sink, void *stream) {
+  if ((kind != LWE_PROBE_KECCAK && kind != LWE_PROBE_AES) || ctas == 0 || !sink ||
+      (kind == LWE_PROBE_AES && (iters & 1)))
+    return LWE_EINVAL;
+  int rc = current_device_setup(nullptr, nullptr);
+  if (rc) return rc;
+  launch_probe(kind, ctas, iters, sink, (cudaStream_t)stream);
+  return check_launch();
+}
+
 int lwe_selftest_bounded_wait(lwe_ctx *c, uint32_t limit_us, void *stream) {
   if (!c || limit_us == 0 || limit_us > 2000000) return LWE_EINVAL;
   int rc = set_device_of(c);

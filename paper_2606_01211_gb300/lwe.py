@@ -73,6 +73,7 @@ def _load():
         "lwe_matmul_modq": (i32, [vp, i32, vp, vp, vp, u32, u32, u32, vp, vp, vp]),
         "lwe_encaps_noalloc": (i32, [P, vp, vp, vp, u32, vp, vp, vp]),
         "lwe_selftest_bounded_wait": (i32, [vp, u32, vp]),
+        "lwe_probe": (i32, [i32, u32, u32, vp, vp]),
         "lwe_strerror": (C.c_char_p, [i32]),
         "lwe_last_cuda_error": (C.c_char_p, []),
         "lwe_ctx_device_error": (i32, [vp]),
@@ -333,3 +334,14 @@ def matmul_modq(side: int, S: torch.Tensor, out: torch.Tensor, n: int, logq: int
 
 def kernel_names():
     return [_lib.lwe_kernel_name(i).decode() for i in range(_lib.lwe_num_kernels())]
+
+
+PROBE_KECCAK, PROBE_AES = 0, 1
+
+
+def probe(kind: int, ctas: int, iters: int, sink: torch.Tensor, stream=None):
+    """Measurement probe (lwe_probe): Keccak-f in registers or AES blocks
+    with the shared-memory tables, no memory traffic; sink is an int32
+    device tensor of at least ctas * 512 words."""
+    _check(_lib.lwe_probe(kind, ctas, iters, _ptr(sink, torch.int32, ctas * 512 * 4, "sink"),
+                          _stream(stream)), "lwe_probe")
