@@ -140,11 +140,18 @@ enum {
                                 SMs share a 256 x 128 tile, tcgen05
                                 cta_group::2; LWE_OPT_GEMM_BN is then
                                 ignored); 0: one CTA per 128 x BN tile        */
-  LWE_OPT_SERIAL = 6         /* 1: work that normally overlaps on the
+  LWE_OPT_SERIAL = 6,        /* 1: work that normally overlaps on the
                                 context's side stream (the tensor path's
                                 limbs, Decaps' H(c)) runs on the caller's
                                 stream, so that per-kernel timings measure
                                 each kernel alone; 0 (default): overlapped   */
+  LWE_OPT_TREE_WARP_MAX = 7  /* tree hashes (H(pk), H(c)) of at most this
+                                many messages per launch run with one Keccak
+                                state per warp (the lanes of the state
+                                spread over the threads: lower latency),
+                                more with one state per thread (higher
+                                throughput).  -1 (default): the number of
+                                SMs; 0: always one state per thread         */
 };
 int lwe_ctx_set_option(lwe_ctx *ctx, int option, int64_t value);
 
@@ -290,10 +297,13 @@ int lwe_selftest_bounded_wait(lwe_ctx *ctx, uint32_t limit_us, void *stream);
  *   LWE_PROBE_AES: `ctas` CTAs of 512 threads with the AES round tables in
  *     shared memory; each thread encrypts `iters` (even) counter blocks, two
  *     at a time (the generator of k_noise).  Work: ctas * 512 * iters blocks.
+ *   LWE_PROBE_KECCAK_WARP: `ctas` CTAs of one warp; each warp applies
+ *     Keccak-f[1600] `iters` times to one state spread over its lanes (the
+ *     permutation of k_tree_warp).  Work: ctas * iters permutations.
  * One word per thread is written to sink (device, >= ctas * 512 words) so
  * that the work is kept.  Asynchronous on `stream`; time it with CUDA events
  * there.  LWE_EINVAL for an unknown kind, ctas = 0, or an odd iters for AES. */
-enum { LWE_PROBE_KECCAK = 0, LWE_PROBE_AES = 1 };
+enum { LWE_PROBE_KECCAK = 0, LWE_PROBE_AES = 1, LWE_PROBE_KECCAK_WARP = 2 };
 int lwe_probe(int kind, uint32_t ctas, uint32_t iters, uint32_t *sink, void *stream);
 
 /* Per-kernel event timing (needs LWE_OPT_TIMING = 1; synchronises). */

@@ -22,7 +22,7 @@
 #include "common.cuh"
 #include "gemm_tc.h"
 #include "kem_kernels.h"
-#include "keccak.cuh"
+#include "keccak_warp.cuh"
 
 // The round table T0 (see aes.cuh); written by lwe_upload_aes_table.
 __device__ uint32_t g_aes_T0[256];
@@ -833,6 +833,48 @@ __global__ void __launch_bounds__(TREE_MAX_THREADS) k_tree(TreeArgs a) {
   sha3_digest(s, a.out + 32 * (size_t)e);
 }
 
+// Tree hash with one Keccak state per warp (keccak_warp.cuh), for launches
+// of few messages, where one state per thread would leave the GPU idle
+// behind a chain of sequential permutations: a CTA per message, warp w
+// hashes chunks w, w + W, ...; warp 0 then hashes the digests (the root)
+// and, for Encaps, derives the key.
+__global__ void __launch_bounds__(TREE_WARP_MAX_THREADS) k_tree_warp(TreeArgs a) {
+  extern __shared__ uint64_t sdig[];  // [m][4]
+  const uint32_t e = blockIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const uint32_t nw = blockDim.x >> 5, t = lane % 25;
+  const KeccakWarpMap km = keccak_warp_map(lane);
+  const uint8_t *msg = a.msg_ptrs ? a.msg_ptrs[e] : a.msgs + (size_t)e * a.stride;
+  for (uint32_t c = warp; c < a.m; c += nw) {
+    const uint32_t off = c * LWE_TREE_CHUNK;
+    const uint64_t v =
+        sha3_256_warp_chunk(km, msg + off, min((uint32_t)LWE_TREE_CHUNK, a.len - off), lane);
+    if (lane < 4) sdig[4 * c + lane] = v;
+  }
+  __syncthreads();
+  if (warp != 0) return;
+  uint64_t v = sha3_256_warp_mem(km, sdig, 32 * a.m, lane);
+  uint8_t *out;
+  if (a.mode == TREE_DIGEST) {
+    if (a.out2 && lane < 4) {
+      uint8_t *o2 = a.out2 + (size_t)e * a.out2_stride + 8 * lane;
+      for (int b = 0; b < 8; b++) o2[b] = (uint8_t)(v >> (8 * b));
+    }
+    out = a.out + (size_t)e * a.out_stride;
+  } else {
+    // Encaps (Alg. 4): K = H(K' || H(c)), one 64-byte block
+    const uint64_t hc = shfl64(v, (lane - 4) & 31);  // lanes 4..7 take the digest
+    uint64_t w = 0;
+    if (t < 4) w = reinterpret_cast<const uint64_t *>(a.kprime + 32 * (size_t)e)[t];
+    else if (t < 8) w = hc;
+    if (t == 8) w ^= 0x06;
+    if (t == SHA3_RATE / 8 - 1) w ^= 0x8000000000000000ull;
+    v = keccak_f1600_warp(km, w);
+    out = a.out + 32 * (size_t)e;
+  }
+  if (lane < 4)
+    for (int b = 0; b < 8; b++) out[8 * lane + b] = (uint8_t)(v >> (8 * b));
+}
+
 __global__ void __launch_bounds__(128) k_final_key(FinalKeyArgs a) {
   const uint32_t e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= a.count) return;
@@ -965,6 +1007,14 @@ __global__ void __launch_bounds__(512, 1) k_probe_aes(uint32_t iters, uint32_t *
   sink[gid] = acc;
 }
 
+__global__ void __launch_bounds__(32) k_probe_keccak_warp(uint32_t iters, uint32_t *sink) {
+  const uint32_t lane = threadIdx.x, t = lane % 25;
+  const KeccakWarpMap km = keccak_warp_map(lane);
+  uint64_t v = ((uint64_t)blockIdx.x << 32) ^ (uint64_t)(t * 0x9E3779B9u);
+  for (uint32_t it = 0; it < iters; it++) v = keccak_f1600_warp(km, v);
+  sink[32 * blockIdx.x + lane] = (uint32_t)(v ^ (v >> 32));
+}
+
 int launch_probe(int kind, uint32_t ctas, uint32_t iters, uint32_t *sink, cudaStream_t st) {
   if (kind == 0) {
     k_probe_keccak<<<ctas, 256, 0, st>>>(iters, sink);
@@ -972,6 +1022,10 @@ int launch_probe(int kind, uint32_t ctas, uint32_t iters, uint32_t *sink, cudaSt
   }
   if (kind == 1) {
     k_probe_aes<<<ctas, 512, AES_SMEM_BYTES, st>>>(iters, sink);
+    return 0;
+  }
+  if (kind == 2) {
+    k_probe_keccak_warp<<<ctas, 32, 0, st>>>(iters, sink);
     return 0;
   }
   return -1;
@@ -1088,8 +1142,13 @@ void launch_derive(const DeriveArgs &a, cudaStream_t st) {
 // One CTA per SM where the batch allows (the leaf work is one wave: CTAs of
 // equal size spread it evenly), at most TREE_MAX_THREADS threads and 48 KB
 // of digests per CTA.
-void launch_tree(TreeArgs &a, int num_sms, cudaStream_t st) {
+void launch_tree(TreeArgs &a, int num_sms, uint32_t warp_max, cudaStream_t st) {
   a.m = (a.len + LWE_TREE_CHUNK - 1) / LWE_TREE_CHUNK;
+  if (a.count <= warp_max) {
+    const uint32_t w = std::min<uint32_t>(a.m, TREE_WARP_MAX_THREADS / 32);
+    k_tree_warp<<<a.count, 32 * w, (size_t)a.m * 32, st>>>(a);
+    return;
+  }
   uint32_t t = 1;
   while (t < a.m && t < 256) t <<= 1;
   a.tpi = t;

@@ -119,6 +119,7 @@ struct DeriveArgs {
 
 enum { TREE_DIGEST = 0, TREE_ENC_KEY = 1 };
 #define TREE_MAX_THREADS 448  // 14 warps
+#define TREE_WARP_MAX_THREADS 512  // 16 warps, one chunk each
 
 // Tree hash of `count` messages of `len` bytes (item e at msgs + e*stride,
 // or msg_ptrs[e]): leaves and root in one kernel, the leaf digests kept in
@@ -165,7 +166,8 @@ void launch_mul_sa(const MulSaArgs &a, uint32_t items, bool fused, bool cmp, int
 void launch_v_encode(const VEncArgs &a, uint32_t count, bool cmp, cudaStream_t st);
 void launch_keygen_seeds(const KeygenSeedArgs &a, cudaStream_t st);
 void launch_derive(const DeriveArgs &a, cudaStream_t st);
-void launch_tree(TreeArgs &a, int num_sms, cudaStream_t st);
+// launches of at most warp_max messages hash with one Keccak state per warp
+void launch_tree(TreeArgs &a, int num_sms, uint32_t warp_max, cudaStream_t st);
 // measurement probes: kind 0 Keccak-f in registers (256-thread CTAs),
 // kind 1 AES counter blocks with the shared-memory tables (512 threads)
 int launch_probe(int kind, uint32_t ctas, uint32_t iters, uint32_t *sink, cudaStream_t st);

@@ -154,6 +154,7 @@ struct lwe_ctx {
   int gemm_bn = 128;
   int gemm_pair = 1;
   bool serial = false;  // LWE_OPT_SERIAL: side-stream work on the caller's stream
+  int64_t tree_warp_max = -1;  // LWE_OPT_TREE_WARP_MAX; -1: the number of SMs
   bool timing = false;
   uint64_t launches = 0;
   std::vector<TimedLaunch> pending;
@@ -448,7 +449,9 @@ void tree_hash(lwe_ctx *c, const uint8_t *msgs, uint64_t stride, uint32_t len, u
   ta.out2 = out2;
   ta.out2_stride = out2_stride;
   ta.kprime = c->kp;
-  LAUNCH(c, KID_TREE, st, launch_tree(ta, c->num_sms, st));
+  const uint32_t warp_max =
+      c->tree_warp_max < 0 ? (uint32_t)c->num_sms : (uint32_t)c->tree_warp_max;
+  LAUNCH(c, KID_TREE, st, launch_tree(ta, c->num_sms, warp_max, st));
 }
 
 int hash_tree(lwe_ctx *c, const uint8_t *msgs, uint64_t stride, uint32_t len, uint32_t count,
@@ -680,6 +683,10 @@ int lwe_ctx_set_option(lwe_ctx *c, int option, int64_t value) {
     case LWE_OPT_GEMM_PAIR:
       if (value != 0 && value != 1) return LWE_EINVAL;
       c->gemm_pair = (int)value;
+      return LWE_OK;
+    case LWE_OPT_TREE_WARP_MAX:
+      if (value < -1 || value > 0xffffffffLL) return LWE_EINVAL;
+      c->tree_warp_max = value;
       return LWE_OK;
     case LWE_OPT_GEMM_KCHUNK:
       if (value == 0) {
@@ -1047,7 +1054,7 @@ int lwe_encaps_noalloc(const lwe_params *p, const uint8_t *pk, const uint16_t *A
 }
 
 int lwe_probe(int kind, uint32_t ctas, uint32_t iters, uint32_t *sink, void *stream) {
-  if ((kind != LWE_PROBE_KECCAK && kind != LWE_PROBE_AES) || ctas == 0 || !sink ||
+  if (kind < LWE_PROBE_KECCAK || kind > LWE_PROBE_KECCAK_WARP || ctas == 0 || !sink ||
       (kind == LWE_PROBE_AES && (iters & 1)))
     return LWE_EINVAL;
   int rc = current_device_setup(nullptr, nullptr);

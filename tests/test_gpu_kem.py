@@ -79,12 +79,14 @@ def test_keygen_matches_oracle(name, stored):
 
 # --------------------------------------------------------- Encaps / Decaps --
 
-def _kem_case(name, count, path, stored, seed=21):
+def _kem_case(name, count, path, stored, seed=21, options=()):
     cfg = SMALL[name] if name in SMALL else PRESETS[name]
     p, po = params(**cfg)
     pk_o, sk_o, A_o, ms = oracle_keys(cfg_key(cfg), seed)
     ctx = lwe.Ctx(p, max_batch=count)
     ctx.set_path(path)
+    for opt, val in options:
+        ctx.set_option(opt, val)
     pk, sk = ctx.empty_pk(1), ctx.empty_sk(1)
     A = torch.empty((p.n, p.n), dtype=torch.int16, device="cuda") if stored else None
     ctx.keygen(dev(ms[None, :]), pk, sk, A_out=A)
@@ -108,6 +110,26 @@ def test_encaps_decaps_skinny_match_oracle(name, stored):
         assert np.array_equal(ct_h[i], ct_o), i
         assert np.array_equal(K_h[i], K_o), i
         assert np.array_equal(K2_h[i], K_o), i
+    assert ctx.device_error() == 0
+
+
+@pytest.mark.parametrize("name", ["n16", "P640", "P976", "P1344"])
+@pytest.mark.parametrize("warp_max", [0, 1 << 20])
+def test_tree_hash_forms_match_oracle(name, warp_max):
+    """The tree hashes (H(pk) in Encaps, H(c) with the Encaps key, H(c) in
+    Decaps) with one Keccak state per thread (warp_max 0) and with one state
+    per warp (every launch at most warp_max messages), on 37 items: the
+    ciphertexts and both keys equal the oracle's."""
+    count = 37
+    ctx, p, po, pk_o, sk_o, A_o, cs, ct, K, K2, *_ = _kem_case(
+        name, count, lwe.PATH_SKINNY, True, seed=23,
+        options=((lwe.OPT_TREE_WARP_MAX, warp_max),))
+    ct_h, K_h, K2_h = host(ct), host(K), host(K2)
+    for i in (0, 1, 17, count - 1):
+        ct_o, K_o = O.encaps(po, pk_o, bytes(cs[i]), A=A_o)
+        assert np.array_equal(ct_h[i], ct_o), i
+        assert np.array_equal(K_h[i], K_o), i
+    assert np.array_equal(K_h, K2_h)
     assert ctx.device_error() == 0
 
 

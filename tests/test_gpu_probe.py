@@ -118,12 +118,34 @@ def test_probe_matches_definition(kind, threads, iters):
 
 
 @pytest.mark.gpu
+@pytest.mark.parametrize("iters", [1, 2])
+def test_warp_probe_matches_definition(iters):
+    """One state per warp (lane t of the state on thread t, threads 25..31
+    mirroring 0..6): the same permutation as the definition."""
+    import torch
+    from paper_2606_01211_gb300 import lwe
+    torch.cuda.set_device(0)
+    ctas = 3
+    sink = torch.zeros(ctas * 512, dtype=torch.int32, device="cuda")
+    lwe.probe(lwe.PROBE_KECCAK_WARP, ctas, iters, sink)
+    torch.cuda.synchronize()
+    got = sink.cpu().numpy().view(np.uint32)
+    for g in range(ctas):
+        s = [((g << 32) ^ ((t * 0x9E3779B9) & 0xFFFFFFFF)) & M64 for t in range(25)]
+        for _ in range(iters):
+            s = keccak_f(s)
+        for lane in range(32):
+            v = s[lane % 25]
+            assert int(got[32 * g + lane]) == (v ^ (v >> 32)) & 0xFFFFFFFF, (g, lane)
+
+
+@pytest.mark.gpu
 def test_probe_rejects_bad_arguments():
     import torch
     from paper_2606_01211_gb300 import lwe
     torch.cuda.set_device(0)
     sink = torch.zeros(512, dtype=torch.int32, device="cuda")
-    for kind, ctas, iters in ((2, 1, 2), (0, 0, 2), (1, 1, 3)):
+    for kind, ctas, iters in ((3, 1, 2), (0, 0, 2), (1, 1, 3)):
         with pytest.raises(Exception):
             lwe.probe(kind, ctas, iters, sink)
     with pytest.raises(ValueError):
