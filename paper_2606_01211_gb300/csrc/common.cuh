@@ -25,6 +25,57 @@ enum LweKernel {
   KID_COUNT
 };
 
+// ---- programmatic dependent launch --------------------------------------
+// The kernels of the Encaps / Decaps chain are launched with programmatic
+// stream serialisation when the context enables it (LWE_OPT_PDL): the next
+// kernel of the stream may start while this one drains and run its
+// prologue (shared-memory tables, barriers, tensor-memory allocation), then
+// waits in pdl_wait() until the previous grid has completed and its memory
+// is visible.  Every kernel launched this way calls pdl_wait() in every
+// thread before it reads or writes memory that another kernel of the
+// stream touches; without the launch attribute both instructions are no-ops.
+LWE_DEV void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+LWE_DEV void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+extern thread_local bool g_launch_pdl;  // set around a context's launches
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_k(void (*k)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                            cudaStream_t st, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = g_launch_pdl ? 1 : 0;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k, args...);
+}
+
+// The same with thread-block clusters of `cluster` CTAs along x.
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_k_cluster(void (*k)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                                    cudaStream_t st, unsigned cluster, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[2];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = g_launch_pdl ? 1 : 0;
+  at[1].id = cudaLaunchAttributeClusterDimension;
+  at[1].val.clusterDim.x = cluster;
+  at[1].val.clusterDim.y = 1;
+  at[1].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 2;
+  return cudaLaunchKernelEx(&cfg, k, args...);
+}
+
 // Device-side error word values (set by bounded waits that ran out).
 #define LWE_DEVERR_TIMEOUT 1u
 

@@ -436,6 +436,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * STAGES + 5);
   volatile uint32_t *abort_flag = tmem_slot + 1;
 
+  pdl_trigger();
   const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t num_m = (a.rows + BM - 1) / BM;
   const uint32_t num_n = (a.ncols + BN - 1) / BN;
@@ -477,6 +478,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem_base = *tmem_slot;
+  pdl_wait();  // the operands are written by the previous kernels of the stream
 
   if (warp == 0 && lane == 0) {
     // ---------------- TMA producer ----------------
@@ -593,6 +595,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHREADS2, 1)
   uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * STAGES2 + 5);
   volatile uint32_t *abort_flag = tmem_slot + 1;
 
+  pdl_trigger();
   const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t rank = cluster_rank();
   const bool leader = rank == 0;
@@ -638,6 +641,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHREADS2, 1)
   cluster_sync();  // the peer's barriers exist before any copy or arrive targets them
   tc_fence_after();
   const uint32_t tmem_base = *tmem_slot;
+  pdl_wait();  // the operands are written by the previous kernels of the stream
 
   if (warp == 0 && lane == 0) {
     // ---------------- TMA producer (both CTAs) ----------------
@@ -800,7 +804,7 @@ int launch_bn(const GemmSaArgs &a, int num_sms, cudaStream_t st) {
   if (!make_map(&tmL, a.limbs, 3, dL, sL, bL)) return LWE_ECUDA;
   const uint32_t tiles = ((a.rows + BM - 1) / BM) * ((a.ncols + BN - 1) / BN);
   const int grid = (int)(tiles < (uint32_t)num_sms ? tiles : (uint32_t)num_sms);
-  k_gemm_sa<BN><<<grid, NTHREADS, C::SMEM, st>>>(tmS, tmL, a);
+  launch_k(k_gemm_sa<BN>, grid, NTHREADS, C::SMEM, st, tmS, tmL, a);
   return LWE_OK;
 }
 
@@ -817,7 +821,7 @@ int launch_pair(const GemmSaArgs &a, int num_sms, cudaStream_t st) {
   const uint32_t tiles = ((a.rows + 2 * BM - 1) / (2 * BM)) * ((a.ncols + BN2 - 1) / BN2);
   const uint32_t pairs = (uint32_t)(num_sms / 2);
   const uint32_t clusters = tiles < pairs ? tiles : pairs;
-  k_gemm_sa2<<<2 * clusters, NTHREADS2, Cfg2::SMEM, st>>>(tmS, tmL, a);
+  launch_k(k_gemm_sa2, 2 * clusters, NTHREADS2, Cfg2::SMEM, st, tmS, tmL, a);
   return LWE_OK;
 }
 

@@ -128,9 +128,11 @@ LWE_DEV void noise_store(const char *smem, const NoiseOut &o, uint8_t *base, uin
 
 __global__ void __launch_bounds__(512, 1) k_noise(NoiseArgs a) {
   extern __shared__ uint32_t sT[];
+  pdl_trigger();
   aes_fill_smem(sT, g_aes_T0);
   noise_fill_table(sT + NOISE_TAB_OFF / 4, a);
   __syncthreads();
+  pdl_wait();
   const AesTab tab = aes_tab(sT);
   const char *smem = reinterpret_cast<const char *>(sT);
   const uint32_t lane = threadIdx.x & 31;
@@ -330,6 +332,8 @@ __global__ void __launch_bounds__(256) k_mul_as_rows(MulAsArgs a) {
 // Decrypt (Alg. 3): warp r of CTA e computes row r of M = C - B' S and the
 // B message bits of its eight coefficients.
 __global__ void __launch_bounds__(256) k_decrypt(DecryptArgs a) {
+  pdl_trigger();
+  pdl_wait();
   const uint32_t e = blockIdx.x;
   const uint32_t r = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t n = a.n;
@@ -730,8 +734,10 @@ __global__ void k_keygen_seeds(KeygenSeedArgs a) {
 // Encaps and one in Decaps instead of three and two.
 __global__ void __launch_bounds__(64) k_derive(DeriveArgs a) {
   __shared__ uint32_t sT0[256];  // the key expansion's S-box lookups stay on chip
+  pdl_trigger();
   for (uint32_t i = threadIdx.x; i < 256; i += blockDim.x) sT0[i] = g_aes_T0[i];
   __syncthreads();
+  pdl_wait();
   const uint32_t w = threadIdx.x >> 5;
   const uint32_t e = blockIdx.x * 32 + (threadIdx.x & 31);
   if (e >= a.count) return;
@@ -794,6 +800,8 @@ __global__ void __launch_bounds__(64) k_derive(DeriveArgs a) {
 // the root threads' 64-bit reads fall in different banks.
 __global__ void __launch_bounds__(TREE_MAX_THREADS) k_tree(TreeArgs a) {
   extern __shared__ uint64_t sleaf[];  // [ipc][4 m + 1]
+  pdl_trigger();
+  pdl_wait();
   const uint32_t words = 4 * a.m + 1;
   const uint32_t e0 = blockIdx.x * a.ipc;
   {
@@ -835,23 +843,36 @@ __global__ void __launch_bounds__(TREE_MAX_THREADS) k_tree(TreeArgs a) {
 
 // Tree hash with one Keccak state per warp (keccak_warp.cuh), for launches
 // of few messages, where one state per thread would leave the GPU idle
-// behind a chain of sequential permutations: a CTA per message, warp w
-// hashes chunks w, w + W, ...; warp 0 then hashes the digests (the root)
-// and, for Encaps, derives the key.
+// behind a chain of sequential permutations.  A thread-block cluster of Q
+// CTAs (W warps each, on Q SMs, so that few warps share an SM's shuffle
+// unit) takes one message: warp w of CTA q hashes chunks qW + w, qW + w +
+// QW, ... and stores each digest in the shared memory of the cluster's
+// first CTA, whose warp 0 then hashes the digests (the root) and, for
+// Encaps, derives the key.
+LWE_DEV void st_cluster_u64(uint32_t addr, uint64_t v) {
+  asm volatile("st.shared::cluster.u64 [%0], %1;" ::"r"(addr), "l"(v) : "memory");
+}
+
 __global__ void __launch_bounds__(TREE_WARP_MAX_THREADS) k_tree_warp(TreeArgs a) {
-  extern __shared__ uint64_t sdig[];  // [m][4]
-  const uint32_t e = blockIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  extern __shared__ uint64_t sdig[];  // [m][4], used in the cluster's first CTA
+  pdl_trigger();
+  pdl_wait();
+  uint32_t q, nq;
+  asm("mov.u32 %0, %%cluster_ctarank;" : "=r"(q));
+  asm("mov.u32 %0, %%cluster_nctarank;" : "=r"(nq));
+  const uint32_t e = blockIdx.x / nq, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const uint32_t nw = blockDim.x >> 5, t = lane % 25;
   const KeccakWarpMap km = keccak_warp_map(lane);
   const uint8_t *msg = a.msg_ptrs ? a.msg_ptrs[e] : a.msgs + (size_t)e * a.stride;
-  for (uint32_t c = warp; c < a.m; c += nw) {
+  const uint32_t dig0 = cluster_map(sdig, 0);
+  for (uint32_t c = q * nw + warp; c < a.m; c += nq * nw) {
     const uint32_t off = c * LWE_TREE_CHUNK;
     const uint64_t v =
         sha3_256_warp_chunk(km, msg + off, min((uint32_t)LWE_TREE_CHUNK, a.len - off), lane);
-    if (lane < 4) sdig[4 * c + lane] = v;
+    if (lane < 4) st_cluster_u64(dig0 + 8 * (4 * c + lane), v);
   }
-  __syncthreads();
-  if (warp != 0) return;
+  cluster_barrier();  // every digest is in the first CTA's shared memory
+  if (q != 0 || warp != 0) return;
   uint64_t v = sha3_256_warp_mem(km, sdig, 32 * a.m, lane);
   uint8_t *out;
   if (a.mode == TREE_DIGEST) {
@@ -876,6 +897,8 @@ __global__ void __launch_bounds__(TREE_WARP_MAX_THREADS) k_tree_warp(TreeArgs a)
 }
 
 __global__ void __launch_bounds__(128) k_final_key(FinalKeyArgs a) {
+  pdl_trigger();
+  pdl_wait();
   const uint32_t e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= a.count) return;
   // all-ones when the re-encryption matched (flag == 0), else zero
@@ -907,9 +930,13 @@ __global__ void __launch_bounds__(256) k_limbs(GemmLimbArgs a) {
   const uint32_t mq = (1u << a.logq) - 1u, mm = mq | (mq << 16);
   AesTab tab;
   uint32_t rk[44];
+  pdl_trigger();
   if (fused) {
     aes_fill_smem(sT, g_aes_T0);
     __syncthreads();
+  }
+  pdl_wait();
+  if (fused) {
     tab = aes_tab(sT);
     uint32_t key[4];
     aes_load_key(a.seedA, key);
@@ -1070,7 +1097,7 @@ void launch_expand_A(const uint8_t *seeds, uint32_t seed_stride, uint32_t count,
 
 void launch_noise(const NoiseArgs &a, int num_sms, cudaStream_t st) {
   const int g = grid_for((uint64_t)a.count * a.runs_per_item, 16, num_sms);
-  k_noise<<<g, 512, NOISE_SMEM_BYTES, st>>>(a);
+  launch_k(k_noise, g, 512, NOISE_SMEM_BYTES, st, a);
 }
 
 void launch_mul_as(const MulAsArgs &a, uint32_t count, bool fused, int num_sms, cudaStream_t st) {
@@ -1088,7 +1115,7 @@ void launch_mul_as(const MulAsArgs &a, uint32_t count, bool fused, int num_sms, 
 }
 
 void launch_decrypt(const DecryptArgs &a, uint32_t count, cudaStream_t st) {
-  k_decrypt<<<count, 256, 0, st>>>(a);
+  launch_k(k_decrypt, count, 256, 0, st, a);
 }
 
 void launch_mul_sa(const MulSaArgs &a, uint32_t items, bool fused, bool cmp, int num_sms,
@@ -1136,7 +1163,7 @@ void launch_keygen_seeds(const KeygenSeedArgs &a, cudaStream_t st) {
 }
 
 void launch_derive(const DeriveArgs &a, cudaStream_t st) {
-  k_derive<<<(a.count + 31) / 32, 64, 0, st>>>(a);
+  launch_k(k_derive, (a.count + 31) / 32, 64, 0, st, a);
 }
 
 // One CTA per SM where the batch allows (the leaf work is one wave: CTAs of
@@ -1145,8 +1172,10 @@ void launch_derive(const DeriveArgs &a, cudaStream_t st) {
 void launch_tree(TreeArgs &a, int num_sms, uint32_t warp_max, cudaStream_t st) {
   a.m = (a.len + LWE_TREE_CHUNK - 1) / LWE_TREE_CHUNK;
   if (a.count <= warp_max) {
-    const uint32_t w = std::min<uint32_t>(a.m, TREE_WARP_MAX_THREADS / 32);
-    k_tree_warp<<<a.count, 32 * w, (size_t)a.m * 32, st>>>(a);
+    // about four warps per SM: chunks over a cluster of up to 8 CTAs
+    const uint32_t q = std::max<uint32_t>(1, std::min<uint32_t>(8, (a.m + 3) / 4));
+    const uint32_t w = std::min<uint32_t>((a.m + q - 1) / q, TREE_WARP_MAX_THREADS / 32);
+    launch_k_cluster(k_tree_warp, a.count * q, 32 * w, (size_t)a.m * 32, st, q, a);
     return;
   }
   uint32_t t = 1;
@@ -1161,18 +1190,18 @@ void launch_tree(TreeArgs &a, int num_sms, uint32_t warp_max, cudaStream_t st) {
   if (a.ipc == 0) a.ipc = 1;
   const uint32_t threads = (a.ipc * t + 31) / 32 * 32;
   const size_t smem = (size_t)a.ipc * words * 8;
-  k_tree<<<(a.count + a.ipc - 1) / a.ipc, threads, smem, st>>>(a);
+  launch_k(k_tree, (a.count + a.ipc - 1) / a.ipc, threads, smem, st, a);
 }
 
 void launch_final_key(const FinalKeyArgs &a, cudaStream_t st) {
-  k_final_key<<<(a.count + 127) / 128, 128, 0, st>>>(a);
+  launch_k(k_final_key, (a.count + 127) / 128, 128, 0, st, a);
 }
 
 void launch_gemm_limbs(const GemmLimbArgs &a, int num_sms, cudaStream_t st) {
   (void)num_sms;
   const uint32_t ncols = a.n + (a.B ? 8u : 0u);
   dim3 grid((ncols + 63) / 64, (a.n + 63) / 64);
-  k_limbs<<<grid, 256, a.A ? 0 : AES_SMEM_BYTES, st>>>(a);
+  launch_k(k_limbs, grid, 256, a.A ? 0 : AES_SMEM_BYTES, st, a);
 }
 
 void launch_s_to_bf16(const int8_t *S, uint64_t count, uint16_t *out, int num_sms, cudaStream_t st) {

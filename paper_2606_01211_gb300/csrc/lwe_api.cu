@@ -137,6 +137,8 @@ const char *kKernelNames[KID_COUNT] = {
 
 }  // namespace
 
+thread_local bool g_launch_pdl = false;
+
 // ---- context ---------------------------------------------------------------
 struct TimedLaunch {
   int kid;
@@ -154,6 +156,7 @@ struct lwe_ctx {
   int gemm_bn = 128;
   int gemm_pair = 1;
   bool serial = false;  // LWE_OPT_SERIAL: side-stream work on the caller's stream
+  bool pdl = true;      // LWE_OPT_PDL
   int64_t tree_warp_max = -1;  // LWE_OPT_TREE_WARP_MAX; -1: the number of SMs
   bool timing = false;
   uint64_t launches = 0;
@@ -200,7 +203,10 @@ struct LaunchScope {
   cudaStream_t st;
   cudaEvent_t a = nullptr, b = nullptr;
   unsigned flags = cudaEventRecordDefault;
+  bool pdl_before = g_launch_pdl;
   LaunchScope(lwe_ctx *c_, int kid_, cudaStream_t st_) : c(c_), kid(kid_), st(st_) {
+    // per-launch event timing brackets each kernel, so it launches plainly
+    g_launch_pdl = c && c->pdl && !c->timing;
     if (c && c->timing) {
       a = take_event(c);
       b = take_event(c);
@@ -213,6 +219,7 @@ struct LaunchScope {
     }
   }
   ~LaunchScope() {
+    g_launch_pdl = pdl_before;
     if (!c) return;
     c->launches++;
     if (a && b) {
@@ -683,6 +690,10 @@ int lwe_ctx_set_option(lwe_ctx *c, int option, int64_t value) {
     case LWE_OPT_GEMM_PAIR:
       if (value != 0 && value != 1) return LWE_EINVAL;
       c->gemm_pair = (int)value;
+      return LWE_OK;
+    case LWE_OPT_PDL:
+      if (value != 0 && value != 1) return LWE_EINVAL;
+      c->pdl = value != 0;
       return LWE_OK;
     case LWE_OPT_TREE_WARP_MAX:
       if (value < -1 || value > 0xffffffffLL) return LWE_EINVAL;
