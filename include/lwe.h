@@ -145,13 +145,14 @@ enum {
                                 limbs, Decaps' H(c)) runs on the caller's
                                 stream, so that per-kernel timings measure
                                 each kernel alone; 0 (default): overlapped   */
-  LWE_OPT_TREE_WARP_MAX = 7, /* tree hashes (H(pk), H(c)) of at most this
-                                many messages per launch run with one Keccak
-                                state per warp (the lanes of the state
-                                spread over the threads: lower latency),
-                                more with one state per thread (higher
-                                throughput).  -1 (default): the number of
-                                SMs; 0: always one state per thread         */
+  LWE_OPT_WARP_HASH_MAX = 7, /* hashing launches (tree hashes H(pk), H(c);
+                                KeyGen seeds; mu, K', seedSE'; the Decaps
+                                key) of at most this many items run with
+                                one Keccak state per warp (the lanes of
+                                the state spread over the threads: lower
+                                latency), larger ones with one state per
+                                thread (higher throughput).  -1 (default):
+                                the number of SMs; 0: always per thread   */
   LWE_OPT_PDL = 8            /* 1 (default): the kernels of Encaps / Decaps
                                 are launched with programmatic stream
                                 serialisation (each may start while the

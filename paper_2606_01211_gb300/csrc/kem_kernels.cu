@@ -35,8 +35,10 @@ __global__ void __launch_bounds__(512, 1) k_expand_A(const uint8_t *__restrict__
                                                   uint32_t logq, uint16_t *__restrict__ A,
                                                   uint64_t a_stride) {
   extern __shared__ uint32_t sT[];
+  pdl_trigger();
   aes_fill_smem(sT, g_aes_T0);
   __syncthreads();
+  pdl_wait();
   const AesTab tab = aes_tab(sT);
   const uint32_t e = blockIdx.y;
   uint32_t key[4], rk[44];
@@ -209,8 +211,10 @@ LWE_DEV void warp_allreduce8(int acc[8]) {
 // per 16-byte chunk = one AES block of A's counter layout).
 __global__ void __launch_bounds__(512, 1) k_mul_as_fused(MulAsArgs a) {
   extern __shared__ uint32_t sT[];
+  pdl_trigger();
   aes_fill_smem(sT, g_aes_T0);
   __syncthreads();
+  pdl_wait();
   const AesTab tab = aes_tab(sT);
   const uint32_t e = blockIdx.y;
   uint32_t key[4], rk[44];
@@ -279,6 +283,8 @@ LWE_DEV void dot8_rows(const uint4 *x, const int8_t *__restrict__ St, uint32_t n
 // Row groups (tasks) are dealt out task = CTA + grid * (warp + 8 k), so
 // that with a grid of two CTAs per SM every SM streams the same share of A.
 __global__ void __launch_bounds__(256) k_mul_as_rows(MulAsArgs a) {
+  pdl_trigger();
+  pdl_wait();
   const uint32_t e = blockIdx.y;
   const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t n = a.n, nch = n / 8;
@@ -466,6 +472,8 @@ LWE_DEV void sa_epilogue(const MulSaArgs &a, int *red, uint32_t cb, uint32_t rsp
 template <bool CMP>
 __global__ void __launch_bounds__(256) k_sa(MulSaArgs a) {
   extern __shared__ uint4 sm4[];
+  pdl_trigger();
+  pdl_wait();
   uint4 *sP = sm4;
   int *red = reinterpret_cast<int *>(sm4 + SA_PAIRS);
   const uint32_t cb = blockIdx.x, rsplit = blockIdx.y, R = gridDim.y, e = blockIdx.z;
@@ -555,10 +563,12 @@ __global__ void __launch_bounds__(512, 1) k_sa_fused(MulSaArgs a) {
   const uint32_t chunk = cb * 32 + half * 16 + (lane >> 1);  // 8-column chunk index
   const uint32_t j0 = 8 * chunk;
   const bool jv = j0 < n;
+  pdl_trigger();
   for (uint32_t i = tid; i < 2048; i += 512) red[i] = 0;
   uint32_t *sT = reinterpret_cast<uint32_t *>(base);
   aes_fill_smem(sT, g_aes_T0);
   __syncthreads();
+  pdl_wait();
   const AesTab tab = aes_tab(sT);
   uint32_t key[4], rk[44];
   aes_load_key(a.seed_ptrs ? a.seed_ptrs[e] + a.seed_off : a.seedA, key);
@@ -620,6 +630,8 @@ __global__ void __launch_bounds__(512, 1) k_sa_fused(MulSaArgs a) {
 // ---------------------------------------------------------------------------
 template <bool CMP>
 __global__ void __launch_bounds__(256) k_v_encode(VEncArgs a) {
+  pdl_trigger();
+  pdl_wait();
   const uint32_t e = blockIdx.x;
   const uint32_t k = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t n = a.n;
@@ -697,6 +709,8 @@ LWE_DEV void sha3_prefixed32(uint8_t prefix, const uint8_t *msg32, uint64_t s[25
 }
 
 __global__ void k_keygen_seeds(KeygenSeedArgs a) {
+  pdl_trigger();
+  pdl_wait();
   const uint32_t e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= a.count) return;
   const uint8_t *ms = a.ms + 32 * (size_t)e;
@@ -793,6 +807,150 @@ __global__ void __launch_bounds__(64) k_derive(DeriveArgs a) {
   for (int i = 0; i < 11; i++) dst[i] = make_uint4(rk[4 * i], rk[4 * i + 1], rk[4 * i + 2], rk[4 * i + 3]);
 }
 
+// ---------------------------------------------------------------------------
+// The same hashes with one Keccak state per warp (keccak_warp.cuh), for
+// launches of few items: one permutation then takes one warp ~1.5-2.7 us
+// instead of one thread ~5.6 us, and independent hashes of an item run in
+// different warps.  Thread t builds lane t of the padded single-block
+// message; lanes 0..3 of the result are the digest.
+// ---------------------------------------------------------------------------
+LWE_DEV uint64_t ld_le64(const uint8_t *p) {
+  if ((reinterpret_cast<uintptr_t>(p) & 7) == 0) return *reinterpret_cast<const uint64_t *>(p);
+  uint64_t v = 0;
+#pragma unroll
+  for (int b = 0; b < 8; b++) v |= (uint64_t)p[b] << (8 * b);
+  return v;
+}
+
+LWE_DEV void st_le64(uint8_t *p, uint64_t v) {
+#pragma unroll
+  for (int b = 0; b < 8; b++) p[b] = (uint8_t)(v >> (8 * b));
+}
+
+// lane t of prefix || 32 bytes, padded: the 32 bytes shifted up one byte,
+// the padding opening byte 1 of lane 4
+LWE_DEV uint64_t prefixed32_lane(uint8_t prefix, const uint8_t *msg32, uint32_t t) {
+  uint64_t v = 0;
+  if (t < 4) v = ld_le64(msg32 + 8 * t) << 8;
+  if (t >= 1 && t <= 4) v |= ld_le64(msg32 + 8 * (t - 1)) >> 56;
+  if (t == 0) v |= prefix;
+  if (t == 4) v |= 0x0600ull;
+  if (t == SHA3_RATE / 8 - 1) v ^= 0x8000000000000000ull;
+  return v;
+}
+
+// KeyGen seeds (Alg. 1): warp j of the item's CTA hashes prefix j || ms
+__global__ void __launch_bounds__(96) k_keygen_seeds_warp(KeygenSeedArgs a) {
+  __shared__ uint32_t sT0[256];
+  pdl_trigger();
+  for (uint32_t i = threadIdx.x; i < 256; i += blockDim.x) sT0[i] = g_aes_T0[i];
+  __syncthreads();
+  pdl_wait();
+  const uint32_t e = blockIdx.x, w = threadIdx.x >> 5, lane = threadIdx.x & 31, t = lane % 25;
+  const KeccakWarpMap km = keccak_warp_map(lane);
+  const uint8_t prefix = w == 0 ? 0x41 : (w == 1 ? 0x53 : 0x5A);
+  const uint64_t v = keccak_f1600_warp(km, prefixed32_lane(prefix, a.ms + 32 * (size_t)e, t));
+  uint8_t *pk = a.pk + (size_t)e * a.pk_bytes;
+  uint8_t *sk = a.sk + (size_t)e * a.sk_bytes;
+  uint8_t *ws = a.ws_seeds + 32 * (size_t)e;
+  if (w == 0) {  // seedA
+    if (lane < 2) {
+      st_le64(pk + 8 * lane, v);
+      st_le64(sk + a.sk_pk_off + 8 * lane, v);
+      st_le64(ws + 8 * lane, v);
+    }
+  } else if (w == 1) {  // seedSE and its key schedule
+    if (lane < 2) st_le64(ws + 16 + 8 * lane, v);
+    const uint64_t v1 = shfl64(v, 1);
+    if (lane == 0) {
+      const uint32_t key[4] = {(uint32_t)v, (uint32_t)(v >> 32), (uint32_t)v1, (uint32_t)(v1 >> 32)};
+      uint32_t rk[44];
+      aes_key_expand_global(sT0, key, rk);
+      uint4 *dst = reinterpret_cast<uint4 *>(a.ws_rk + 44 * (size_t)e);
+#pragma unroll
+      for (int i = 0; i < 11; i++)
+        dst[i] = make_uint4(rk[4 * i], rk[4 * i + 1], rk[4 * i + 2], rk[4 * i + 3]);
+    }
+  } else if (lane < 4) {  // z
+    st_le64(sk + a.sk_z_off + 8 * lane, v);
+  }
+}
+
+// Encaps / Decaps derivation (Alg. 4, 5): both warps of the item's CTA
+// hash mu (Encaps), then warp 0 K' = H(pkh || mu) and warp 1
+// seedSE' = H(0x01 || pkh || mu) with its key schedule
+__global__ void __launch_bounds__(64, 1) k_derive_warp(DeriveArgs a) {
+  __shared__ uint32_t sT0[256];
+  pdl_trigger();
+  for (uint32_t i = threadIdx.x; i < 256; i += blockDim.x) sT0[i] = g_aes_T0[i];
+  __syncthreads();
+  pdl_wait();
+  const uint32_t e = blockIdx.x, w = threadIdx.x >> 5, lane = threadIdx.x & 31, t = lane % 25;
+  const KeccakWarpMap km = keccak_warp_map(lane);
+  const uint32_t nb = a.mu_bytes / 8;  // lanes of mu, 1..4
+  uint64_t *mu64 = reinterpret_cast<uint64_t *>(a.mu + 32 * (size_t)e);
+  uint64_t mu_l = 0;  // lane t < 4: lane t of mu (zero beyond nb)
+  if (a.coins) {
+    const uint64_t v = keccak_f1600_warp(km, prefixed32_lane(0x4D, a.coins + 32 * (size_t)e, t));
+    mu_l = t < nb ? v : 0;
+    if (w == 0 && lane < 4) mu64[lane] = mu_l;
+  } else if (t < nb) {
+    mu_l = mu64[t];
+  }
+  // x = pkh (4 lanes) || mu (4 lanes) || zeros; thread t holds x[t]
+  const uint8_t *pkh = a.pkh_ptrs ? a.pkh_ptrs[e] + a.pkh_off : a.pkh + (size_t)e * a.pkh_stride;
+  const uint64_t mu_at = shfl64(mu_l, (lane - 4) & 31);
+  const uint64_t x = t < 4 ? ld_le64(pkh + 8 * t) : (t < 8 ? mu_at : 0);
+  if (w == 0) {
+    uint64_t m = x;
+    if (t == 4 + nb) m ^= 0x06ull;
+    if (t == SHA3_RATE / 8 - 1) m ^= 0x8000000000000000ull;
+    const uint64_t v = keccak_f1600_warp(km, m);
+    if (lane < 4) st_le64(a.kprime + 32 * (size_t)e + 8 * lane, v);
+    return;
+  }
+  const uint64_t xp = shfl64(x, (lane + 31) & 31);  // x[t - 1]
+  uint64_t m = t == 0 ? (0x01ull | (x << 8)) : ((xp >> 56) | (x << 8));
+  if (t == 4 + nb) m ^= 0x0600ull;
+  if (t == SHA3_RATE / 8 - 1) m ^= 0x8000000000000000ull;
+  const uint64_t v = keccak_f1600_warp(km, m);
+  if (lane < 2) st_le64(a.seeds + 32 * (size_t)e + 8 * lane, v);
+  const uint64_t v1 = shfl64(v, 1);
+  if (lane == 0) {
+    const uint32_t key[4] = {(uint32_t)v, (uint32_t)(v >> 32), (uint32_t)v1, (uint32_t)(v1 >> 32)};
+    uint32_t rk[44];
+    aes_key_expand_global(sT0, key, rk);
+    uint4 *dst = reinterpret_cast<uint4 *>(a.rk + 44 * (size_t)e);
+#pragma unroll
+    for (int i = 0; i < 11; i++)
+      dst[i] = make_uint4(rk[4 * i], rk[4 * i + 1], rk[4 * i + 2], rk[4 * i + 3]);
+  }
+}
+
+// Decaps key (Alg. 5): K = H(K' || H(c)) when the re-encryption matched,
+// else H(z || H(c)); one warp per item
+__global__ void __launch_bounds__(32) k_final_key_warp(FinalKeyArgs a) {
+  pdl_trigger();
+  pdl_wait();
+  const uint32_t e = blockIdx.x, lane = threadIdx.x, t = lane % 25;
+  const KeccakWarpMap km = keccak_warp_map(lane);
+  const uint32_t f = a.flags[e];
+  const uint64_t keep = (uint64_t)0 - (uint64_t)(((f | (0u - f)) >> 31) ^ 1u);
+  uint64_t m = 0;
+  if (t < 4) {
+    const uint64_t *kp = reinterpret_cast<const uint64_t *>(a.kprime + 32 * (size_t)e);
+    const uint64_t *z =
+        reinterpret_cast<const uint64_t *>(a.z_ptrs ? a.z_ptrs[e] + a.z_off : a.z);
+    m = (kp[t] & keep) | (z[t] & ~keep);
+  } else if (t < 8) {
+    m = reinterpret_cast<const uint64_t *>(a.hc + 32 * (size_t)e)[t - 4];
+  }
+  if (t == 8) m ^= 0x06ull;
+  if (t == SHA3_RATE / 8 - 1) m ^= 0x8000000000000000ull;
+  const uint64_t v = keccak_f1600_warp(km, m);
+  if (lane < 4) st_le64(a.K + 32 * (size_t)e + 8 * lane, v);
+}
+
 // Tree hash: tpi threads per message compute its 1024-byte-chunk digests
 // into shared memory; threads 0..ipc-1 (one per message, so the root phase
 // fills whole warps) then hash the digests -- the root -- and, for Encaps,
@@ -853,7 +1011,7 @@ LWE_DEV void st_cluster_u64(uint32_t addr, uint64_t v) {
   asm volatile("st.shared::cluster.u64 [%0], %1;" ::"r"(addr), "l"(v) : "memory");
 }
 
-__global__ void __launch_bounds__(TREE_WARP_MAX_THREADS) k_tree_warp(TreeArgs a) {
+__global__ void __launch_bounds__(TREE_WARP_MAX_THREADS, 1) k_tree_warp(TreeArgs a) {
   extern __shared__ uint64_t sdig[];  // [m][4], used in the cluster's first CTA
   pdl_trigger();
   pdl_wait();
@@ -993,6 +1151,8 @@ __global__ void __launch_bounds__(256) k_limbs(GemmLimbArgs a) {
 }
 
 __global__ void k_s_to_bf16(const int8_t *__restrict__ S, uint64_t count, uint16_t *out) {
+  pdl_trigger();
+  pdl_wait();
   for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
        i += (uint64_t)gridDim.x * blockDim.x) {
     __nv_bfloat16 b = __float2bfloat16_rn((float)S[i]);
@@ -1092,7 +1252,8 @@ void launch_expand_A(const uint8_t *seeds, uint32_t seed_stride, uint32_t count,
                      uint32_t logq, uint16_t *A, uint64_t a_stride, int num_sms, cudaStream_t st) {
   const uint64_t nblk = (uint64_t)n * n / 8;
   const int gx = grid_for(nblk, 512 * 4, num_sms);
-  k_expand_A<<<dim3(gx, count), 512, AES_SMEM_BYTES, st>>>(seeds, seed_stride, n, logq, A, a_stride);
+  launch_k(k_expand_A, dim3(gx, count), 512, AES_SMEM_BYTES, st, seeds, seed_stride, n, logq, A,
+           a_stride);
 }
 
 void launch_noise(const NoiseArgs &a, int num_sms, cudaStream_t st) {
@@ -1104,13 +1265,13 @@ void launch_mul_as(const MulAsArgs &a, uint32_t count, bool fused, int num_sms, 
   if (fused) {
     const uint32_t per_item = std::max<uint32_t>(1u, (uint32_t)std::max(num_sms, 1) / count);
     dim3 grid(std::min((a.n + 15) / 16, per_item), count);
-    k_mul_as_fused<<<grid, 512, AES_SMEM_BYTES, st>>>(a);
+    launch_k(k_mul_as_fused, grid, 512, AES_SMEM_BYTES, st, a);
   } else {
     // two CTAs per SM in all, spread over the items
     const uint32_t want = (a.n / AS_ROWS + 7) / 8;
     const uint32_t share = std::max<uint32_t>(1u, 2u * (uint32_t)std::max(num_sms, 1) / count);
     dim3 grid(std::min(want, share), count);
-    k_mul_as_rows<<<grid, 256, 0, st>>>(a);
+    launch_k(k_mul_as_rows, grid, 256, 0, st, a);
   }
 }
 
@@ -1131,13 +1292,15 @@ void launch_mul_sa(const MulSaArgs &a, uint32_t items, bool fused, bool cmp, int
   cfg.dynamicSmemBytes = (fused ? AES_SMEM_BYTES : 0) + SA_PAIRS * 16 + 2048 * 4;
   cfg.blockDim = dim3(fused ? 512 : 256, 1, 1);
   cfg.stream = st;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = 1;
-  attr[0].val.clusterDim.y = R;
-  attr[0].val.clusterDim.z = 1;
+  cudaLaunchAttribute attr[2];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = g_launch_pdl ? 1 : 0;
+  attr[1].id = cudaLaunchAttributeClusterDimension;
+  attr[1].val.clusterDim.x = 1;
+  attr[1].val.clusterDim.y = R;
+  attr[1].val.clusterDim.z = 1;
   cfg.attrs = attr;
-  cfg.numAttrs = R > 1 ? 1 : 0;
+  cfg.numAttrs = R > 1 ? 2 : 1;
   if (fused) {
     if (cmp)
       cudaLaunchKernelEx(&cfg, k_sa_fused<true>, a);
@@ -1153,16 +1316,24 @@ void launch_mul_sa(const MulSaArgs &a, uint32_t items, bool fused, bool cmp, int
 
 void launch_v_encode(const VEncArgs &a, uint32_t count, bool cmp, cudaStream_t st) {
   if (cmp)
-    k_v_encode<true><<<count, 256, 0, st>>>(a);
+    launch_k(k_v_encode<true>, count, 256, 0, st, a);
   else
-    k_v_encode<false><<<count, 256, 0, st>>>(a);
+    launch_k(k_v_encode<false>, count, 256, 0, st, a);
 }
 
-void launch_keygen_seeds(const KeygenSeedArgs &a, cudaStream_t st) {
-  k_keygen_seeds<<<(a.count + 63) / 64, 64, 0, st>>>(a);
+void launch_keygen_seeds(const KeygenSeedArgs &a, uint32_t warp_max, cudaStream_t st) {
+  if (a.count <= warp_max) {
+    launch_k(k_keygen_seeds_warp, a.count, 96, 0, st, a);
+    return;
+  }
+  launch_k(k_keygen_seeds, (a.count + 63) / 64, 64, 0, st, a);
 }
 
-void launch_derive(const DeriveArgs &a, cudaStream_t st) {
+void launch_derive(const DeriveArgs &a, uint32_t warp_max, cudaStream_t st) {
+  if (a.count <= warp_max) {
+    launch_k(k_derive_warp, a.count, 64, 0, st, a);
+    return;
+  }
   launch_k(k_derive, (a.count + 31) / 32, 64, 0, st, a);
 }
 
@@ -1193,7 +1364,11 @@ void launch_tree(TreeArgs &a, int num_sms, uint32_t warp_max, cudaStream_t st) {
   launch_k(k_tree, (a.count + a.ipc - 1) / a.ipc, threads, smem, st, a);
 }
 
-void launch_final_key(const FinalKeyArgs &a, cudaStream_t st) {
+void launch_final_key(const FinalKeyArgs &a, uint32_t warp_max, cudaStream_t st) {
+  if (a.count <= warp_max) {
+    launch_k(k_final_key_warp, a.count, 32, 0, st, a);
+    return;
+  }
   launch_k(k_final_key, (a.count + 127) / 128, 128, 0, st, a);
 }
 
@@ -1206,5 +1381,5 @@ void launch_gemm_limbs(const GemmLimbArgs &a, int num_sms, cudaStream_t st) {
 
 void launch_s_to_bf16(const int8_t *S, uint64_t count, uint16_t *out, int num_sms, cudaStream_t st) {
   const int g = grid_for(count, 256 * 8, num_sms * 8);
-  k_s_to_bf16<<<g, 256, 0, st>>>(S, count, out);
+  launch_k(k_s_to_bf16, g, 256, 0, st, S, count, out);
 }

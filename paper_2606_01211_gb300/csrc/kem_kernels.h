@@ -164,11 +164,11 @@ void launch_decrypt(const DecryptArgs &a, uint32_t count, cudaStream_t st);
 void launch_mul_sa(const MulSaArgs &a, uint32_t items, bool fused, bool cmp, int num_sms,
                    cudaStream_t st);
 void launch_v_encode(const VEncArgs &a, uint32_t count, bool cmp, cudaStream_t st);
-void launch_keygen_seeds(const KeygenSeedArgs &a, cudaStream_t st);
-void launch_derive(const DeriveArgs &a, cudaStream_t st);
-// launches of at most warp_max messages hash with one Keccak state per warp
+// launches of at most warp_max items hash with one Keccak state per warp
+void launch_keygen_seeds(const KeygenSeedArgs &a, uint32_t warp_max, cudaStream_t st);
+void launch_derive(const DeriveArgs &a, uint32_t warp_max, cudaStream_t st);
 void launch_tree(TreeArgs &a, int num_sms, uint32_t warp_max, cudaStream_t st);
 // measurement probes: kind 0 Keccak-f in registers (256-thread CTAs),
 // kind 1 AES counter blocks with the shared-memory tables (512 threads)
 int launch_probe(int kind, uint32_t ctas, uint32_t iters, uint32_t *sink, cudaStream_t st);
-void launch_final_key(const FinalKeyArgs &a, cudaStream_t st);
+void launch_final_key(const FinalKeyArgs &a, uint32_t warp_max, cudaStream_t st);

@@ -157,7 +157,7 @@ struct lwe_ctx {
   int gemm_pair = 1;
   bool serial = false;  // LWE_OPT_SERIAL: side-stream work on the caller's stream
   bool pdl = true;      // LWE_OPT_PDL
-  int64_t tree_warp_max = -1;  // LWE_OPT_TREE_WARP_MAX; -1: the number of SMs
+  int64_t tree_warp_max = -1;  // LWE_OPT_WARP_HASH_MAX; -1: the number of SMs
   bool timing = false;
   uint64_t launches = 0;
   std::vector<TimedLaunch> pending;
@@ -195,6 +195,11 @@ cudaEvent_t take_event(lwe_ctx *c) {
   cudaEvent_t e = nullptr;
   if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
   return e;
+}
+
+// hashing launches of at most this many items use one Keccak state per warp
+uint32_t warp_hash_max(const lwe_ctx *c) {
+  return c->tree_warp_max < 0 ? (uint32_t)c->num_sms : (uint32_t)c->tree_warp_max;
 }
 
 struct LaunchScope {
@@ -456,9 +461,7 @@ void tree_hash(lwe_ctx *c, const uint8_t *msgs, uint64_t stride, uint32_t len, u
   ta.out2 = out2;
   ta.out2_stride = out2_stride;
   ta.kprime = c->kp;
-  const uint32_t warp_max =
-      c->tree_warp_max < 0 ? (uint32_t)c->num_sms : (uint32_t)c->tree_warp_max;
-  LAUNCH(c, KID_TREE, st, launch_tree(ta, c->num_sms, warp_max, st));
+  LAUNCH(c, KID_TREE, st, launch_tree(ta, c->num_sms, warp_hash_max(c), st));
 }
 
 int hash_tree(lwe_ctx *c, const uint8_t *msgs, uint64_t stride, uint32_t len, uint32_t count,
@@ -481,7 +484,7 @@ void final_key(lwe_ctx *c, const uint8_t *z, const uint8_t *const *z_ptrs, uint6
   fa.flags = c->flags;
   fa.K = K;
   fa.count = count;
-  LAUNCH(c, KID_FINAL_KEY, st, launch_final_key(fa, st));
+  LAUNCH(c, KID_FINAL_KEY, st, launch_final_key(fa, warp_hash_max(c), st));
 }
 
 int set_device_of(lwe_ctx *c) {
@@ -695,7 +698,7 @@ int lwe_ctx_set_option(lwe_ctx *c, int option, int64_t value) {
       if (value != 0 && value != 1) return LWE_EINVAL;
       c->pdl = value != 0;
       return LWE_OK;
-    case LWE_OPT_TREE_WARP_MAX:
+    case LWE_OPT_WARP_HASH_MAX:
       if (value < -1 || value > 0xffffffffLL) return LWE_EINVAL;
       c->tree_warp_max = value;
       return LWE_OK;
@@ -729,7 +732,7 @@ int lwe_keygen(lwe_ctx *c, const uint8_t *seeds, uint32_t count, uint8_t *pk, ui
   const size_t pkb = pk_bytes(p), skb = sk_bytes(p);
 
   KeygenSeedArgs ka{seeds, pk, sk, c->seeds, c->rk, pkb, skb, 8ull * n, 8ull * n + 64, count, 0};
-  LAUNCH(c, KID_KEYGEN_SEEDS, st, launch_keygen_seeds(ka, st));
+  LAUNCH(c, KID_KEYGEN_SEEDS, st, launch_keygen_seeds(ka, warp_hash_max(c), st));
 
   NoiseArgs na = noise_args(c, count);
   na.nout = 2;
@@ -792,7 +795,7 @@ int lwe_encaps(lwe_ctx *c, const uint8_t *pk, const uint16_t *A, const uint8_t *
   rc = hash_tree(c, pk, pkb, (uint32_t)pkb, 1, TREE_DIGEST, c->pkh, 32, nullptr, 0, st);
   if (rc) return rc;
   DeriveArgs da = derive_args(c, coins, c->pkh, count);
-  LAUNCH(c, KID_DERIVE, st, launch_derive(da, st));
+  LAUNCH(c, KID_DERIVE, st, launch_derive(da, warp_hash_max(c), st));
   rc = run_encrypt(c, pk, A, count, ct, false, st, nullptr, side);
   if (rc) return rc;
   return hash_tree(c, ct, ctb, (uint32_t)ctb, count, TREE_ENC_KEY, K, 32, nullptr, 0, st);
@@ -833,7 +836,7 @@ int lwe_decaps(lwe_ctx *c, const uint8_t *sk, const uint16_t *A, const uint8_t *
   DecryptArgs dca = decrypt_args(c, ct, reinterpret_cast<const int8_t *>(sk), nullptr);
   LAUNCH(c, KID_DECRYPT, st, launch_decrypt(dca, count, st));
   DeriveArgs da = derive_args(c, nullptr, pkh, count);
-  LAUNCH(c, KID_DERIVE, st, launch_derive(da, st));
+  LAUNCH(c, KID_DERIVE, st, launch_derive(da, warp_hash_max(c), st));
   rc = run_encrypt(c, pk, A, count, const_cast<uint8_t *>(ct), true, st, nullptr, side);
   if (rc) return rc;
   CUDA_TRY(cudaStreamWaitEvent(st, c->ev_join, 0));
@@ -865,7 +868,7 @@ int lwe_encaps_multi(lwe_ctx *c, const uint8_t *const *pk_ptrs, const uint8_t *c
     da.pkh = c->pkhs;
     da.pkh_stride = 32;
   }
-  LAUNCH(c, KID_DERIVE, st, launch_derive(da, st));
+  LAUNCH(c, KID_DERIVE, st, launch_derive(da, warp_hash_max(c), st));
   ItemKeys ik;
   ik.ptrs = pk_ptrs;
   ik.pk_off = 0;
@@ -900,7 +903,7 @@ int lwe_decaps_multi(lwe_ctx *c, const uint8_t *const *sk_ptrs, const uint16_t *
   DeriveArgs da = derive_args(c, nullptr, nullptr, count);
   da.pkh_ptrs = sk_ptrs;  // H(pk) is stored inside sk
   da.pkh_off = 8ull * n + 32;
-  LAUNCH(c, KID_DERIVE, st, launch_derive(da, st));
+  LAUNCH(c, KID_DERIVE, st, launch_derive(da, warp_hash_max(c), st));
   ItemKeys ik;
   ik.ptrs = sk_ptrs;
   ik.pk_off = 8ull * n + 64;  // pk is stored inside sk
@@ -1058,7 +1061,7 @@ int lwe_encaps_noalloc(const lwe_params *p, const uint8_t *pk, const uint16_t *A
   rc = hash_tree(&c, pk, pkb, (uint32_t)pkb, 1, TREE_DIGEST, c.pkh, 32, nullptr, 0, st);
   if (rc) return rc;
   DeriveArgs da = derive_args(&c, coins, c.pkh, count);
-  LAUNCH(&c, KID_DERIVE, st, launch_derive(da, st));
+  LAUNCH(&c, KID_DERIVE, st, launch_derive(da, warp_hash_max(&c), st));
   rc = run_encrypt(&c, pk, A, count, ct, false, st);
   if (rc) return rc;
   return hash_tree(&c, ct, ctb, (uint32_t)ctb, count, TREE_ENC_KEY, K, 32, nullptr, 0, st);

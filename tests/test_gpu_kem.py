@@ -58,12 +58,17 @@ def test_expand_A_large_sampled_rows():
 
 @pytest.mark.parametrize("name", list(SMALL))
 @pytest.mark.parametrize("stored", [True, False])
-def test_keygen_matches_oracle(name, stored):
+@pytest.mark.parametrize("warp_max", [0, None])
+def test_keygen_matches_oracle(name, stored, warp_max):
+    """warp_max 0: the seeds hashed with one Keccak state per thread;
+    default: one state per warp (a launch of 3 items)."""
     cfg = SMALL[name]
     p, po = params(**cfg)
     count = 3
     ms = master_seeds(count, seed=11)
     ctx = lwe.Ctx(p, max_batch=count)
+    if warp_max is not None:
+        ctx.set_option(lwe.OPT_WARP_HASH_MAX, warp_max)
     pk, sk = ctx.empty_pk(count), ctx.empty_sk(count)
     A = torch.empty((count, p.n, p.n), dtype=torch.int16, device="cuda") if stored else None
     ctx.keygen(dev(ms), pk, sk, A_out=A)
@@ -123,7 +128,7 @@ def test_tree_hash_forms_match_oracle(name, warp_max):
     count = 37
     ctx, p, po, pk_o, sk_o, A_o, cs, ct, K, K2, *_ = _kem_case(
         name, count, lwe.PATH_SKINNY, True, seed=23,
-        options=((lwe.OPT_TREE_WARP_MAX, warp_max),))
+        options=((lwe.OPT_WARP_HASH_MAX, warp_max),))
     ct_h, K_h, K2_h = host(ct), host(K), host(K2)
     for i in (0, 1, 17, count - 1):
         ct_o, K_o = O.encaps(po, pk_o, bytes(cs[i]), A=A_o)
