@@ -128,20 +128,13 @@ LWE_DEV void noise_store(const char *smem, const NoiseOut &o, uint8_t *base, uin
   }
 }
 
-__global__ void __launch_bounds__(512, 1) k_noise(NoiseArgs a) {
-  extern __shared__ uint32_t sT[];
-  pdl_trigger();
-  aes_fill_smem(sT, g_aes_T0);
-  noise_fill_table(sT + NOISE_TAB_OFF / 4, a);
-  __syncthreads();
-  pdl_wait();
-  const AesTab tab = aes_tab(sT);
-  const char *smem = reinterpret_cast<const char *>(sT);
+// The runs of one warp: warp `gwarp` of `nwarps` takes runs gwarp,
+// gwarp + nwarps, ...
+LWE_DEV void noise_runs(const NoiseArgs &a, const AesTab &tab, const char *smem, uint64_t gwarp,
+                        uint64_t nwarps) {
   const uint32_t lane = threadIdx.x & 31;
   const uint64_t nruns = (uint64_t)a.count * a.runs_per_item;
-  const uint64_t nwarps = (uint64_t)gridDim.x * (blockDim.x >> 5);
-  for (uint64_t run = (uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); run < nruns;
-       run += nwarps) {
+  for (uint64_t run = gwarp; run < nruns; run += nwarps) {
     const uint32_t e = (uint32_t)(run / a.runs_per_item);
     uint32_t r = (uint32_t)(run % a.runs_per_item);
     uint32_t s = 0;
@@ -178,6 +171,19 @@ __global__ void __launch_bounds__(512, 1) k_noise(NoiseArgs a) {
       for (uint32_t b = b0; b < nblk; b += 32) noise_store(smem, o, base, b, aes_ctr_block(tab, rk, o.domain, b));
     }
   }
+}
+
+__global__ void __launch_bounds__(512, 1) k_noise(NoiseArgs a) {
+  extern __shared__ uint32_t sT[];
+  pdl_trigger();
+  aes_fill_smem(sT, g_aes_T0);
+  noise_fill_table(sT + NOISE_TAB_OFF / 4, a);
+  __syncthreads();
+  pdl_wait();
+  const AesTab tab = aes_tab(sT);
+  noise_runs(a, tab, reinterpret_cast<const char *>(sT),
+             (uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5),
+             (uint64_t)gridDim.x * (blockDim.x >> 5));
 }
 
 // ---------------------------------------------------------------------------
@@ -1234,6 +1240,7 @@ cudaError_t lwe_kernel_smem_setup() {
   e = cudaFuncSetAttribute(k_expand_A, cudaFuncAttributeMaxDynamicSharedMemorySize, AES_SMEM_BYTES);
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_noise, cudaFuncAttributeMaxDynamicSharedMemorySize, NOISE_SMEM_BYTES);
+
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_mul_as_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, AES_SMEM_BYTES);
   if (e != cudaSuccess) return e;
