@@ -341,6 +341,66 @@ __global__ void __launch_bounds__(256) k_mul_as_rows(MulAsArgs a) {
   }
 }
 
+// The same for calls with few rows in all (one item, n up to a few
+// thousand): the kernel above then has less than one row group per warp and
+// each warp's chain of dependent loads sets the time.  Here a CTA takes one
+// row group and its 8 warps split the columns, so 8 times as many warps keep
+// loads in flight; their partial sums meet in shared memory.
+__global__ void __launch_bounds__(256) k_mul_as_split(MulAsArgs a) {
+  __shared__ int red[8][32];
+  pdl_trigger();
+  pdl_wait();
+  const uint32_t e = blockIdx.y, i0 = blockIdx.x * AS_ROWS;
+  const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t n = a.n, nch = n / 8;
+  const uint32_t c0 = warp * nch / 8, c1 = (warp + 1) * nch / 8;
+  const int8_t *St = a.St + (size_t)e * a.st_stride;
+  const uint16_t *A0 = a.A + (size_t)e * a.a_stride + (size_t)i0 * n;
+  int acc[AS_ROWS][8];
+#pragma unroll
+  for (int r = 0; r < AS_ROWS; r++)
+#pragma unroll
+    for (int l = 0; l < 8; l++) acc[r][l] = 0;
+  for (uint32_t jc = c0 + lane; jc < c1; jc += 64) {
+    const bool two = jc + 32 < c1;
+    uint4 x0[AS_ROWS], x1[AS_ROWS];
+#pragma unroll
+    for (int r = 0; r < AS_ROWS; r++) x0[r] = ld_stream_u4(A0 + (size_t)r * n + 8 * (size_t)jc);
+#pragma unroll
+    for (int r = 0; r < AS_ROWS; r++)
+      x1[r] = two ? ld_stream_u4(A0 + (size_t)r * n + 8 * (size_t)(jc + 32)) : make_uint4(0, 0, 0, 0);
+    dot8_rows(x0, St, n, 8 * jc, acc);
+    if (two) dot8_rows(x1, St, n, 8 * (jc + 32), acc);
+  }
+  int v[32];
+#pragma unroll
+  for (int r = 0; r < AS_ROWS; r++)
+#pragma unroll
+    for (int l = 0; l < 8; l++) v[8 * r + l] = acc[r][l];
+#pragma unroll
+  for (int o = 16; o >= 1; o >>= 1) {
+    const bool up = (lane & o) != 0;
+#pragma unroll
+    for (int j = 0; j < o; j++) {
+      const int send = up ? v[j] : v[j + o];
+      const int keep = up ? v[j + o] : v[j];
+      v[j] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+    }
+  }
+  red[warp][lane] = v[0];
+  __syncthreads();
+  if (warp != 0) return;
+  int sum = 0;
+#pragma unroll
+  for (int w = 0; w < 8; w++) sum += red[w][lane];
+  const uint32_t r = lane >> 3, l = lane & 7, i = i0 + r;
+  const uint32_t m = (1u << a.logq) - 1u;
+  const int ev = a.E ? (int)a.E[(size_t)e * a.e_stride + (size_t)i * 8 + l] : 0;
+  const uint16_t val = (uint16_t)((uint32_t)(sum + ev) & m);
+  reinterpret_cast<uint16_t *>(a.out + (size_t)e * a.out_stride + 16 * (size_t)i)[l] = val;
+  if (a.out2) reinterpret_cast<uint16_t *>(a.out2 + (size_t)e * a.out2_stride + 16 * (size_t)i)[l] = val;
+}
+
 // Decrypt (Alg. 3): warp r of CTA e computes row r of M = C - B' S and the
 // B message bits of its eight coefficients.
 __global__ void __launch_bounds__(256) k_decrypt(DecryptArgs a) {
@@ -1273,6 +1333,9 @@ void launch_mul_as(const MulAsArgs &a, uint32_t count, bool fused, int num_sms, 
     const uint32_t per_item = std::max<uint32_t>(1u, (uint32_t)std::max(num_sms, 1) / count);
     dim3 grid(std::min((a.n + 15) / 16, per_item), count);
     launch_k(k_mul_as_fused, grid, 512, AES_SMEM_BYTES, st, a);
+  } else if ((uint64_t)count * (a.n / AS_ROWS) < 4ull * 16 * (uint64_t)std::max(num_sms, 1)) {
+    // fewer than ~4 row groups per warp of the grid below: split columns
+    launch_k(k_mul_as_split, dim3(a.n / AS_ROWS, count), 256, 0, st, a);
   } else {
     // two CTAs per SM in all, spread over the items
     const uint32_t want = (a.n / AS_ROWS + 7) / 8;

@@ -62,9 +62,18 @@ def test_expand_A_large_sampled_rows():
 def test_keygen_matches_oracle(name, stored, warp_max):
     """warp_max 0: the seeds hashed with one Keccak state per thread;
     default: one state per warp (a launch of 3 items)."""
+    _keygen_case(name, stored, warp_max, 3)
+
+
+def test_keygen_batch_matches_oracle():
+    """70 P640 key pairs in one call: enough rows that A S runs as one warp
+    per row group (k_mul_as_rows) instead of splitting columns."""
+    _keygen_case("P640", True, None, 70)
+
+
+def _keygen_case(name, stored, warp_max, count):
     cfg = SMALL[name]
     p, po = params(**cfg)
-    count = 3
     ms = master_seeds(count, seed=11)
     ctx = lwe.Ctx(p, max_batch=count)
     if warp_max is not None:
