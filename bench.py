@@ -194,11 +194,12 @@ def algorithmic_bytes(p, count):
     """Bytes each kernel must move through HBM in one step (summed over its
     launches), to set against the measured DRAM traffic."""
     n = p.n
-    ct_bytes, pk_bytes = 16 * n + 128, 16 + 16 * n
+    ct_bytes = 16 * n + 128
     rows = 8 * count
     return {
-        # H(pk) once, H(c) read in Encaps and in Decaps
-        "k_tree": float(pk_bytes + 2 * count * ct_bytes),
+        # the batched launches: H(c) read in Encaps and in Decaps (H(pk), one
+        # message, runs as k_tree_warp)
+        "k_tree": float(2 * count * ct_bytes),
         # per launch: S' (bf16) + limbs + E' read; ct written (Encaps) or read (Decaps)
         "k_gemm_tc": 2.0 * (2 * rows * n + 2 * 2 * (n + 8) * n + rows * n + count * ct_bytes),
         # per launch: S' (bf16), E' (int8), E'' written
@@ -210,17 +211,16 @@ def algorithmic(p, count):
     """Algorithmic work of the kernels in one step (summed over launches)."""
     n = p.n
     rows, ncols = 8 * count, n + 8
-    ct_bytes, pk_bytes = 16 * n + 128, 16 + 16 * n
+    ct_bytes = 16 * n + 128
     return {
         # two limbs, 2 flops per multiply-add, Encaps + Decaps
         "k_gemm_tc": ("tensor", 2 * (2.0 * 2 * rows * ncols * n), "TFLOP/s", 1e12),
         # AES keystream bytes: S', E' (8n samples each) and E'' (64) per item,
         # 2 bytes per sample, Encaps + Decaps
         "k_noise": ("alu", 2 * (2.0 * (16 * n + 64) * count), "GB/s of AES keystream", 1e9),
-        # Keccak-f calls: H(pk) once, H(c) in Encaps and in Decaps, and
-        # Encaps' K = H(K' || H(c))
-        "k_tree": ("alu", float(keccak_perms(pk_bytes) + 2 * count * keccak_perms(ct_bytes) + count),
-                   "G Keccak-f/s", 1e9),
+        # Keccak-f calls of the batched launches: H(c) in Encaps and in
+        # Decaps, and Encaps' K = H(K' || H(c))
+        "k_tree": ("alu", float(2 * count * keccak_perms(ct_bytes) + count), "G Keccak-f/s", 1e9),
     }
 
 
@@ -232,16 +232,17 @@ def algorithmic(p, count):
 CSRC = os.path.join(ROOT, "paper_2606_01211_gb300", "csrc")
 TRAFFIC = {
     # kernel: (bytes per step, launches per step, [(file, function or None)], fingerprint, profile)
-    "k_tree": (129.588480e6, 3,
+    "k_tree": (129.488640e6, 2,
                [("kem_kernels.cu", "k_tree"), ("kem_kernels.cu", "launch_tree"), ("keccak.cuh", None)],
-               "4f1363b566d02733", "profiles/k_tree_p976.md"),
-    "k_gemm_tc": (302.765056e6, 2, [("gemm_tc.cu", None)], "a0989a5c202077cc",
+               "67134a7a529e4ea2", "profiles/k_tree_p976.md"),
+    "k_gemm_tc": (302.521088e6, 2, [("gemm_tc.cu", None)], "397015ef0b62cd77",
                   "profiles/k_gemm_sa2_p976.md"),
     "k_noise": (70.732800e6, 2,
-                [("kem_kernels.cu", "k_noise"), ("kem_kernels.cu", "noise_store"),
+                [("kem_kernels.cu", "k_noise"), ("kem_kernels.cu", "noise_runs"),
+                 ("kem_kernels.cu", "noise_store"),
                  ("kem_kernels.cu", "noise_fill_table"), ("kem_kernels.cu", "launch_noise"),
                  ("aes.cuh", None)],
-                "43372c8896e2089c", "profiles/k_noise_p976.md"),
+                "853efc1fa5cba1e4", "profiles/k_noise_p976.md"),
 }
 
 

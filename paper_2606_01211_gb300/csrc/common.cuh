@@ -22,6 +22,7 @@ enum LweKernel {
   KID_DERIVE,
   KID_LIMBS,
   KID_GEMM,
+  KID_TREE_WARP,
   KID_COUNT
 };
 

@@ -133,7 +133,7 @@ uint32_t mu_bytes(const lwe_params &p) { return 8 * p.B; }
 const char *kKernelNames[KID_COUNT] = {
     "k_expand_A", "k_noise",    "k_keygen_seeds", "k_mul_as", "k_decrypt",
     "k_sa",       "k_sa_fused", "k_v_encode",     "k_tree",   "k_final_key",
-    "k_derive",   "k_limbs",    "k_gemm_tc"};
+    "k_derive",   "k_limbs",    "k_gemm_tc",      "k_tree_warp"};
 
 }  // namespace
 
@@ -461,7 +461,9 @@ void tree_hash(lwe_ctx *c, const uint8_t *msgs, uint64_t stride, uint32_t len, u
   ta.out2 = out2;
   ta.out2_stride = out2_stride;
   ta.kprime = c->kp;
-  LAUNCH(c, KID_TREE, st, launch_tree(ta, c->num_sms, warp_hash_max(c), st));
+  const uint32_t warp_max = warp_hash_max(c);
+  LAUNCH(c, count <= warp_max ? KID_TREE_WARP : KID_TREE, st,
+         launch_tree(ta, c->num_sms, warp_max, st));
 }
 
 int hash_tree(lwe_ctx *c, const uint8_t *msgs, uint64_t stride, uint32_t len, uint32_t count,
