@@ -138,6 +138,15 @@ void orc_ctr_block(const uint8_t rk[176], uint64_t domain, uint64_t index,
   orc_aes128_encrypt(rk, in, out);
 }
 
+/* `count` consecutive keystream blocks (domain, first .. first + count - 1)
+ * under one key, for the paper-profile oracle's long streams. */
+void orc_ctr_stream(const uint8_t key[16], uint64_t domain, uint64_t first, size_t count,
+                    uint8_t *out) {
+  uint8_t rk[176];
+  orc_aes128_key_expand(key, rk);
+  for (size_t b = 0; b < count; b++) orc_ctr_block(rk, domain, first + b, out + 16 * b);
+}
+
 /* ======================================================================== */
 /* Keccak-f[1600] and SHA3-256, FIPS 202                                     */
 /* ======================================================================== */

@@ -64,6 +64,9 @@ void orc_aes128_encrypt(const uint8_t rk[176], const uint8_t in[16],
 /* keystream block for (domain, index): AES_key(BE64(domain) || BE64(index)) */
 void orc_ctr_block(const uint8_t rk[176], uint64_t domain, uint64_t index,
                    uint8_t out[16]);
+/* Blocks first .. first + count - 1 of the stream (key, domain). */
+void orc_ctr_stream(const uint8_t key[16], uint64_t domain, uint64_t first, size_t count,
+                    uint8_t *out);
 void orc_sha3_256(const uint8_t *msg, size_t len, uint8_t out[32]);
 /* two-level tree: SHA3-256( SHA3-256(chunk_0) || ... || SHA3-256(chunk_m-1) ),
  * chunks of ORC_TREE_CHUNK bytes, the last one possibly shorter */

@@ -75,6 +75,7 @@ def _declare(L):
     L.orc_aes128_key_expand.argtypes = [_vp, _vp]
     L.orc_aes128_encrypt.argtypes = [_vp, _vp, _vp]
     L.orc_ctr_block.argtypes = [_vp, C.c_uint64, C.c_uint64, _vp]
+    L.orc_ctr_stream.argtypes = [_vp, C.c_uint64, C.c_uint64, _sz, _vp]
     L.orc_sha3_256.argtypes = [_vp, _sz, _vp]
     L.orc_htree.argtypes = [_vp, _sz, _vp]
     L.orc_cdf_table.argtypes = [C.c_double, _u32, _vp]
@@ -142,6 +143,14 @@ def ctr_blocks(key: bytes, domain: int, first: int, count: int) -> bytes:
         lib().orc_ctr_block(_ptr(rk), domain, b, _ptr(out))
         res += out.tobytes()
     return bytes(res)
+
+
+def ctr_stream(key: bytes, domain: int, first: int, count: int) -> np.ndarray:
+    """`count` keystream blocks as one uint8 array (16 count bytes)."""
+    out = np.zeros(16 * max(count, 1), np.uint8)
+    if count:
+        lib().orc_ctr_stream(_ptr(_u8(key)), domain, first, count, _ptr(out))
+    return out[:16 * count]
 
 
 def sha3_256(msg: bytes) -> bytes:
