@@ -35,7 +35,9 @@ Readings, where the paper is silent or at odds with itself:
   or mu_k >= 3q/4.
 * Layouts: pk = seedA || t (n uint32 LE); sk = s (n int8) || z || pkh ||
   pk; ct = U^T (256 x n uint32 LE, row k = u_k) || v (256 uint32 LE).  H is
-  SHA3-256; H(c) and H(pk) are the tree hash of the matrix form.
+  SHA3-256; H(pk) is the tree hash of the matrix form (``oracle.htree``),
+  and H(c) = htree(htree(u_0) || ... || htree(u_255) || htree(v)), so that
+  the multi-megabyte ciphertext needs no long sequential root.
 """
 from __future__ import annotations
 
@@ -240,6 +242,14 @@ def decrypt(p: PParams, s: np.ndarray, ct: bytes) -> bytes:
     return bytes(out)
 
 
+def hash_ct(p: PParams, ct: bytes) -> bytes:
+    """H(c): the tree hash of the rows' and v's tree hashes."""
+    row = 4 * p.n
+    parts = [O.htree(ct[k * row:(k + 1) * row]) for k in range(MBITS)]
+    parts.append(O.htree(ct[MBITS * row:]))
+    return O.htree(b"".join(parts))
+
+
 def _derive(pkh: bytes, m: bytes):
     return _h(pkh + m), _h(b"\x01" + pkh + m)[:16]
 
@@ -251,7 +261,7 @@ def encaps(p: PParams, pk: bytes, coins: bytes, A: np.ndarray | None = None):
     kp, seed = _derive(pkh, m)
     Ut, v = encrypt(p, pk, m, seed, A)
     ct = ct_bytes_of(Ut, v)
-    return ct, _h(kp + O.htree(ct))
+    return ct, _h(kp + hash_ct(p, ct))
 
 
 def decaps(p: PParams, sk: bytes, ct: bytes, A: np.ndarray | None = None) -> bytes:
@@ -263,5 +273,5 @@ def decaps(p: PParams, sk: bytes, ct: bytes, A: np.ndarray | None = None) -> byt
     m = decrypt(p, s, ct)
     kp, seed = _derive(pkh, m)
     Ut, v = encrypt(p, pk, m, seed, A)
-    hc = O.htree(ct)
+    hc = hash_ct(p, ct)
     return _h((kp if ct_bytes_of(Ut, v) == ct else z) + hc)

@@ -22,6 +22,7 @@
 #include "common.cuh"
 #include "gemm_tc.h"
 #include "kem_kernels.h"
+#include "pp_types.h"
 #include "keccak_warp.cuh"
 
 // The round table T0 (see aes.cuh); written by lwe_upload_aes_table.
@@ -1226,6 +1227,8 @@ __global__ void k_s_to_bf16(const int8_t *__restrict__ S, uint64_t count, uint16
   }
 }
 
+#include "pp_kernels.cuh"
+
 // ---------------------------------------------------------------------------
 // Host-side launch wrappers (called from lwe_api.cu)
 // ---------------------------------------------------------------------------
@@ -1310,6 +1313,10 @@ cudaError_t lwe_kernel_smem_setup() {
   e = cudaFuncSetAttribute(k_sa_fused<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, fused_smem);
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_probe_aes, cudaFuncAttributeMaxDynamicSharedMemorySize, AES_SMEM_BYTES);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_pp_expand_A, cudaFuncAttributeMaxDynamicSharedMemorySize, AES_SMEM_BYTES);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_pp_noise, cudaFuncAttributeMaxDynamicSharedMemorySize, AES_SMEM_BYTES);
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_limbs, cudaFuncAttributeMaxDynamicSharedMemorySize, AES_SMEM_BYTES);
   return e;
@@ -1452,4 +1459,41 @@ void launch_gemm_limbs(const GemmLimbArgs &a, int num_sms, cudaStream_t st) {
 void launch_s_to_bf16(const int8_t *S, uint64_t count, uint16_t *out, int num_sms, cudaStream_t st) {
   const int g = grid_for(count, 256 * 8, num_sms * 8);
   launch_k(k_s_to_bf16, g, 256, 0, st, S, count, out);
+}
+
+// ---- the paper's own parameter profile ------------------------------------
+void launch_pp_expand_A(const uint8_t *seedA, uint32_t n, ModQ M, uint32_t *A, int num_sms,
+                        cudaStream_t st) {
+  const int g = grid_for((uint64_t)n * n / 4, 512 * 4, num_sms);
+  launch_k(k_pp_expand_A, g, 512, AES_SMEM_BYTES, st, seedA, n, M, A);
+}
+
+void launch_pp_noise(const PpNoiseArgs &a, int num_sms, cudaStream_t st) {
+  uint64_t blocks = 0;
+  for (uint32_t s = 0; s < a.nout; s++)
+    blocks += a.o[s].kind == PP_BINOMIAL ? (a.o[s].count + 15) / 16 : (a.o[s].count + 7) / 8;
+  launch_k(k_pp_noise, grid_for(blocks, 512 * 4, num_sms), 512, AES_SMEM_BYTES, st, a);
+}
+
+void launch_pp_as(const PpAsArgs &a, cudaStream_t st) {
+  launch_k(k_pp_as, (a.n + 7) / 8, 256, 0, st, a);
+}
+
+void launch_pp_encrypt(const PpEncArgs &a, bool cmp, cudaStream_t st) {
+  const dim3 grid(a.n / PPE_BN, PP_MBITS / PPE_BM);
+  if (cmp)
+    launch_k(k_pp_encrypt<true>, grid, 256, 0, st, a);
+  else
+    launch_k(k_pp_encrypt<false>, grid, 256, 0, st, a);
+}
+
+void launch_pp_v(const PpVArgs &a, bool cmp, cudaStream_t st) {
+  if (cmp)
+    launch_k(k_pp_v<true>, PP_MBITS / 8, 256, 0, st, a);
+  else
+    launch_k(k_pp_v<false>, PP_MBITS / 8, 256, 0, st, a);
+}
+
+void launch_pp_decrypt(const PpDecArgs &a, cudaStream_t st) {
+  launch_k(k_pp_decrypt, PP_MBITS / 8, 256, 0, st, a);
 }

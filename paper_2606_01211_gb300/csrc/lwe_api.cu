@@ -16,6 +16,8 @@
 #include "common.cuh"
 #include "gemm_tc.h"
 #include "kem_kernels.h"
+#include "pp_types.h"
+#include "../../include/lwe_pp.h"
 
 namespace {
 
@@ -1165,5 +1167,318 @@ const char *lwe_kernel_name(int kid) {
 }
 
 int lwe_num_kernels(void) { return KID_COUNT; }
+
+}  // extern "C"
+
+// ===========================================================================
+// The paper's own parameter profile (lwe_pp.h; Tab. 1, Alg. 1-5 with odd q
+// and a 256-bit message encrypted bit by bit)
+// ===========================================================================
+namespace {
+
+// Tab. 1: n, q, sigma, k; the clip is the largest (<= 15) whose CDF table is
+// valid for that sigma
+const struct {
+  uint32_t n, q;
+  double sigma;
+  uint32_t k;
+} kPpPresets[] = {{512, 3329, 2.3, 3},   {1024, 12289, 2.3, 3}, {2048, 12289, 2.3, 3},
+                  {4096, 12289, 1.7, 3}, {8192, 65537, 1.2, 2}, {16384, 65537, 1.2, 2},
+                  {32768, 65537, 1.0, 2}};
+
+ModQ modq(uint32_t q) { return ModQ{q, (uint32_t)(0x100000000ull / q)}; }
+
+size_t pp_pk_bytes(const lwe_pp_params &p) { return 16 + 4 * (size_t)p.n; }
+size_t pp_sk_bytes(const lwe_pp_params &p) { return p.n + 64 + pp_pk_bytes(p); }
+size_t pp_ct_bytes(const lwe_pp_params &p) { return 4 * (size_t)PP_MBITS * p.n + 4 * PP_MBITS; }
+
+}  // namespace
+
+struct lwe_pp_ctx {
+  lwe_pp_params p;
+  uint16_t T[16];
+  int device = 0, num_sms = 0;
+  uint8_t *ws = nullptr;
+  uint8_t *seeds = nullptr, *mu = nullptr, *kp = nullptr, *pkh = nullptr, *hc = nullptr;
+  uint8_t *digests = nullptr;  // 257 x 32: the rows' and v's tree hashes
+  uint32_t *rk = nullptr, *flags = nullptr;
+  int8_t *e = nullptr, *Rt = nullptr, *E1t = nullptr;
+  int32_t *e2 = nullptr;
+};
+
+namespace {
+
+void pp_tree(lwe_pp_ctx *c, const uint8_t *msgs, uint64_t stride, uint32_t len, uint32_t count,
+             int mode, uint8_t *out, uint64_t out_stride, cudaStream_t st) {
+  TreeArgs ta;
+  memset(&ta, 0, sizeof ta);
+  ta.msgs = msgs;
+  ta.stride = stride;
+  ta.len = len;
+  ta.count = count;
+  ta.mode = mode;
+  ta.out = out;
+  ta.out_stride = out_stride;
+  ta.kprime = c->kp;
+  launch_tree(ta, c->num_sms, (uint32_t)c->num_sms, st);
+}
+
+// H(c) = Htree(Htree(u_0) || ... || Htree(u_255) || Htree(v)); with
+// TREE_ENC_KEY the last launch returns K = H(K' || H(c)) instead
+void pp_hash_ct(lwe_pp_ctx *c, const uint8_t *ct, int mode, uint8_t *out, cudaStream_t st) {
+  const uint32_t row = 4 * c->p.n;
+  pp_tree(c, ct, row, row, PP_MBITS, TREE_DIGEST, c->digests, 32, st);
+  pp_tree(c, ct + (size_t)PP_MBITS * row, 4 * PP_MBITS, 4 * PP_MBITS, 1, TREE_DIGEST,
+          c->digests + 32 * PP_MBITS, 32, st);
+  pp_tree(c, c->digests, 32 * (PP_MBITS + 1), 32 * (PP_MBITS + 1), 1, mode, out, 32, st);
+}
+
+// Encrypt's noise from the round keys in c->rk: r, e1 (Gaussian, 256 x n)
+// and e2 (centred uniform, 256)
+void pp_encrypt_noise(lwe_pp_ctx *c, cudaStream_t st) {
+  PpNoiseArgs na;
+  memset(&na, 0, sizeof na);
+  na.rk = c->rk;
+  const uint32_t n = c->p.n;
+  na.o[0] = PpNoiseOut{c->Rt, PP_MBITS * n, PP_GAUSS, 3, 0};
+  na.o[1] = PpNoiseOut{c->E1t, PP_MBITS * n, PP_GAUSS, 4, 0};
+  na.o[2] = PpNoiseOut{c->e2, PP_MBITS, PP_UNIFORM, 5, 0};
+  na.nout = 3;
+  na.clip = c->p.clip;
+  na.kunif = c->p.k;
+  for (int i = 0; i < 16; i++) na.T[i] = c->T[i];
+  launch_pp_noise(na, c->num_sms, st);
+}
+
+// U^T and v of Encrypt from c's noise and message c->mu; cmp compares them
+// with ct (Decaps) instead of writing
+void pp_encrypt(lwe_pp_ctx *c, const uint32_t *t, const uint32_t *A, uint8_t *ct, bool cmp,
+                cudaStream_t st) {
+  const uint32_t n = c->p.n;
+  const ModQ M = modq(c->p.q);
+  PpEncArgs ea{A, c->Rt, c->E1t, reinterpret_cast<uint32_t *>(ct), c->flags, n, M};
+  launch_pp_encrypt(ea, cmp, st);
+  PpVArgs va{t, c->Rt, c->e2, c->mu, reinterpret_cast<uint32_t *>(ct) + (size_t)PP_MBITS * n,
+             c->flags, n, M};
+  launch_pp_v(va, cmp, st);
+}
+
+DeriveArgs pp_derive_args(lwe_pp_ctx *c, const uint8_t *coins, const uint8_t *pkh) {
+  DeriveArgs da;
+  memset(&da, 0, sizeof da);
+  da.coins = coins;
+  da.pkh = pkh;
+  da.pkh_stride = 32;
+  da.mu = c->mu;
+  da.kprime = c->kp;
+  da.seeds = c->seeds;
+  da.rk = c->rk;
+  da.count = 1;
+  da.mu_bytes = 32;
+  return da;
+}
+
+}  // namespace
+
+extern "C" {
+
+int lwe_pp_params_preset(int id, lwe_pp_params *out) {
+  if (!out || id < 0 || id >= (int)(sizeof kPpPresets / sizeof kPpPresets[0])) return LWE_EINVAL;
+  lwe_pp_params p;
+  p.n = kPpPresets[id].n;
+  p.q = kPpPresets[id].q;
+  p.sigma = kPpPresets[id].sigma;
+  p.k = kPpPresets[id].k;
+  uint16_t T[16];
+  p.clip = 15;
+  while (p.clip > 1 && cdf_table(p.sigma, p.clip, T) != LWE_OK) p.clip--;
+  *out = p;
+  return LWE_OK;
+}
+
+int lwe_pp_params_check(const lwe_pp_params *p) {
+  if (!p) return LWE_EINVAL;
+  if (p->n < 64 || p->n > 65536 || (p->n % 64)) return LWE_EINVAL;
+  if (p->q < 3 || p->q > 65537 || !(p->q & 1)) return LWE_EINVAL;
+  if (p->k < 1 || p->k > 15) return LWE_EINVAL;
+  uint16_t T[16];
+  return cdf_table(p->sigma, p->clip, T);
+}
+
+size_t lwe_pp_pk_bytes(const lwe_pp_params *p) { return p ? pp_pk_bytes(*p) : 0; }
+size_t lwe_pp_sk_bytes(const lwe_pp_params *p) { return p ? pp_sk_bytes(*p) : 0; }
+size_t lwe_pp_ct_bytes(const lwe_pp_params *p) { return p ? pp_ct_bytes(*p) : 0; }
+
+int lwe_pp_ctx_create(const lwe_pp_params *p, int device, lwe_pp_ctx **out) {
+  if (!out) return LWE_EINVAL;
+  *out = nullptr;
+  if (lwe_pp_params_check(p) != LWE_OK) return LWE_EINVAL;
+  int ndev = 0;
+  CUDA_TRY(cudaGetDeviceCount(&ndev));
+  if (device < 0 || device >= ndev) return LWE_EINVAL;
+  int rc = device_setup(device);
+  if (rc != LWE_OK) return rc;
+  int prev = 0;
+  CUDA_TRY(cudaGetDevice(&prev));
+  CUDA_TRY(cudaSetDevice(device));
+  lwe_pp_ctx *c = new lwe_pp_ctx();
+  c->p = *p;
+  cdf_table(p->sigma, p->clip, c->T);
+  c->device = device;
+  cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
+  const size_t n = p->n;
+  size_t off = 0;
+  auto carve = [&](size_t bytes) {
+    size_t o = off;
+    off = align_up(off + bytes, 256);
+    return o;
+  };
+  const size_t o_seeds = carve(32), o_mu = carve(32), o_kp = carve(32), o_pkh = carve(32);
+  const size_t o_hc = carve(32), o_dig = carve(32 * (PP_MBITS + 1)), o_rk = carve(176);
+  const size_t o_flags = carve(16), o_e = carve(n), o_Rt = carve(PP_MBITS * n);
+  const size_t o_E1t = carve(PP_MBITS * n), o_e2 = carve(4 * PP_MBITS);
+  cudaError_t e = cudaMalloc(&c->ws, off);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    delete c;
+    cudaSetDevice(prev);
+    return LWE_ENOMEM;
+  }
+  c->seeds = c->ws + o_seeds;
+  c->mu = c->ws + o_mu;
+  c->kp = c->ws + o_kp;
+  c->pkh = c->ws + o_pkh;
+  c->hc = c->ws + o_hc;
+  c->digests = c->ws + o_dig;
+  c->rk = reinterpret_cast<uint32_t *>(c->ws + o_rk);
+  c->flags = reinterpret_cast<uint32_t *>(c->ws + o_flags);
+  c->e = reinterpret_cast<int8_t *>(c->ws + o_e);
+  c->Rt = reinterpret_cast<int8_t *>(c->ws + o_Rt);
+  c->E1t = reinterpret_cast<int8_t *>(c->ws + o_E1t);
+  c->e2 = reinterpret_cast<int32_t *>(c->ws + o_e2);
+  e = cudaMemset(c->ws, 0, off);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  cudaSetDevice(prev);
+  if (e != cudaSuccess) {
+    cudaFree(c->ws);
+    delete c;
+    return cuda_fail(e);
+  }
+  *out = c;
+  return LWE_OK;
+}
+
+int lwe_pp_ctx_destroy(lwe_pp_ctx *c) {
+  if (!c) return LWE_OK;
+  int prev = 0;
+  cudaGetDevice(&prev);
+  cudaSetDevice(c->device);
+  cudaDeviceSynchronize();
+  cudaFree(c->ws);
+  cudaSetDevice(prev);
+  delete c;
+  return LWE_OK;
+}
+
+int lwe_pp_expand_A(const lwe_pp_params *p, const uint8_t *seedA, uint32_t *A, void *stream) {
+  if (lwe_pp_params_check(p) != LWE_OK || !seedA || !A || !aligned16(A)) return LWE_EINVAL;
+  int sms = 0;
+  int rc = current_device_setup(nullptr, &sms);
+  if (rc) return rc;
+  launch_pp_expand_A(seedA, p->n, modq(p->q), A, sms, (cudaStream_t)stream);
+  return check_launch();
+}
+
+int lwe_pp_keygen(lwe_pp_ctx *c, const uint8_t *seed32, uint8_t *pk, uint8_t *sk, uint32_t *A,
+                  void *stream) {
+  if (!c || !seed32 || !pk || !sk || !A || !aligned16(pk) || !aligned16(sk) || !aligned16(A))
+    return LWE_EINVAL;
+  CUDA_TRY(cudaSetDevice(c->device));
+  cudaStream_t st = (cudaStream_t)stream;
+  const lwe_pp_params &p = c->p;
+  const uint32_t n = p.n;
+  const ModQ M = modq(p.q);
+  // seedA -> pk, the copy of pk in sk and seeds[0:16]; seedSE -> seeds[16:32]
+  // and its key schedule; z -> sk
+  KeygenSeedArgs ka;
+  memset(&ka, 0, sizeof ka);
+  ka.ms = seed32;
+  ka.pk = pk;
+  ka.sk = sk;
+  ka.ws_seeds = c->seeds;
+  ka.ws_rk = c->rk;
+  ka.pk_bytes = pp_pk_bytes(p);
+  ka.sk_bytes = pp_sk_bytes(p);
+  ka.sk_z_off = n;
+  ka.sk_pk_off = n + 64;
+  ka.count = 1;
+  launch_keygen_seeds(ka, (uint32_t)c->num_sms, st);
+  launch_pp_expand_A(c->seeds, n, M, A, c->num_sms, st);
+  PpNoiseArgs na;
+  memset(&na, 0, sizeof na);
+  na.rk = c->rk;
+  na.o[0] = PpNoiseOut{sk, n, PP_BINOMIAL, 1, 0};  // s: the first n bytes of sk
+  na.o[1] = PpNoiseOut{c->e, n, PP_GAUSS, 2, 0};
+  na.nout = 2;
+  na.clip = p.clip;
+  na.kunif = p.k;
+  for (int i = 0; i < 16; i++) na.T[i] = c->T[i];
+  launch_pp_noise(na, c->num_sms, st);
+  PpAsArgs aa{A, reinterpret_cast<const int8_t *>(sk), c->e, reinterpret_cast<uint32_t *>(pk + 16),
+              reinterpret_cast<uint32_t *>(sk + n + 64 + 16), n, M};
+  launch_pp_as(aa, st);
+  pp_tree(c, pk, pp_pk_bytes(p), (uint32_t)pp_pk_bytes(p), 1, TREE_DIGEST, sk + n + 32, 32, st);
+  return check_launch();
+}
+
+int lwe_pp_encaps(lwe_pp_ctx *c, const uint8_t *pk, const uint32_t *A, const uint8_t *coins32,
+                  uint8_t *ct, uint8_t *K, void *stream) {
+  if (!c || !pk || !A || !coins32 || !ct || !K || !aligned16(pk) || !aligned16(A) ||
+      !aligned16(ct))
+    return LWE_EINVAL;
+  CUDA_TRY(cudaSetDevice(c->device));
+  cudaStream_t st = (cudaStream_t)stream;
+  const lwe_pp_params &p = c->p;
+  pp_tree(c, pk, pp_pk_bytes(p), (uint32_t)pp_pk_bytes(p), 1, TREE_DIGEST, c->pkh, 32, st);
+  // m = H(0x4D || coins), K' = H(H(pk) || m), seedSE' and its key schedule
+  launch_derive(pp_derive_args(c, coins32, c->pkh), (uint32_t)c->num_sms, st);
+  pp_encrypt_noise(c, st);
+  pp_encrypt(c, reinterpret_cast<const uint32_t *>(pk + 16), A, ct, false, st);
+  pp_hash_ct(c, ct, TREE_ENC_KEY, K, st);  // K = H(K' || H(c))
+  return check_launch();
+}
+
+int lwe_pp_decaps(lwe_pp_ctx *c, const uint8_t *sk, const uint32_t *A, const uint8_t *ct,
+                  uint8_t *K, void *stream) {
+  if (!c || !sk || !A || !ct || !K || !aligned16(sk) || !aligned16(A) || !aligned16(ct))
+    return LWE_EINVAL;
+  CUDA_TRY(cudaSetDevice(c->device));
+  cudaStream_t st = (cudaStream_t)stream;
+  const lwe_pp_params &p = c->p;
+  const uint32_t n = p.n;
+  const uint8_t *z = sk + n, *pkh = sk + n + 32, *pk = sk + n + 64;
+  CUDA_TRY(cudaMemsetAsync(c->flags, 0, 4, st));
+  CUDA_TRY(cudaMemsetAsync(c->mu, 0, 32, st));
+  PpDecArgs dargs{reinterpret_cast<const uint32_t *>(ct),
+                  reinterpret_cast<const uint32_t *>(ct) + (size_t)PP_MBITS * n,
+                  reinterpret_cast<const int8_t *>(sk), reinterpret_cast<uint32_t *>(c->mu), n,
+                  modq(p.q)};
+  launch_pp_decrypt(dargs, st);  // m' into c->mu
+  launch_derive(pp_derive_args(c, nullptr, pkh), (uint32_t)c->num_sms, st);
+  pp_encrypt_noise(c, st);
+  pp_encrypt(c, reinterpret_cast<const uint32_t *>(pk + 16), A, const_cast<uint8_t *>(ct), true,
+             st);
+  pp_hash_ct(c, ct, TREE_DIGEST, c->hc, st);
+  FinalKeyArgs fa;
+  memset(&fa, 0, sizeof fa);
+  fa.kprime = c->kp;
+  fa.hc = c->hc;
+  fa.z = z;
+  fa.flags = c->flags;
+  fa.K = K;
+  fa.count = 1;
+  launch_final_key(fa, (uint32_t)c->num_sms, st);
+  return check_launch();
+}
 
 }  // extern "C"

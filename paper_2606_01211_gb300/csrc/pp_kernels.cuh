@@ -1,0 +1,345 @@
+// pp_kernels.cuh -- the paper's own parameter profile (Tab. 1): odd q in
+// {3329, 12289, 65537}, a 256-bit message encrypted bit by bit (Alg. 2 run
+// for 256 columns r_k at once), a binomial secret (eta = 3), Gaussian e, r,
+// e1 and a centred-uniform e2, threshold decoding (Alg. 3).  Entries mod q
+// are uint32; products accumulate in int32 with A centred to (-q/2, q/2]
+// and a reduction mod q at least every 4096 terms, so no sum exceeds 2^31.
+//
+// Included once, by kem_kernels.cu (it uses that file's AES table).
+#pragma once
+#include "pp_types.h"
+
+#define PP_A_DOMAIN 16  // stream domain of A's first try; try t uses 16 + t
+#define PP_A_TRIES 8
+#define PP_REDUCE_EVERY 4096
+
+// x mod q for x < 2^32 by Barrett reduction: m = floor(2^32 / q), so the
+// estimated quotient is low by at most one
+LWE_DEV uint32_t mod_u32(uint32_t x, ModQ M) {
+  const uint32_t r = x - __umulhi(x, M.m) * M.q;
+  return r >= M.q ? r - M.q : r;
+}
+
+LWE_DEV uint32_t mod_s32(int32_t x, ModQ M) {  // |x| < 2^31
+  const uint32_t r = mod_u32((uint32_t)(x < 0 ? -x : x), M);
+  return (x < 0 && r) ? M.q - r : r;
+}
+
+LWE_DEV int32_t centre(uint32_t a, uint32_t q) {
+  return a > q / 2 ? (int32_t)a - (int32_t)q : (int32_t)a;
+}
+
+// ---------------------------------------------------------------------------
+// A (Alg. 1 line 1) uniform mod q by rejection: entry (i, j) is 32-bit word
+// i n + j of the stream (seedA, domain 16 + t), accepted when below the
+// largest multiple of q under 2^32; a rejected word moves to the next try.
+// A thread takes one counter block = 4 consecutive entries of a row.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(512, 1) k_pp_expand_A(const uint8_t *__restrict__ seedA,
+                                                     uint32_t n, ModQ M, uint32_t *__restrict__ A) {
+  extern __shared__ uint32_t sT[];
+  pdl_trigger();
+  aes_fill_smem(sT, g_aes_T0);
+  __syncthreads();
+  pdl_wait();
+  const AesTab tab = aes_tab(sT);
+  uint32_t key[4], rk[44];
+  aes_load_key(seedA, key);
+  aes_key_expand(tab, key, rk);
+  const uint32_t limit = (uint32_t)((0x100000000ull / M.q) * M.q);
+  const uint64_t nblk = (uint64_t)n * n / 4;
+  uint4 *out = reinterpret_cast<uint4 *>(A);
+  for (uint64_t b = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; b < nblk;
+       b += (uint64_t)gridDim.x * blockDim.x) {
+    const uint4 v = aes_ctr_block(tab, rk, PP_A_DOMAIN, b);
+    uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+    for (int c = 0; c < 4; c++) {
+      bool ok = w[c] < limit;
+      for (uint32_t t = 1; !ok && t < PP_A_TRIES; t++) {  // rare: probability < q / 2^32
+        const uint4 u = aes_ctr_block(tab, rk, PP_A_DOMAIN + t, b);
+        const uint32_t x = c == 0 ? u.x : c == 1 ? u.y : c == 2 ? u.z : u.w;
+        if (x < limit) {
+          w[c] = x;
+          ok = true;
+        }
+      }
+      w[c] = ok ? mod_u32(w[c], M) : 0u;
+    }
+    out[b] = make_uint4(w[0], w[1], w[2], w[3]);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Noise streams (key schedule rk, one item): binomial eta = 3 from one byte
+// per sample, the CDF-table Gaussian from one 16-bit word, or the centred
+// uniform floor((2k + 1) w / 2^16) - k from one 16-bit word.
+// ---------------------------------------------------------------------------
+LWE_DEV uint32_t pp_noise_blocks(const PpNoiseOut &o) {
+  return o.kind == PP_BINOMIAL ? (o.count + 15) / 16 : (o.count + 7) / 8;
+}
+
+__global__ void __launch_bounds__(512, 1) k_pp_noise(PpNoiseArgs a) {
+  extern __shared__ uint32_t sT[];
+  pdl_trigger();
+  aes_fill_smem(sT, g_aes_T0);
+  __syncthreads();
+  pdl_wait();
+  const AesTab tab = aes_tab(sT);
+  uint32_t rk[44];
+#pragma unroll
+  for (int i = 0; i < 44; i++) rk[i] = a.rk[i];
+  uint32_t nb[3] = {0, 0, 0};
+  uint64_t total = 0;
+  for (uint32_t s = 0; s < a.nout; s++) {
+    nb[s] = pp_noise_blocks(a.o[s]);
+    total += nb[s];
+  }
+  for (uint64_t g = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; g < total;
+       g += (uint64_t)gridDim.x * blockDim.x) {
+    uint32_t s = 0;
+    uint64_t b = g;
+    while (s + 1 < a.nout && b >= nb[s]) {
+      b -= nb[s];
+      s++;
+    }
+    const PpNoiseOut o = a.o[s];
+    const uint4 v = aes_ctr_block(tab, rk, o.domain, b);
+    const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+    if (o.kind == PP_BINOMIAL) {
+      int8_t *dst = reinterpret_cast<int8_t *>(o.out);
+#pragma unroll
+      for (int t = 0; t < 16; t++) {
+        const uint32_t x = (w[t >> 2] >> (8 * (t & 3))) & 0xffu;
+        const int e = __popc(x & 7u) - __popc((x >> 3) & 7u);
+        const uint64_t idx = 16 * b + t;
+        if (idx < o.count) dst[idx] = (int8_t)e;
+      }
+    } else {
+#pragma unroll
+      for (int t = 0; t < 8; t++) {
+        const uint32_t h = (w[t >> 1] >> (16 * (t & 1))) & 0xffffu;
+        int e;
+        if (o.kind == PP_GAUSS) {
+          const uint32_t tt = h >> 1;
+          int mag = 0;
+          for (uint32_t i = 0; i < a.clip; i++) mag += tt > a.T[i] ? 1 : 0;
+          e = (h & 1u) ? -mag : mag;
+        } else {
+          e = (int)(((2u * a.kunif + 1u) * h) >> 16) - (int)a.kunif;
+        }
+        const uint64_t idx = 8 * b + t;
+        if (idx < o.count) {
+          if (o.kind == PP_GAUSS)
+            reinterpret_cast<int8_t *>(o.out)[idx] = (int8_t)e;
+          else
+            reinterpret_cast<int32_t *>(o.out)[idx] = e;
+        }
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// KeyGen (Alg. 1 line 4): t = A s + e mod q, warp per row, written to the
+// public key and to the copy of it inside the secret key.
+// ---------------------------------------------------------------------------
+LWE_DEV uint32_t warp_sum_mod(uint32_t x, ModQ M) {  // x < q on every lane
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+  return mod_u32(x, M);  // < 32 q < 2^32
+}
+
+__global__ void __launch_bounds__(256) k_pp_as(PpAsArgs a) {
+  pdl_trigger();
+  pdl_wait();
+  const uint32_t lane = threadIdx.x & 31;
+  const uint32_t i = blockIdx.x * 8 + (threadIdx.x >> 5);
+  if (i >= a.n) return;
+  const uint32_t *row = a.A + (size_t)i * a.n;
+  int32_t acc = 0;
+  uint32_t red = 0, since = 0;
+  for (uint32_t j = 4 * lane; j < a.n; j += 128) {
+    const uint4 x = ld_nc_u4(row + j);
+    const char4 s = *reinterpret_cast<const char4 *>(a.s + j);
+    acc += centre(x.x, a.M.q) * s.x + centre(x.y, a.M.q) * s.y + centre(x.z, a.M.q) * s.z +
+           centre(x.w, a.M.q) * s.w;
+    if ((since += 4) >= PP_REDUCE_EVERY) {
+      red = mod_u32(red + mod_s32(acc, a.M), a.M);
+      acc = 0;
+      since = 0;
+    }
+  }
+  red = mod_u32(red + mod_s32(acc, a.M), a.M);
+  const uint32_t sum = warp_sum_mod(red, a.M);
+  if (lane == 0) {
+    const uint32_t t = mod_u32(sum + mod_s32(a.e[i], a.M), a.M);
+    a.t[i] = t;
+    if (a.t2) a.t2[i] = t;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Encrypt's products (Alg. 2 line 4 for the 256 columns r_k at once):
+// U^T = R^T A + E1^T (mod q), R^T 256 x n int8, A n x n, as a CUDA-core GEMM.
+// CTA = 64 rows k x 64 columns j; thread (ty, tx) holds 4 x 4 sums; A tiles
+// of 32 x 64 (centred, int32) and R^T tiles of 64 x 32 (transposed to
+// [i][k], so 4 rows k are one 32-bit word) are staged in shared memory.
+// CMP (Decaps' re-encryption): compare with the received U^T instead of
+// storing, and flag a mismatch.
+// ---------------------------------------------------------------------------
+
+#define PPE_BM 64
+#define PPE_BN 64
+#define PPE_BK 32
+
+template <bool CMP>
+__global__ void __launch_bounds__(256) k_pp_encrypt(PpEncArgs a) {
+  __shared__ __align__(16) int32_t As[PPE_BK][PPE_BN];
+  __shared__ __align__(16) int8_t Rs[PPE_BK][PPE_BM];
+  pdl_trigger();
+  pdl_wait();
+  const uint32_t n = a.n, q = a.M.q;
+  const uint32_t j0 = blockIdx.x * PPE_BN, k0 = blockIdx.y * PPE_BM;
+  const uint32_t tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  int32_t acc[4][4];
+  uint32_t red[4][4];
+#pragma unroll
+  for (int r = 0; r < 4; r++)
+#pragma unroll
+    for (int c = 0; c < 4; c++) acc[r][c] = 0, red[r][c] = 0;
+  for (uint32_t i0 = 0; i0 < n; i0 += PPE_BK) {
+    // A tile: 32 rows x 64 columns = 512 uint4, two per thread
+#pragma unroll
+    for (int u = 0; u < 2; u++) {
+      const uint32_t idx = tid + 256 * u, row = idx >> 4, c4 = idx & 15;
+      const uint4 x = ld_nc_u4(a.A + (size_t)(i0 + row) * n + j0 + 4 * c4);
+      *reinterpret_cast<int4 *>(&As[row][4 * c4]) =
+          make_int4(centre(x.x, q), centre(x.y, q), centre(x.z, q), centre(x.w, q));
+    }
+    // R^T tile: 64 rows k x 32 columns i = 2048 bytes, 8 per thread
+    {
+      const uint32_t kk = tid >> 2, i8 = 8 * (tid & 3);
+      const uint2 r = ld_nc_u2(a.Rt + (size_t)(k0 + kk) * n + i0 + i8);
+#pragma unroll
+      for (int b = 0; b < 8; b++)
+        Rs[i8 + b][kk] = (int8_t)((b < 4 ? r.x >> (8 * b) : r.y >> (8 * (b - 4))) & 0xff);
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int ii = 0; ii < PPE_BK; ii++) {
+      const int4 x = *reinterpret_cast<const int4 *>(&As[ii][4 * tx]);
+      const uint32_t rw = *reinterpret_cast<const uint32_t *>(&Rs[ii][4 * ty]);
+      const int xv[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+      for (int r = 0; r < 4; r++) {
+        const int rv = (int)(int8_t)(rw >> (8 * r));
+#pragma unroll
+        for (int c = 0; c < 4; c++) acc[r][c] += rv * xv[c];
+      }
+    }
+    __syncthreads();
+    if ((i0 + PPE_BK) % PP_REDUCE_EVERY == 0) {
+#pragma unroll
+      for (int r = 0; r < 4; r++)
+#pragma unroll
+        for (int c = 0; c < 4; c++) {
+          red[r][c] = mod_u32(red[r][c] + mod_s32(acc[r][c], a.M), a.M);
+          acc[r][c] = 0;
+        }
+    }
+  }
+  uint32_t diff = 0;
+#pragma unroll
+  for (int r = 0; r < 4; r++) {
+    const uint32_t k = k0 + 4 * ty + r, j = j0 + 4 * tx;
+    const char4 e = *reinterpret_cast<const char4 *>(a.E1t + (size_t)k * n + j);
+    const int ev[4] = {e.x, e.y, e.z, e.w};
+    uint32_t val[4];
+#pragma unroll
+    for (int c = 0; c < 4; c++)
+      val[c] = mod_u32(mod_u32(red[r][c] + mod_s32(acc[r][c], a.M), a.M) + mod_s32(ev[c], a.M),
+                       a.M);
+    uint4 *o = reinterpret_cast<uint4 *>(a.Ut + (size_t)k * n + j);
+    if (CMP) {
+      const uint4 g = *o;
+      diff |= (g.x ^ val[0]) | (g.y ^ val[1]) | (g.z ^ val[2]) | (g.w ^ val[3]);
+    } else {
+      *o = make_uint4(val[0], val[1], val[2], val[3]);
+    }
+  }
+  if (CMP) {
+    diff = __reduce_or_sync(0xffffffffu, diff);
+    if ((tid & 31) == 0 && diff) atomicOr(a.flags, 1u);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// v_k = t^T r_k + e2_k + m_k floor(q/2) (mod q) (Alg. 2 line 5), warp per k;
+// CMP compares with the received v.
+// ---------------------------------------------------------------------------
+
+template <bool CMP>
+__global__ void __launch_bounds__(256) k_pp_v(PpVArgs a) {
+  pdl_trigger();
+  pdl_wait();
+  const uint32_t lane = threadIdx.x & 31, k = blockIdx.x * 8 + (threadIdx.x >> 5);
+  const int8_t *r = a.Rt + (size_t)k * a.n;
+  int32_t acc = 0;
+  uint32_t red = 0, since = 0;
+  for (uint32_t i = 4 * lane; i < a.n; i += 128) {
+    const uint4 x = ld_nc_u4(a.t + i);
+    const char4 s = *reinterpret_cast<const char4 *>(r + i);
+    acc += centre(x.x, a.M.q) * s.x + centre(x.y, a.M.q) * s.y + centre(x.z, a.M.q) * s.z +
+           centre(x.w, a.M.q) * s.w;
+    if ((since += 4) >= PP_REDUCE_EVERY) {
+      red = mod_u32(red + mod_s32(acc, a.M), a.M);
+      acc = 0;
+      since = 0;
+    }
+  }
+  red = mod_u32(red + mod_s32(acc, a.M), a.M);
+  const uint32_t sum = warp_sum_mod(red, a.M);
+  if (lane == 0) {
+    const uint32_t bit = (a.m[k >> 3] >> (k & 7)) & 1u;
+    const uint32_t v = mod_u32(mod_u32(sum + mod_s32(a.e2[k], a.M), a.M) + bit * (a.M.q / 2), a.M);
+    if (CMP) {
+      if (a.v[k] != v) atomicOr(a.flags, 1u);
+    } else {
+      a.v[k] = v;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Decrypt (Alg. 3): mu_k = v_k - s^T u_k (mod q), warp per k; bit k of m is
+// 1 iff q < 4 mu_k < 3q.  m (8 words, zeroed by the caller) gathers the bits.
+// ---------------------------------------------------------------------------
+
+__global__ void __launch_bounds__(256) k_pp_decrypt(PpDecArgs a) {
+  pdl_trigger();
+  pdl_wait();
+  const uint32_t lane = threadIdx.x & 31, k = blockIdx.x * 8 + (threadIdx.x >> 5);
+  const uint32_t *u = a.Ut + (size_t)k * a.n;
+  int32_t acc = 0;
+  uint32_t red = 0, since = 0;
+  for (uint32_t j = 4 * lane; j < a.n; j += 128) {
+    const uint4 x = ld_nc_u4(u + j);
+    const char4 s = *reinterpret_cast<const char4 *>(a.s + j);
+    acc += centre(x.x, a.M.q) * s.x + centre(x.y, a.M.q) * s.y + centre(x.z, a.M.q) * s.z +
+           centre(x.w, a.M.q) * s.w;
+    if ((since += 4) >= PP_REDUCE_EVERY) {
+      red = mod_u32(red + mod_s32(acc, a.M), a.M);
+      acc = 0;
+      since = 0;
+    }
+  }
+  red = mod_u32(red + mod_s32(acc, a.M), a.M);
+  const uint32_t su = warp_sum_mod(red, a.M);
+  if (lane == 0) {
+    const uint32_t q = a.M.q, mu = mod_u32(a.v[k] + q - su, a.M);
+    const uint64_t m4 = 4ull * mu;
+    const uint32_t bit = (m4 > q && m4 < 3ull * q) ? 1u : 0u;
+    if (bit) atomicOr(a.m + (k >> 5), 1u << (k & 31));
+  }
+}

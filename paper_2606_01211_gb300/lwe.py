@@ -47,6 +47,11 @@ class _Params(C.Structure):
                 ("sigma", C.c_double)]
 
 
+class _PpParams(C.Structure):
+    _fields_ = [("n", C.c_uint32), ("q", C.c_uint32), ("k", C.c_uint32), ("clip", C.c_uint32),
+                ("sigma", C.c_double)]
+
+
 def _load():
     if not os.path.exists(LIB):
         raise ImportError("liblwe.so is not built (run __graft_entry__.build() or "
@@ -54,6 +59,7 @@ def _load():
     lib = C.CDLL(LIB)
     vp, u32, i32, sz = C.c_void_p, C.c_uint32, C.c_int, C.c_size_t
     P = C.POINTER(_Params)
+    PP = C.POINTER(_PpParams)
     sig = {
         "lwe_params_preset": (i32, [i32, P]),
         "lwe_params_check": (i32, [P]),
@@ -84,6 +90,17 @@ def _load():
         "lwe_ctx_timing_replay": (i32, [vp]),
         "lwe_kernel_name": (C.c_char_p, [i32]),
         "lwe_num_kernels": (i32, []),
+        "lwe_pp_params_preset": (i32, [i32, PP]),
+        "lwe_pp_params_check": (i32, [PP]),
+        "lwe_pp_pk_bytes": (sz, [PP]),
+        "lwe_pp_sk_bytes": (sz, [PP]),
+        "lwe_pp_ct_bytes": (sz, [PP]),
+        "lwe_pp_ctx_create": (i32, [PP, i32, C.POINTER(vp)]),
+        "lwe_pp_ctx_destroy": (i32, [vp]),
+        "lwe_pp_expand_A": (i32, [PP, vp, vp, vp]),
+        "lwe_pp_keygen": (i32, [vp, vp, vp, vp, vp, vp]),
+        "lwe_pp_encaps": (i32, [vp, vp, vp, vp, vp, vp, vp]),
+        "lwe_pp_decaps": (i32, [vp, vp, vp, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -345,3 +362,94 @@ def probe(kind: int, ctas: int, iters: int, sink: torch.Tensor, stream=None):
     device tensor of at least ctas * 512 words."""
     _check(_lib.lwe_probe(kind, ctas, iters, _ptr(sink, torch.int32, ctas * 512 * 4, "sink"),
                           _stream(stream)), "lwe_probe")
+
+
+# ---- the paper's own parameter profile (lwe_pp.h) ---------------------------
+PP_PRESET_IDS = {"PP512": 0, "PP1024": 1, "PP2048": 2, "PP4096": 3, "PP8192": 4, "PP16384": 5,
+                 "PP32768": 6}
+
+
+class PpParams:
+    """Tab. 1 parameters: n, odd q, Gaussian sigma (clip), e2 bound k."""
+
+    def __init__(self, name: str | None = None, n: int = 0, q: int = 0, sigma: float = 0.0,
+                 k: int = 0, clip: int = 0):
+        self._c = _PpParams()
+        if name is not None:
+            _check(_lib.lwe_pp_params_preset(PP_PRESET_IDS[name], C.byref(self._c)),
+                   "lwe_pp_params_preset")
+        else:
+            self._c.n, self._c.q, self._c.sigma, self._c.k, self._c.clip = n, q, sigma, k, clip
+            _check(_lib.lwe_pp_params_check(C.byref(self._c)), "lwe_pp_params_check")
+        self.n, self.q, self.sigma = self._c.n, self._c.q, self._c.sigma
+        self.k, self.clip = self._c.k, self._c.clip
+        self.pk_bytes = int(_lib.lwe_pp_pk_bytes(C.byref(self._c)))
+        self.sk_bytes = int(_lib.lwe_pp_sk_bytes(C.byref(self._c)))
+        self.ct_bytes = int(_lib.lwe_pp_ct_bytes(C.byref(self._c)))
+
+
+def pp_expand_A(p: PpParams, seedA: torch.Tensor, A: torch.Tensor, stream=None):
+    _check(_lib.lwe_pp_expand_A(C.byref(p._c), _ptr(seedA, torch.uint8, 16, "seedA"),
+                                _ptr(A, torch.int32, 4 * p.n * p.n, "A"), _stream(stream)),
+           "lwe_pp_expand_A")
+
+
+class PpCtx:
+    """Workspace of the paper-profile KEM; one call at a time.  A is an
+    n x n int32 tensor holding the uint32 entries mod q."""
+
+    def __init__(self, p: PpParams, device: int | None = None):
+        self.params = p
+        h = C.c_void_p()
+        dev = torch.cuda.current_device() if device is None else device
+        _check(_lib.lwe_pp_ctx_create(C.byref(p._c), dev, C.byref(h)), "lwe_pp_ctx_create")
+        self._h = h
+
+    def close(self):
+        if self._h:
+            _lib.lwe_pp_ctx_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def empty_pk(self):
+        return torch.empty(self.params.pk_bytes, dtype=torch.uint8, device="cuda")
+
+    def empty_sk(self):
+        return torch.empty(self.params.sk_bytes, dtype=torch.uint8, device="cuda")
+
+    def empty_ct(self):
+        return torch.empty(self.params.ct_bytes, dtype=torch.uint8, device="cuda")
+
+    def empty_A(self):
+        n = self.params.n
+        return torch.empty((n, n), dtype=torch.int32, device="cuda")
+
+    def keygen(self, seed32, pk, sk, A, stream=None):
+        p = self.params
+        _check(_lib.lwe_pp_keygen(self._h, _ptr(seed32, torch.uint8, 32, "seed"),
+                                  _ptr(pk, torch.uint8, p.pk_bytes, "pk"),
+                                  _ptr(sk, torch.uint8, p.sk_bytes, "sk"),
+                                  _ptr(A, torch.int32, 4 * p.n * p.n, "A"), _stream(stream)),
+               "lwe_pp_keygen")
+
+    def encaps(self, pk, A, coins32, ct, K, stream=None):
+        p = self.params
+        _check(_lib.lwe_pp_encaps(self._h, _ptr(pk, torch.uint8, p.pk_bytes, "pk"),
+                                  _ptr(A, torch.int32, 4 * p.n * p.n, "A"),
+                                  _ptr(coins32, torch.uint8, 32, "coins"),
+                                  _ptr(ct, torch.uint8, p.ct_bytes, "ct"),
+                                  _ptr(K, torch.uint8, 32, "K"), _stream(stream)),
+               "lwe_pp_encaps")
+
+    def decaps(self, sk, A, ct, K, stream=None):
+        p = self.params
+        _check(_lib.lwe_pp_decaps(self._h, _ptr(sk, torch.uint8, p.sk_bytes, "sk"),
+                                  _ptr(A, torch.int32, 4 * p.n * p.n, "A"),
+                                  _ptr(ct, torch.uint8, p.ct_bytes, "ct"),
+                                  _ptr(K, torch.uint8, 32, "K"), _stream(stream)),
+               "lwe_pp_decaps")

@@ -1,0 +1,111 @@
+"""GPU parity of the paper-profile KEM (lwe_pp.h; Tab. 1: odd q, a 256-bit
+message encrypted bit by bit) against its oracle (oracle/pp.py), bit-exact:
+A, the keys, the ciphertext and both shared keys, implicit rejection, and a
+dimension above 4096 where the products reduce their sums mod q mid-way."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import pp
+from paper_2606_01211_gb300 import lwe
+
+pytestmark = pytest.mark.gpu
+
+CUSTOM = {  # q = 65537 with n > 4096: the 17-bit entries and the mid-way reduction
+    "Q65537_N4160": dict(n=4160, q=65537, sigma=1.2, k=2, clip=5),
+    "Q65537_N256": dict(n=256, q=65537, sigma=1.2, k=2, clip=5),
+}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _device():
+    assert torch.cuda.is_available()
+    torch.cuda.set_device(0)
+
+
+def _params(name):
+    if name in CUSTOM:
+        return lwe.PpParams(**CUSTOM[name]), pp.PParams(**CUSTOM[name])
+    return lwe.PpParams(name), pp.preset(name)
+
+
+def _dev(b: bytes) -> torch.Tensor:
+    return torch.from_numpy(np.frombuffer(b, np.uint8).copy()).cuda()
+
+
+def _host(t: torch.Tensor) -> bytes:
+    torch.cuda.synchronize()
+    return t.cpu().numpy().tobytes()
+
+
+@pytest.mark.parametrize("name", ["PP512", "PP1024", "Q65537_N256"])
+def test_expand_A_matches_oracle(name):
+    p, po = _params(name)
+    seed = bytes(range(40, 56))
+    A = torch.empty((p.n, p.n), dtype=torch.int32, device="cuda")
+    lwe.pp_expand_A(p, _dev(seed), A)
+    got = np.frombuffer(_host(A), "<u4").reshape(p.n, p.n)
+    assert np.array_equal(got, pp.expand_A(seed, po))
+
+
+@pytest.mark.parametrize("name", ["PP512", "PP1024", "Q65537_N256", "Q65537_N4160"])
+def test_kem_matches_oracle(name):
+    p, po = _params(name)
+    ms = bytes(range(7, 39))
+    coins = bytes(range(90, 122))
+    ctx = lwe.PpCtx(p)
+    pk, sk, A = ctx.empty_pk(), ctx.empty_sk(), ctx.empty_A()
+    ctx.keygen(_dev(ms), pk, sk, A)
+    pk_o, sk_o, A_o = pp.keygen(po, ms, want_A=True)
+    assert np.array_equal(np.frombuffer(_host(A), "<u4").reshape(p.n, p.n), A_o)
+    assert _host(pk) == pk_o
+    assert _host(sk) == sk_o
+    ct = ctx.empty_ct()
+    K = torch.empty(32, dtype=torch.uint8, device="cuda")
+    ctx.encaps(pk, A, _dev(coins), ct, K)
+    ct_o, K_o = pp.encaps(po, pk_o, coins, A_o)
+    ct_h = _host(ct)
+    if ct_h != ct_o:
+        g = np.frombuffer(ct_h, "<u4")
+        o = np.frombuffer(ct_o, "<u4")
+        bad = np.nonzero(g != o)[0]
+        raise AssertionError("ct differs at %d words, first %s" % (len(bad), bad[:5]))
+    assert _host(K) == K_o
+    K2 = torch.empty_like(K)
+    ctx.decaps(sk, A, ct, K2)
+    assert _host(K2) == K_o
+    # implicit rejection: one flipped bit in u and one in v
+    for pos in (4 * p.n + 3, po.ct_bytes - 5):
+        bad = ct.clone()
+        bad[pos] ^= 1
+        Kb = torch.empty_like(K)
+        ctx.decaps(sk, A, bad, Kb)
+        assert _host(Kb) == pp.decaps(po, sk_o, _host(bad), A_o)
+        assert _host(Kb) != K_o
+    ctx.close()
+
+
+@pytest.mark.parametrize("name", ["PP2048", "PP4096", "PP8192"])
+def test_round_trip_at_table_sizes(name):
+    """Decaps(Encaps) = K over several coins at the larger rows of Tab. 1
+    (the oracle checks sampled rows of A and the first item's keys)."""
+    p, po = _params(name)
+    ctx = lwe.PpCtx(p)
+    pk, sk, A = ctx.empty_pk(), ctx.empty_sk(), ctx.empty_A()
+    ms = bytes([3]) * 32
+    ctx.keygen(_dev(ms), pk, sk, A)
+    # sampled rows of A against the oracle's rejection sampler
+    seedA = _host(pk)[:16]
+    for i in (0, p.n // 2 + 1, p.n - 1):
+        words = [np.frombuffer(pp.O.ctr_stream(seedA, pp.A_DOMAIN + t, i * p.n // 4, p.n // 4),
+                               "<u4") for t in range(pp.A_TRIES)]
+        row = pp.a_from_words(words, p.q)
+        assert np.array_equal(A[i].cpu().numpy().view(np.uint32), row), i
+    K = torch.empty(32, dtype=torch.uint8, device="cuda")
+    K2 = torch.empty_like(K)
+    ct = ctx.empty_ct()
+    for j in range(3):
+        ctx.encaps(pk, A, _dev(bytes([j + 1]) * 32), ct, K)
+        ctx.decaps(sk, A, ct, K2)
+        assert _host(K) == _host(K2), j
+    ctx.close()

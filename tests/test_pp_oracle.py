@@ -146,9 +146,13 @@ def test_kem_round_trip_and_implicit_rejection():
     assert pp.decaps(p, sk, ct, A) == K
     m = hashlib.sha3_256(b"\x4d" + bytes([1]) * 32).digest()
     kp = hashlib.sha3_256(O.htree(pk) + m).digest()
-    assert K == hashlib.sha3_256(kp + O.htree(ct)).digest()
+    row = 4 * p.n
+    hc = O.htree(b"".join([O.htree(ct[k * row:(k + 1) * row]) for k in range(256)] +
+                          [O.htree(ct[256 * row:])]))
+    assert hc == pp.hash_ct(p, ct)
+    assert K == hashlib.sha3_256(kp + hc).digest()
     bad = bytearray(ct)
     bad[12345] ^= 4
     bad = bytes(bad)
     z = sk[p.n:p.n + 32]
-    assert pp.decaps(p, sk, bad, A) == hashlib.sha3_256(z + O.htree(bad)).digest()
+    assert pp.decaps(p, sk, bad, A) == hashlib.sha3_256(z + pp.hash_ct(p, bad)).digest()
