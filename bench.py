@@ -480,6 +480,7 @@ def run_ours(args, rank, world, local_rank):
     latency = single_request_latency(lwe, torch, dev) if extras and not args.no_latency else None
     sweep = kernel_sweep(lwe, torch, dev, flush) if extras and not args.no_sweep else None
     large = large_n(lwe, torch, dev) if extras and not args.no_large else None
+    ppr = paper_profile(lwe, torch, dev, cpu=not args.no_cpu) if extras and not args.no_pp else None
 
     cpu = None
     if extras and not args.no_cpu:
@@ -513,6 +514,7 @@ def run_ours(args, rank, world, local_rank):
         "as_gbs": sweep["AS_stored"] if sweep else None,
         "kernel_sweep": sweep,
         "large_n": large,
+        "paper_profile": ppr,
         "correct": bool(ok) and err == 0,
     }
     print(json.dumps(line))
@@ -691,6 +693,57 @@ def kernel_sweep(lwe, torch, dev, flush, sizes=(1344, 2048, 4096, 8192)):
     return out
 
 
+# The paper's own timings of this profile (Tab. 2 of the paper: OpenACC on
+# one GH200, microseconds per call), for context beside ours
+PAPER_PP_US = {1024: (3636.0, 8121.1, 5785.05), 4096: (8576.53, 19668.7, 10551.8)}
+
+
+def paper_profile(lwe, torch, dev, cpu: bool = True,
+                  names=("PP1024", "PP4096", "PP8192", "PP32768")):
+    """The paper's own parameter profile (Tab. 1: odd q, one Regev
+    encryption per message bit): one KeyGen, Encaps and Decaps per call with
+    A stored, CUDA-event ms per call (median of 3), Encaps+Decaps pairs/s,
+    and the rate of Encrypt's 256 x n by n x n product (G multiply-adds/s).
+    The oracle (numpy, BLAS) is timed on one PP1024 Encaps + Decaps."""
+    stream = torch.cuda.current_stream()
+    res = {}
+    for name in names:
+        p = lwe.PpParams(name)
+        n = p.n
+        ctx = lwe.PpCtx(p, device=dev.index)
+        pk, sk, A, ct = ctx.empty_pk(), ctx.empty_sk(), ctx.empty_A(), ctx.empty_ct()
+        K = torch.empty(32, dtype=torch.uint8, device=dev)
+        K2 = torch.empty_like(K)
+        ms = torch.from_numpy(master_seeds(1, seed=11)[0].copy()).to(dev)
+        cs = torch.from_numpy(coins(1, seed=11)[0].copy()).to(dev)
+        kg = _event_ms(torch, stream, lambda: ctx.keygen(ms, pk, sk, A), None, reps=3)
+        en = _event_ms(torch, stream, lambda: ctx.encaps(pk, A, cs, ct, K), None, reps=3)
+        de = _event_ms(torch, stream, lambda: ctx.decaps(sk, A, ct, K2), None, reps=3)
+        torch.cuda.synchronize()
+        assert torch.equal(K, K2)
+        r = {"keygen_ms": kg, "encaps_ms": en, "decaps_ms": de,
+             "pairs_per_s": 1e3 / (en + de),
+             "encrypt_gmac_per_s": 256.0 * n * n / (en / 1e3) / 1e9,
+             "ct_bytes": p.ct_bytes}
+        if n in PAPER_PP_US:
+            pk_, pe, pd = PAPER_PP_US[n]
+            r["paper_gh200_ms"] = {"keygen": pk_ / 1e3, "encaps": pe / 1e3, "decaps": pd / 1e3}
+            r["encaps_decaps_vs_paper"] = (pe + pd) / 1e3 / (en + de)
+        res[name] = r
+        ctx.close()
+        del A
+    if cpu:
+        from oracle import pp as opp
+        po = opp.preset("PP1024")
+        pk_o, sk_o, A_o = opp.keygen(po, bytes(32), want_A=True)
+        t0 = time.perf_counter()
+        ct_o, _ = opp.encaps(po, pk_o, bytes(range(32)), A_o)
+        opp.decaps(po, sk_o, ct_o, A_o)
+        res["oracle_PP1024_encaps_decaps_ms"] = (time.perf_counter() - t0) * 1e3
+    res["unit"] = "ms per call; one item per call"
+    return res
+
+
 def large_n(lwe, torch, dev, batch: int = 1024):
     """n = 16384 and 32768 (A = 0.5 / 2 GiB): one KeyGen, Encaps and Decaps
     per call with A stored in HBM vs regenerated tile by tile inside the
@@ -750,6 +803,7 @@ def main():
     ap.add_argument("--no-sweep", action="store_true")
     ap.add_argument("--no-large", action="store_true")
     ap.add_argument("--no-energy", action="store_true")
+    ap.add_argument("--no-pp", action="store_true")
     ap.add_argument("--sweep-only", type=str, default=None, metavar="N[,N...]",
                     help="only the standalone kernel sweep at these n (prints its JSON, not the bench line)")
     ap.add_argument("--cpu-s", type=float, default=12.0)
