@@ -63,10 +63,18 @@ size_t lwe_pp_sk_bytes(const lwe_pp_params *p);
 size_t lwe_pp_ct_bytes(const lwe_pp_params *p);
 
 typedef struct lwe_pp_ctx lwe_pp_ctx;
-/* Allocates the workspace (about 512 n + 4 KB bytes) on `device`; the only
- * allocating call.  LWE_EINVAL, LWE_ENOMEM, LWE_ECUDA. */
+/* Allocates the workspace on `device`: about 2.6 KB per unit of n for the
+ * noise, the bf16 copy of r and the K-split sums, plus 4 n^2 bytes for the
+ * bf16 limbs of A; the only allocating call.  LWE_EINVAL, LWE_ENOMEM,
+ * LWE_ECUDA. */
 int lwe_pp_ctx_create(const lwe_pp_params *p, int device, lwe_pp_ctx **out);
 int lwe_pp_ctx_destroy(lwe_pp_ctx *ctx);
+/* Options.  LWE_PP_OPT_TENSOR: 1 (default) computes Encrypt's product
+ * R^T A on the tensor cores (A split into two signed 8-bit limbs of its
+ * centred value, exact bf16 tcgen05 GEMM in K passes, reduced mod q in the
+ * epilogue); 0 on the CUDA cores (int32 multiply-adds). */
+enum { LWE_PP_OPT_TENSOR = 0 };
+int lwe_pp_ctx_set_option(lwe_pp_ctx *ctx, int option, int64_t value);
 
 /* A = sample(seedA) (Alg. 1 line 1) into A (n x n uint32).  seedA: 16
  * device bytes. */

@@ -274,9 +274,10 @@ LWE_DEV uint32_t fold_small(uint32_t lo_bits, uint32_t hi_bits) {
 // column n0 (zero where absent): E' and, for Decaps (ov != nullptr), the
 // received B'.  Issued ahead of the accumulator wait so that the load
 // latency overlaps the tile's MMAs.
-template <int CHUNKS>
+template <int CHUNKS, bool ODDQ = false>
 LWE_DEV void epilogue_prefetch(const GemmSaArgs &a, uint32_t row, uint32_t n0, uint4 *ev,
                                uint4 *ov) {
+  if (ODDQ) ov = nullptr;  // the odd-modulus epilogue reads the received rows itself
   const bool rv = row < a.rows;
   const uint8_t *obase = a.out + (size_t)(row >> 3) * a.out_stride + 2 * (size_t)(row & 7) * a.n;
 #pragma unroll
@@ -297,6 +298,87 @@ LWE_DEV void epilogue_prefetch(const GemmSaArgs &a, uint32_t row, uint32_t n0, u
   }
 }
 
+// x mod q for x < 2^32 (Barrett: m = floor(2^32 / q); one correction)
+LWE_DEV uint32_t oq_mod(uint32_t x, uint32_t q, uint32_t m) {
+  const uint32_t r = x - __umulhi(x, m) * q;
+  return r >= q ? r - q : r;
+}
+
+LWE_DEV uint32_t oq_mod_s(int32_t x, uint32_t q, uint32_t m) {  // |x| < 2^31
+  const uint32_t r = oq_mod((uint32_t)(x < 0 ? -x : x), q, m);
+  return (x < 0 && r) ? q - r : r;
+}
+
+// The odd-modulus epilogue (paper profile): the limbs' exact FP32 sums lo,
+// hi give (lo + 256 hi) mod q; add the K-split running sum (uint32 mod q)
+// and, in the final pass, E1 (int8), then store the row's uint32 entries or
+// compare them with the received ciphertext (item = row / 256).
+template <int CHUNKS>
+LWE_DEV void epilogue_tile_oddq(const GemmSaArgs &a, uint32_t row, uint32_t n0, uint32_t tl,
+                                uint32_t hi_off, const uint4 *ev) {
+  const uint32_t q = a.oddq_q, m = a.oddq_m;
+  const bool rv = row < a.rows;
+  uint32_t *orow = reinterpret_cast<uint32_t *>(a.out) + (size_t)row * a.n;
+  uint32_t diff = 0;
+#pragma unroll
+  for (uint32_t cc = 0; cc < CHUNKS; cc++) {
+    const uint32_t c = n0 + 16 * cc;
+    uint32_t lo[16], hi[16];
+    tmem_ld16(tl + 16 * cc, lo);
+    tmem_ld16(tl + hi_off + 16 * cc, hi);
+    tmem_wait_ld();
+    if (rv && c < a.ncols) {
+      uint32_t v[16];
+#pragma unroll
+      for (int t = 0; t < 16; t++) {
+        const int l = __float2int_rn(__uint_as_float(lo[t]));
+        const int h = __float2int_rn(__uint_as_float(hi[t]));
+        v[t] = oq_mod(oq_mod_s(l, q, m) + oq_mod(256u * oq_mod_s(h, q, m), q, m), q, m);
+      }
+      if (a.partial_in) {
+        const uint4 *pin = reinterpret_cast<const uint4 *>(
+            reinterpret_cast<const uint32_t *>(a.partial_in) + (size_t)row * a.ncols + c);
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+          const uint4 p = __ldg(pin + u);
+          v[4 * u] = oq_mod(v[4 * u] + p.x, q, m);
+          v[4 * u + 1] = oq_mod(v[4 * u + 1] + p.y, q, m);
+          v[4 * u + 2] = oq_mod(v[4 * u + 2] + p.z, q, m);
+          v[4 * u + 3] = oq_mod(v[4 * u + 3] + p.w, q, m);
+        }
+      }
+      uint4 *dst;
+      if (a.partial_out) {
+        dst = reinterpret_cast<uint4 *>(reinterpret_cast<uint32_t *>(a.partial_out) +
+                                        (size_t)row * a.ncols + c);
+      } else {
+        if (a.E) {
+          const uint32_t ew[4] = {ev[cc].x, ev[cc].y, ev[cc].z, ev[cc].w};
+#pragma unroll
+          for (int t = 0; t < 16; t++) v[t] = oq_mod(v[t] + oq_mod_s(sext8(ew[t >> 2], t & 3), q, m), q, m);
+        }
+        dst = reinterpret_cast<uint4 *>(orow + c);
+        if (a.cmp) {
+#pragma unroll
+          for (int u = 0; u < 4; u++) {
+            const uint4 g = __ldg(dst + u);
+            diff |= (g.x ^ v[4 * u]) | (g.y ^ v[4 * u + 1]) | (g.z ^ v[4 * u + 2]) |
+                    (g.w ^ v[4 * u + 3]);
+          }
+          continue;
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 4; u++)
+        dst[u] = make_uint4(v[4 * u], v[4 * u + 1], v[4 * u + 2], v[4 * u + 3]);
+    }
+  }
+  if (a.cmp && !a.partial_out) {
+    diff = __reduce_or_sync(0xffffffffu, diff);
+    if (rv && (row & 31) == 0 && diff) atomicOr(a.flags + (row >> 8), 1u);
+  }
+}
+
 // CHUNKS 16-column chunks of one output row of this CTA from its TMEM
 // accumulator (lo limb products at column tl + j, hi at tl + hi_off + j):
 // fold the limbs, add the K-split running sum, E' (B' columns) or E'' +
@@ -305,9 +387,13 @@ LWE_DEV void epilogue_prefetch(const GemmSaArgs &a, uint32_t row, uint32_t n0, u
 // column, tl the TMEM address of the first lo column of its lane quarter.
 // The received B' comes from ov when given (prefetched with the E'), else
 // it is loaded here one chunk ahead of its use.
-template <int CHUNKS>
+template <int CHUNKS, bool ODDQ = false>
 LWE_DEV void epilogue_tile(const GemmSaArgs &a, uint32_t row, uint32_t n0, uint32_t tl,
                            uint32_t hi_off, const uint4 *ev, const uint4 *ov) {
+  if (ODDQ) {
+    epilogue_tile_oddq<CHUNKS>(a, row, n0, tl, hi_off, ev);
+    return;
+  }
   const uint32_t D = a.logq, mask = (1u << D) - 1u;
   const bool rv = row < a.rows;
   const uint32_t e = row >> 3, kk = row & 7;
@@ -423,7 +509,7 @@ LWE_DEV void epilogue_tile(const GemmSaArgs &a, uint32_t row, uint32_t n0, uint3
   }
 }
 
-template <int BN>
+template <int BN, bool ODDQ>
 __global__ void __launch_bounds__(NTHREADS, 1)
     k_gemm_sa(const __grid_constant__ CUtensorMap tmS, const __grid_constant__ CUtensorMap tmL,
               const GemmSaArgs a) {
@@ -559,11 +645,11 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       const uint32_t m0 = (tile / num_n) * BM, n0 = (tile % num_n) * BN;
       const uint32_t row = m0 + 32 * q + lane;
       uint4 ev[BN / 16];
-      epilogue_prefetch<BN / 16>(a, row, n0, ev, nullptr);
+      epilogue_prefetch<BN / 16, ODDQ>(a, row, n0, ev, nullptr);
       if (!wait_bar_warp(tfull(acc), use & 1, abort_flag, a.dev_err)) break;
       tc_fence_after();
-      epilogue_tile<BN / 16>(a, row, n0, tmem_base + ((32 * q) << 16) + acc * (2 * BN), BN, ev,
-                             nullptr);
+      epilogue_tile<BN / 16, ODDQ>(a, row, n0, tmem_base + ((32 * q) << 16) + acc * (2 * BN), BN,
+                                   ev, nullptr);
       tc_fence_before();
       mbar_arrive(tempty(acc));
     }
@@ -582,6 +668,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 // only the leader (rank 0) issues MMAs.  Tiles: 256 rows (rank r owns rows
 // 128 r .. 128 r + 127 of the tile) x BN2 columns, both CTAs of a cluster
 // walking the same tile sequence.
+template <bool ODDQ>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHREADS2, 1)
     k_gemm_sa2(const __grid_constant__ CUtensorMap tmS, const __grid_constant__ CUtensorMap tmL,
                const GemmSaArgs a) {
@@ -736,19 +823,20 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHREADS2, 1)
     // the next tile's E' / received B' are loaded while this tile drains
     uint4 ev[BN2 / 32], ov[BN2 / 16];
     uint32_t it = 0;
-    if (cluster < num_tiles) epilogue_prefetch<BN2 / 32>(a, row_of(cluster), col_of(cluster), ev, ov);
+    if (cluster < num_tiles)
+      epilogue_prefetch<BN2 / 32, ODDQ>(a, row_of(cluster), col_of(cluster), ev, ov);
     for (uint32_t tile = cluster; tile < num_tiles; tile += nclusters, ++it) {
       const uint32_t acc = it & 1, use = it >> 1;
       if (!wait_bar_warp(tfull(acc), use & 1, abort_flag, a.dev_err)) break;
       tc_fence_after();
-      epilogue_tile<BN2 / 32>(a, row_of(tile), col_of(tile),
+      epilogue_tile<BN2 / 32, ODDQ>(a, row_of(tile), col_of(tile),
                               tmem_base + ((32 * q) << 16) + acc * (2 * BN2) + half * (BN2 / 2),
                               BN2, ev, ov);
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive_cluster(peer_addr(tempty(acc), 0));
       const uint32_t next = tile + nclusters;
-      if (next < num_tiles) epilogue_prefetch<BN2 / 32>(a, row_of(next), col_of(next), ev, ov);
+      if (next < num_tiles) epilogue_prefetch<BN2 / 32, ODDQ>(a, row_of(next), col_of(next), ev, ov);
     }
   }
   tc_fence_before();
@@ -804,7 +892,10 @@ int launch_bn(const GemmSaArgs &a, int num_sms, cudaStream_t st) {
   if (!make_map(&tmL, a.limbs, 3, dL, sL, bL)) return LWE_ECUDA;
   const uint32_t tiles = ((a.rows + BM - 1) / BM) * ((a.ncols + BN - 1) / BN);
   const int grid = (int)(tiles < (uint32_t)num_sms ? tiles : (uint32_t)num_sms);
-  launch_k(k_gemm_sa<BN>, grid, NTHREADS, C::SMEM, st, tmS, tmL, a);
+  if (a.oddq_q)
+    launch_k(k_gemm_sa<BN, true>, grid, NTHREADS, C::SMEM, st, tmS, tmL, a);
+  else
+    launch_k(k_gemm_sa<BN, false>, grid, NTHREADS, C::SMEM, st, tmS, tmL, a);
   return LWE_OK;
 }
 
@@ -821,7 +912,10 @@ int launch_pair(const GemmSaArgs &a, int num_sms, cudaStream_t st) {
   const uint32_t tiles = ((a.rows + 2 * BM - 1) / (2 * BM)) * ((a.ncols + BN2 - 1) / BN2);
   const uint32_t pairs = (uint32_t)(num_sms / 2);
   const uint32_t clusters = tiles < pairs ? tiles : pairs;
-  launch_k(k_gemm_sa2, 2 * clusters, NTHREADS2, Cfg2::SMEM, st, tmS, tmL, a);
+  if (a.oddq_q)
+    launch_k(k_gemm_sa2<true>, 2 * clusters, NTHREADS2, Cfg2::SMEM, st, tmS, tmL, a);
+  else
+    launch_k(k_gemm_sa2<false>, 2 * clusters, NTHREADS2, Cfg2::SMEM, st, tmS, tmL, a);
   return LWE_OK;
 }
 
@@ -837,13 +931,20 @@ cudaError_t lwe_gemm_setup() {
     if (q != cudaDriverEntryPointSuccess || !fn) return cudaErrorNotSupported;
     g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
   }
-  cudaError_t e = cudaFuncSetAttribute(k_gemm_sa<128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       Cfg<128>::SMEM);
-  if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_gemm_sa2, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg2::SMEM);
-  if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(k_gemm_sa<64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              Cfg<64>::SMEM);
+  cudaError_t e = cudaSuccess;
+  for (auto k : {k_gemm_sa<128, false>, k_gemm_sa<128, true>}) {
+    e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg<128>::SMEM);
+    if (e != cudaSuccess) return e;
+  }
+  for (auto k : {k_gemm_sa<64, false>, k_gemm_sa<64, true>}) {
+    e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg<64>::SMEM);
+    if (e != cudaSuccess) return e;
+  }
+  for (auto k : {k_gemm_sa2<false>, k_gemm_sa2<true>}) {
+    e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg2::SMEM);
+    if (e != cudaSuccess) return e;
+  }
+  return e;
 }
 
 // The fp32 accumulator is exact while every partial sum stays below 2^24:

@@ -44,6 +44,12 @@ struct GemmSaArgs {
   uint32_t kchunk;        // host: maximum exact K per pass (multiple of 64)
   uint32_t clip;          // |S'| bound c
   uint32_t fast_fold;     // set per pass: every partial sum is below 2^22
+  // Odd modulus (the paper's own profile, Tab. 1) when oddq_q != 0: the
+  // folded sums are reduced mod oddq_q (Barrett, oddq_m = floor(2^32 / q)),
+  // out holds rows of n uint32 (U^T, 256 rows per item), the K-split
+  // running sums are uint32 mod q (partial_in / partial_out reinterpreted),
+  // and there are no V columns.
+  uint32_t oddq_q, oddq_m;
 };
 
 cudaError_t lwe_gemm_setup();

@@ -1204,6 +1204,11 @@ struct lwe_pp_ctx {
   uint32_t *rk = nullptr, *flags = nullptr;
   int8_t *e = nullptr, *Rt = nullptr, *E1t = nullptr;
   int32_t *e2 = nullptr;
+  uint32_t *dev_err = nullptr;
+  uint16_t *Rbf = nullptr;     // r^T as bf16 (GEMM operand)
+  uint16_t *limbs = nullptr;   // [2][n][n] bf16 limbs of A
+  uint32_t *partial = nullptr; // K-split running sums, [256][n] mod q
+  bool tensor = false;         // LWE_PP_OPT_TENSOR (set when the GEMM supports n)
 };
 
 namespace {
@@ -1252,15 +1257,44 @@ void pp_encrypt_noise(lwe_pp_ctx *c, cudaStream_t st) {
 
 // U^T and v of Encrypt from c's noise and message c->mu; cmp compares them
 // with ct (Decaps) instead of writing
-void pp_encrypt(lwe_pp_ctx *c, const uint32_t *t, const uint32_t *A, uint8_t *ct, bool cmp,
-                cudaStream_t st) {
+int pp_encrypt(lwe_pp_ctx *c, const uint32_t *t, const uint32_t *A, uint8_t *ct, bool cmp,
+               cudaStream_t st) {
   const uint32_t n = c->p.n;
   const ModQ M = modq(c->p.q);
-  PpEncArgs ea{A, c->Rt, c->E1t, reinterpret_cast<uint32_t *>(ct), c->flags, n, M};
-  launch_pp_encrypt(ea, cmp, st);
+  if (c->tensor) {
+    // U^T = R^T A + E1^T on the tensor cores
+    launch_pp_limbs(A, n, c->p.q, c->limbs, st);
+    launch_s_to_bf16(c->Rt, (uint64_t)PP_MBITS * n, c->Rbf, c->num_sms, st);
+    GemmSaArgs ga;
+    memset(&ga, 0, sizeof ga);
+    ga.S = c->Rbf;
+    ga.limbs = c->limbs;
+    ga.E = c->E1t;
+    ga.out = ct;
+    ga.flags = c->flags;
+    ga.dev_err = c->dev_err;
+    ga.n = n;
+    ga.ncols = n;
+    ga.rows = PP_MBITS;
+    ga.logq = 16;
+    ga.cmp = cmp ? 1 : 0;
+    ga.bn = 128;
+    ga.pair = 1;
+    ga.clip = c->p.clip;
+    ga.kchunk = lwe_gemm_kchunk(c->p.clip);
+    ga.partial_out = reinterpret_cast<uint16_t *>(c->partial);
+    ga.oddq_q = M.q;
+    ga.oddq_m = M.m;
+    const int rc = launch_gemm_sa(ga, c->num_sms, st);
+    if (rc != LWE_OK) return rc;
+  } else {
+    PpEncArgs ea{A, c->Rt, c->E1t, reinterpret_cast<uint32_t *>(ct), c->flags, n, M};
+    launch_pp_encrypt(ea, cmp, st);
+  }
   PpVArgs va{t, c->Rt, c->e2, c->mu, reinterpret_cast<uint32_t *>(ct) + (size_t)PP_MBITS * n,
              c->flags, n, M};
   launch_pp_v(va, cmp, st);
+  return LWE_OK;
 }
 
 DeriveArgs pp_derive_args(lwe_pp_ctx *c, const uint8_t *coins, const uint8_t *pkh) {
@@ -1336,7 +1370,14 @@ int lwe_pp_ctx_create(const lwe_pp_params *p, int device, lwe_pp_ctx **out) {
   const size_t o_seeds = carve(32), o_mu = carve(32), o_kp = carve(32), o_pkh = carve(32);
   const size_t o_hc = carve(32), o_dig = carve(32 * (PP_MBITS + 1)), o_rk = carve(176);
   const size_t o_flags = carve(16), o_e = carve(n), o_Rt = carve(PP_MBITS * n);
-  const size_t o_E1t = carve(PP_MBITS * n), o_e2 = carve(4 * PP_MBITS);
+  const size_t o_E1t = carve(PP_MBITS * n), o_e2 = carve(4 * PP_MBITS), o_err = carve(16);
+  const bool tensor = lwe_gemm_supported((uint32_t)n, 16, p->clip);
+  size_t o_Rbf = 0, o_limbs = 0, o_partial = 0;
+  if (tensor) {
+    o_Rbf = carve(2 * PP_MBITS * n);
+    o_limbs = carve(4 * n * n);
+    o_partial = carve(4 * PP_MBITS * n);
+  }
   cudaError_t e = cudaMalloc(&c->ws, off);
   if (e != cudaSuccess) {
     cudaGetLastError();
@@ -1356,6 +1397,13 @@ int lwe_pp_ctx_create(const lwe_pp_params *p, int device, lwe_pp_ctx **out) {
   c->Rt = reinterpret_cast<int8_t *>(c->ws + o_Rt);
   c->E1t = reinterpret_cast<int8_t *>(c->ws + o_E1t);
   c->e2 = reinterpret_cast<int32_t *>(c->ws + o_e2);
+  c->dev_err = reinterpret_cast<uint32_t *>(c->ws + o_err);
+  c->tensor = tensor;
+  if (tensor) {
+    c->Rbf = reinterpret_cast<uint16_t *>(c->ws + o_Rbf);
+    c->limbs = reinterpret_cast<uint16_t *>(c->ws + o_limbs);
+    c->partial = reinterpret_cast<uint32_t *>(c->ws + o_partial);
+  }
   e = cudaMemset(c->ws, 0, off);
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
   cudaSetDevice(prev);
@@ -1378,6 +1426,17 @@ int lwe_pp_ctx_destroy(lwe_pp_ctx *c) {
   cudaSetDevice(prev);
   delete c;
   return LWE_OK;
+}
+
+int lwe_pp_ctx_set_option(lwe_pp_ctx *c, int option, int64_t value) {
+  if (!c) return LWE_EINVAL;
+  if (option == LWE_PP_OPT_TENSOR) {
+    if (value != 0 && value != 1) return LWE_EINVAL;
+    if (value && !c->limbs) return LWE_EUNSUPPORTED;
+    c->tensor = value != 0;
+    return LWE_OK;
+  }
+  return LWE_EINVAL;
 }
 
 int lwe_pp_expand_A(const lwe_pp_params *p, const uint8_t *seedA, uint32_t *A, void *stream) {
@@ -1443,7 +1502,8 @@ int lwe_pp_encaps(lwe_pp_ctx *c, const uint8_t *pk, const uint32_t *A, const uin
   // m = H(0x4D || coins), K' = H(H(pk) || m), seedSE' and its key schedule
   launch_derive(pp_derive_args(c, coins32, c->pkh), (uint32_t)c->num_sms, st);
   pp_encrypt_noise(c, st);
-  pp_encrypt(c, reinterpret_cast<const uint32_t *>(pk + 16), A, ct, false, st);
+  const int rc = pp_encrypt(c, reinterpret_cast<const uint32_t *>(pk + 16), A, ct, false, st);
+  if (rc != LWE_OK) return rc;
   pp_hash_ct(c, ct, TREE_ENC_KEY, K, st);  // K = H(K' || H(c))
   return check_launch();
 }
@@ -1466,8 +1526,9 @@ int lwe_pp_decaps(lwe_pp_ctx *c, const uint8_t *sk, const uint32_t *A, const uin
   launch_pp_decrypt(dargs, st);  // m' into c->mu
   launch_derive(pp_derive_args(c, nullptr, pkh), (uint32_t)c->num_sms, st);
   pp_encrypt_noise(c, st);
-  pp_encrypt(c, reinterpret_cast<const uint32_t *>(pk + 16), A, const_cast<uint8_t *>(ct), true,
-             st);
+  const int rc = pp_encrypt(c, reinterpret_cast<const uint32_t *>(pk + 16), A,
+                            const_cast<uint8_t *>(ct), true, st);
+  if (rc != LWE_OK) return rc;
   pp_hash_ct(c, ct, TREE_DIGEST, c->hc, st);
   FinalKeyArgs fa;
   memset(&fa, 0, sizeof fa);

@@ -343,3 +343,48 @@ __global__ void __launch_bounds__(256) k_pp_decrypt(PpDecArgs a) {
     if (bit) atomicOr(a.m + (k >> 5), 1u << (k & 31));
   }
 }
+
+// ---------------------------------------------------------------------------
+// The tensor-core form of Encrypt's product: the columns of A split into
+// two limbs of its centred value, x = lo + 256 hi with lo in [-128, 127]
+// and hi in [-128, 128], written as bf16 K-major (limbs[l][c][i]) for the
+// odd-modulus GEMM.  A 64 x 64 tile is transposed through shared memory.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_pp_limbs(const uint32_t *__restrict__ A, uint32_t n,
+                                                  uint32_t q, uint16_t *__restrict__ L) {
+  __shared__ int32_t tile[64][65];
+  pdl_trigger();
+  pdl_wait();
+  const uint32_t i0 = blockIdx.y * 64, c0 = blockIdx.x * 64;
+  for (uint32_t idx = threadIdx.x; idx < 64 * 16; idx += blockDim.x) {
+    const uint32_t r = idx >> 4, c4 = idx & 15;
+    const uint4 x = ld_nc_u4(A + (size_t)(i0 + r) * n + c0 + 4 * c4);
+    tile[r][4 * c4] = centre(x.x, q);
+    tile[r][4 * c4 + 1] = centre(x.y, q);
+    tile[r][4 * c4 + 2] = centre(x.z, q);
+    tile[r][4 * c4 + 3] = centre(x.w, q);
+  }
+  __syncthreads();
+  for (uint32_t idx = threadIdx.x; idx < 64 * 8; idx += blockDim.x) {
+    const uint32_t cl = idx >> 3, ic = idx & 7;
+    uint32_t lo[4], hi[4];
+#pragma unroll
+    for (int t = 0; t < 8; t += 2) {
+      float fl[2], fh[2];
+#pragma unroll
+      for (int u = 0; u < 2; u++) {
+        const int x = tile[8 * ic + t + u][cl];
+        const int l = (int)(int8_t)(uint8_t)(x & 0xff);
+        fl[u] = (float)l;
+        fh[u] = (float)((x - l) >> 8);
+      }
+      __nv_bfloat162 bl = __floats2bfloat162_rn(fl[0], fl[1]);
+      __nv_bfloat162 bh = __floats2bfloat162_rn(fh[0], fh[1]);
+      lo[t / 2] = *reinterpret_cast<uint32_t *>(&bl);
+      hi[t / 2] = *reinterpret_cast<uint32_t *>(&bh);
+    }
+    const size_t at = (size_t)(c0 + cl) * n + i0 + 8 * ic;
+    *reinterpret_cast<uint4 *>(L + at) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+    *reinterpret_cast<uint4 *>(L + (size_t)n * n + at) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+  }
+}

@@ -75,3 +75,5 @@ void launch_pp_as(const PpAsArgs &a, cudaStream_t st);
 void launch_pp_encrypt(const PpEncArgs &a, bool cmp, cudaStream_t st);
 void launch_pp_v(const PpVArgs &a, bool cmp, cudaStream_t st);
 void launch_pp_decrypt(const PpDecArgs &a, cudaStream_t st);
+// A (n x n uint32, entries mod q) -> bf16 limbs [2][n][n] of the GEMM
+void launch_pp_limbs(const uint32_t *A, uint32_t n, uint32_t q, uint16_t *limbs, cudaStream_t st);

@@ -97,6 +97,7 @@ def _load():
         "lwe_pp_ct_bytes": (sz, [PP]),
         "lwe_pp_ctx_create": (i32, [PP, i32, C.POINTER(vp)]),
         "lwe_pp_ctx_destroy": (i32, [vp]),
+        "lwe_pp_ctx_set_option": (i32, [vp, i32, C.c_int64]),
         "lwe_pp_expand_A": (i32, [PP, vp, vp, vp]),
         "lwe_pp_keygen": (i32, [vp, vp, vp, vp, vp, vp]),
         "lwe_pp_encaps": (i32, [vp, vp, vp, vp, vp, vp, vp]),
@@ -365,6 +366,7 @@ def probe(kind: int, ctas: int, iters: int, sink: torch.Tensor, stream=None):
 
 
 # ---- the paper's own parameter profile (lwe_pp.h) ---------------------------
+PP_OPT_TENSOR = 0
 PP_PRESET_IDS = {"PP512": 0, "PP1024": 1, "PP2048": 2, "PP4096": 3, "PP8192": 4, "PP16384": 5,
                  "PP32768": 6}
 
@@ -415,6 +417,10 @@ class PpCtx:
             self.close()
         except Exception:
             pass
+
+    def set_tensor(self, on: bool):
+        """Encrypt's product on the tensor cores (default) or the CUDA cores."""
+        _check(_lib.lwe_pp_ctx_set_option(self._h, PP_OPT_TENSOR, int(on)), "lwe_pp_ctx_set_option")
 
     def empty_pk(self):
         return torch.empty(self.params.pk_bytes, dtype=torch.uint8, device="cuda")

@@ -49,11 +49,15 @@ def test_expand_A_matches_oracle(name):
 
 
 @pytest.mark.parametrize("name", ["PP512", "PP1024", "Q65537_N256", "Q65537_N4160"])
-def test_kem_matches_oracle(name):
+@pytest.mark.parametrize("tensor", [True, False])
+def test_kem_matches_oracle(name, tensor):
+    """tensor: Encrypt's product on the tcgen05 GEMM (odd-modulus epilogue);
+    otherwise the CUDA-core kernel."""
     p, po = _params(name)
     ms = bytes(range(7, 39))
     coins = bytes(range(90, 122))
     ctx = lwe.PpCtx(p)
+    ctx.set_tensor(tensor)
     pk, sk, A = ctx.empty_pk(), ctx.empty_sk(), ctx.empty_A()
     ctx.keygen(_dev(ms), pk, sk, A)
     pk_o, sk_o, A_o = pp.keygen(po, ms, want_A=True)
@@ -85,7 +89,7 @@ def test_kem_matches_oracle(name):
     ctx.close()
 
 
-@pytest.mark.parametrize("name", ["PP2048", "PP4096", "PP8192"])
+@pytest.mark.parametrize("name", ["PP2048", "PP4096", "PP8192", "PP16384"])
 def test_round_trip_at_table_sizes(name):
     """Decaps(Encaps) = K over several coins at the larger rows of Tab. 1
     (the oracle checks sampled rows of A and the first item's keys)."""
@@ -104,8 +108,14 @@ def test_round_trip_at_table_sizes(name):
     K = torch.empty(32, dtype=torch.uint8, device="cuda")
     K2 = torch.empty_like(K)
     ct = ctx.empty_ct()
+    ct2 = ctx.empty_ct()
     for j in range(3):
         ctx.encaps(pk, A, _dev(bytes([j + 1]) * 32), ct, K)
         ctx.decaps(sk, A, ct, K2)
         assert _host(K) == _host(K2), j
+    # the tensor-core and CUDA-core products give the same ciphertext (at
+    # n = 16384 the GEMM runs in two exact K passes)
+    ctx.set_tensor(False)
+    ctx.encaps(pk, A, _dev(bytes([3]) * 32), ct2, K2)
+    assert torch.equal(ct, ct2) and torch.equal(K, K2)
     ctx.close()
