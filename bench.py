@@ -235,7 +235,7 @@ TRAFFIC = {
     "k_tree": (129.488640e6, 2,
                [("kem_kernels.cu", "k_tree"), ("kem_kernels.cu", "launch_tree"), ("keccak.cuh", None)],
                "67134a7a529e4ea2", "profiles/k_tree_p976.md"),
-    "k_gemm_tc": (302.521088e6, 2, [("gemm_tc.cu", None)], "397015ef0b62cd77",
+    "k_gemm_tc": (302.244608e6, 2, [("gemm_tc.cu", None)], "0e969b386a26680a",
                   "profiles/k_gemm_sa2_p976.md"),
     "k_noise": (70.732800e6, 2,
                 [("kem_kernels.cu", "k_noise"), ("kem_kernels.cu", "noise_runs"),

@@ -1297,6 +1297,14 @@ int pp_encrypt(lwe_pp_ctx *c, const uint32_t *t, const uint32_t *A, uint8_t *ct,
   return LWE_OK;
 }
 
+// the paper-profile calls launch their kernels with programmatic dependent
+// launch (every kernel they use waits on the device for its predecessor)
+struct PdlOn {
+  bool before = g_launch_pdl;
+  PdlOn() { g_launch_pdl = true; }
+  ~PdlOn() { g_launch_pdl = before; }
+};
+
 DeriveArgs pp_derive_args(lwe_pp_ctx *c, const uint8_t *coins, const uint8_t *pkh) {
   DeriveArgs da;
   memset(&da, 0, sizeof da);
@@ -1457,6 +1465,7 @@ int lwe_pp_keygen(lwe_pp_ctx *c, const uint8_t *seed32, uint8_t *pk, uint8_t *sk
   const lwe_pp_params &p = c->p;
   const uint32_t n = p.n;
   const ModQ M = modq(p.q);
+  PdlOn pdl;
   // seedA -> pk, the copy of pk in sk and seeds[0:16]; seedSE -> seeds[16:32]
   // and its key schedule; z -> sk
   KeygenSeedArgs ka;
@@ -1498,6 +1507,7 @@ int lwe_pp_encaps(lwe_pp_ctx *c, const uint8_t *pk, const uint32_t *A, const uin
   CUDA_TRY(cudaSetDevice(c->device));
   cudaStream_t st = (cudaStream_t)stream;
   const lwe_pp_params &p = c->p;
+  PdlOn pdl;
   pp_tree(c, pk, pp_pk_bytes(p), (uint32_t)pp_pk_bytes(p), 1, TREE_DIGEST, c->pkh, 32, st);
   // m = H(0x4D || coins), K' = H(H(pk) || m), seedSE' and its key schedule
   launch_derive(pp_derive_args(c, coins32, c->pkh), (uint32_t)c->num_sms, st);
@@ -1517,6 +1527,7 @@ int lwe_pp_decaps(lwe_pp_ctx *c, const uint8_t *sk, const uint32_t *A, const uin
   const lwe_pp_params &p = c->p;
   const uint32_t n = p.n;
   const uint8_t *z = sk + n, *pkh = sk + n + 32, *pk = sk + n + 64;
+  PdlOn pdl;
   CUDA_TRY(cudaMemsetAsync(c->flags, 0, 4, st));
   CUDA_TRY(cudaMemsetAsync(c->mu, 0, 32, st));
   PpDecArgs dargs{reinterpret_cast<const uint32_t *>(ct),
