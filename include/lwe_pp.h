@@ -72,8 +72,11 @@ int lwe_pp_ctx_destroy(lwe_pp_ctx *ctx);
 /* Options.  LWE_PP_OPT_TENSOR: 1 (default) computes Encrypt's product
  * R^T A on the tensor cores (A split into two signed 8-bit limbs of its
  * centred value, exact bf16 tcgen05 GEMM in K passes, reduced mod q in the
- * epilogue); 0 on the CUDA cores (int32 multiply-adds). */
-enum { LWE_PP_OPT_TENSOR = 0 };
+ * epilogue); 0 on the CUDA cores (int32 multiply-adds).  LWE_PP_OPT_PDL: 1
+ * launches the kernels of a call with programmatic stream serialisation (as
+ * LWE_OPT_PDL of lwe.h); 0 (default): plain launches, measured faster for
+ * these calls at n = 1024, 8192 and 32768. */
+enum { LWE_PP_OPT_TENSOR = 0, LWE_PP_OPT_PDL = 1 };
 int lwe_pp_ctx_set_option(lwe_pp_ctx *ctx, int option, int64_t value);
 
 /* A = sample(seedA) (Alg. 1 line 1) into A (n x n uint32).  seedA: 16

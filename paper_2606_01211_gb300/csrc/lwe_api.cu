@@ -1209,6 +1209,7 @@ struct lwe_pp_ctx {
   uint16_t *limbs = nullptr;   // [2][n][n] bf16 limbs of A
   uint32_t *partial = nullptr; // K-split running sums, [256][n] mod q
   bool tensor = false;         // LWE_PP_OPT_TENSOR (set when the GEMM supports n)
+  bool pdl = false;            // LWE_PP_OPT_PDL
 };
 
 namespace {
@@ -1297,11 +1298,11 @@ int pp_encrypt(lwe_pp_ctx *c, const uint32_t *t, const uint32_t *A, uint8_t *ct,
   return LWE_OK;
 }
 
-// the paper-profile calls launch their kernels with programmatic dependent
-// launch (every kernel they use waits on the device for its predecessor)
+// programmatic dependent launch for the paper-profile calls when enabled
+// (every kernel they use waits on the device for its predecessor)
 struct PdlOn {
   bool before = g_launch_pdl;
-  PdlOn() { g_launch_pdl = true; }
+  explicit PdlOn(bool on) { g_launch_pdl = on; }
   ~PdlOn() { g_launch_pdl = before; }
 };
 
@@ -1438,10 +1439,14 @@ int lwe_pp_ctx_destroy(lwe_pp_ctx *c) {
 
 int lwe_pp_ctx_set_option(lwe_pp_ctx *c, int option, int64_t value) {
   if (!c) return LWE_EINVAL;
+  if (value != 0 && value != 1) return LWE_EINVAL;
   if (option == LWE_PP_OPT_TENSOR) {
-    if (value != 0 && value != 1) return LWE_EINVAL;
     if (value && !c->limbs) return LWE_EUNSUPPORTED;
     c->tensor = value != 0;
+    return LWE_OK;
+  }
+  if (option == LWE_PP_OPT_PDL) {
+    c->pdl = value != 0;
     return LWE_OK;
   }
   return LWE_EINVAL;
@@ -1465,7 +1470,7 @@ int lwe_pp_keygen(lwe_pp_ctx *c, const uint8_t *seed32, uint8_t *pk, uint8_t *sk
   const lwe_pp_params &p = c->p;
   const uint32_t n = p.n;
   const ModQ M = modq(p.q);
-  PdlOn pdl;
+  PdlOn pdl(c->pdl);
   // seedA -> pk, the copy of pk in sk and seeds[0:16]; seedSE -> seeds[16:32]
   // and its key schedule; z -> sk
   KeygenSeedArgs ka;
@@ -1507,7 +1512,7 @@ int lwe_pp_encaps(lwe_pp_ctx *c, const uint8_t *pk, const uint32_t *A, const uin
   CUDA_TRY(cudaSetDevice(c->device));
   cudaStream_t st = (cudaStream_t)stream;
   const lwe_pp_params &p = c->p;
-  PdlOn pdl;
+  PdlOn pdl(c->pdl);
   pp_tree(c, pk, pp_pk_bytes(p), (uint32_t)pp_pk_bytes(p), 1, TREE_DIGEST, c->pkh, 32, st);
   // m = H(0x4D || coins), K' = H(H(pk) || m), seedSE' and its key schedule
   launch_derive(pp_derive_args(c, coins32, c->pkh), (uint32_t)c->num_sms, st);
@@ -1527,7 +1532,7 @@ int lwe_pp_decaps(lwe_pp_ctx *c, const uint8_t *sk, const uint32_t *A, const uin
   const lwe_pp_params &p = c->p;
   const uint32_t n = p.n;
   const uint8_t *z = sk + n, *pkh = sk + n + 32, *pk = sk + n + 64;
-  PdlOn pdl;
+  PdlOn pdl(c->pdl);
   CUDA_TRY(cudaMemsetAsync(c->flags, 0, 4, st));
   CUDA_TRY(cudaMemsetAsync(c->mu, 0, 32, st));
   PpDecArgs dargs{reinterpret_cast<const uint32_t *>(ct),

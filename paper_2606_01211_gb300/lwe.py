@@ -366,7 +366,7 @@ def probe(kind: int, ctas: int, iters: int, sink: torch.Tensor, stream=None):
 
 
 # ---- the paper's own parameter profile (lwe_pp.h) ---------------------------
-PP_OPT_TENSOR = 0
+PP_OPT_TENSOR, PP_OPT_PDL = 0, 1
 PP_PRESET_IDS = {"PP512": 0, "PP1024": 1, "PP2048": 2, "PP4096": 3, "PP8192": 4, "PP16384": 5,
                  "PP32768": 6}
 
@@ -421,6 +421,9 @@ class PpCtx:
     def set_tensor(self, on: bool):
         """Encrypt's product on the tensor cores (default) or the CUDA cores."""
         _check(_lib.lwe_pp_ctx_set_option(self._h, PP_OPT_TENSOR, int(on)), "lwe_pp_ctx_set_option")
+
+    def set_option(self, option: int, value: int):
+        _check(_lib.lwe_pp_ctx_set_option(self._h, option, int(value)), "lwe_pp_ctx_set_option")
 
     def empty_pk(self):
         return torch.empty(self.params.pk_bytes, dtype=torch.uint8, device="cuda")
