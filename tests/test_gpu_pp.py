@@ -48,16 +48,20 @@ def test_expand_A_matches_oracle(name):
     assert np.array_equal(got, pp.expand_A(seed, po))
 
 
-@pytest.mark.parametrize("name", ["PP512", "PP1024", "Q65537_N256", "Q65537_N4160"])
-@pytest.mark.parametrize("tensor", [True, False])
-def test_kem_matches_oracle(name, tensor):
-    """tensor: Encrypt's product on the tcgen05 GEMM (odd-modulus epilogue);
-    otherwise the CUDA-core kernel."""
+@pytest.mark.parametrize("name,tensor,pdl", [
+    ("PP512", True, False), ("PP512", False, False), ("PP1024", True, False),
+    ("PP1024", False, False), ("Q65537_N256", True, False), ("Q65537_N256", False, False),
+    ("Q65537_N4160", True, False), ("Q65537_N4160", False, False),
+    ("PP1024", True, True), ("Q65537_N256", True, True)])
+def test_kem_matches_oracle(name, tensor, pdl):
+    """tensor: Encrypt's product on the tcgen05 GEMM (odd-modulus epilogue),
+    otherwise the CUDA-core kernel; pdl: programmatic dependent launch."""
     p, po = _params(name)
     ms = bytes(range(7, 39))
     coins = bytes(range(90, 122))
     ctx = lwe.PpCtx(p)
     ctx.set_tensor(tensor)
+    ctx.set_option(lwe.PP_OPT_PDL, int(pdl))
     pk, sk, A = ctx.empty_pk(), ctx.empty_sk(), ctx.empty_A()
     ctx.keygen(_dev(ms), pk, sk, A)
     pk_o, sk_o, A_o = pp.keygen(po, ms, want_A=True)
