@@ -207,6 +207,15 @@ def algorithmic_bytes(p, count):
     }
 
 
+# What bounds each kernel in ncu (profiles/): "alu" above means an
+# instruction-throughput bound measured against lwe_probe, not HBM or tensor
+LIMITER = {
+    "k_noise": "shared-memory pipe: AES round-table lookups plus the sampler's table",
+    "k_tree": "integer ALU pipe: Keccak-f XORs, rotations and chi",
+    "k_gemm_tc": "tensor pipe (bf16 tcgen05, CTA pairs)",
+}
+
+
 def algorithmic(p, count):
     """Algorithmic work of the kernels in one step (summed over launches)."""
     n = p.n
@@ -445,7 +454,8 @@ def run_ours(args, rank, world, local_rank):
                 "share": kernel_total[dom] / sum(kernel_total.values()),
                 "algorithmic_bytes": algorithmic_bytes(p, COUNT).get(dom, 0.0) / (nl / args.steps),
                 "traffic": traffic_per_launch(dom),
-                "timing": "CUDA events around each launch of direct-launch steps, one stream"}
+                "timing": "CUDA events around each launch of direct-launch steps, one stream",
+                "limiter": LIMITER.get(dom)}
 
     # the per-GPU extras (energy, plain path, serving, latency, sweeps, the
     # CPU baseline) are measured at N = 1; a multi-GPU run reports the
