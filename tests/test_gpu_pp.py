@@ -123,3 +123,26 @@ def test_round_trip_at_table_sizes(name):
     ctx.encaps(pk, A, _dev(bytes([3]) * 32), ct2, K2)
     assert torch.equal(ct, ct2) and torch.equal(K, K2)
     ctx.close()
+
+
+@pytest.mark.parametrize("name", ["PP512", "PP4096", "PP32768"])
+def test_round_trips_over_many_coins(name):
+    """Decaps(Encaps(pk)) = K for 64 coin values against one key (Tab. 1's
+    parameters keep the decryption noise below q/4 by 6-84 standard
+    deviations), and a ciphertext with one flipped bit is rejected."""
+    p = lwe.PpParams(name)
+    ctx = lwe.PpCtx(p)
+    pk, sk, A, ct = ctx.empty_pk(), ctx.empty_sk(), ctx.empty_A(), ctx.empty_ct()
+    ctx.keygen(_dev(bytes([5]) * 32), pk, sk, A)
+    K = torch.empty(32, dtype=torch.uint8, device="cuda")
+    K2 = torch.empty_like(K)
+    reps = 64 if p.n <= 4096 else 8
+    for j in range(reps):
+        ctx.encaps(pk, A, _dev(j.to_bytes(32, "little")), ct, K)
+        ctx.decaps(sk, A, ct, K2)
+        assert torch.equal(K, K2), j
+        if j % 8 == 0:
+            ct[(j * 7919) % p.ct_bytes] ^= 1
+            ctx.decaps(sk, A, ct, K2)
+            assert not torch.equal(K, K2), j
+    ctx.close()
