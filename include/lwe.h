@@ -302,14 +302,19 @@ int lwe_selftest_bounded_wait(lwe_ctx *ctx, uint32_t limit_us, void *stream);
  *     permutation of k_tree).  Work: ctas * 256 * iters permutations.
  *   LWE_PROBE_AES: `ctas` CTAs of 512 threads with the AES round tables in
  *     shared memory; each thread encrypts `iters` (even) counter blocks, two
- *     at a time (the generator of k_noise).  Work: ctas * 512 * iters blocks.
+ *     at a time (the generator of A).  Work: ctas * 512 * iters blocks.
+ *   LWE_PROBE_AES_RUN: as LWE_PROBE_AES with the blocks of a warp taken
+ *     four per lane from one 128-block run of counter indices, whose first
+ *     two rounds are shared (the generator of k_noise); iters a multiple
+ *     of 4.
  *   LWE_PROBE_KECCAK_WARP: `ctas` CTAs of one warp; each warp applies
  *     Keccak-f[1600] `iters` times to one state spread over its lanes (the
  *     permutation of k_tree_warp).  Work: ctas * iters permutations.
  * One word per thread is written to sink (device, >= ctas * 512 words) so
  * that the work is kept.  Asynchronous on `stream`; time it with CUDA events
- * there.  LWE_EINVAL for an unknown kind, ctas = 0, or an odd iters for AES. */
-enum { LWE_PROBE_KECCAK = 0, LWE_PROBE_AES = 1, LWE_PROBE_KECCAK_WARP = 2 };
+ * there.  LWE_EINVAL for an unknown kind, ctas = 0, or iters not a multiple
+ * of 2 (AES) or 4 (AES_RUN). */
+enum { LWE_PROBE_KECCAK = 0, LWE_PROBE_AES = 1, LWE_PROBE_KECCAK_WARP = 2, LWE_PROBE_AES_RUN = 3 };
 int lwe_probe(int kind, uint32_t ctas, uint32_t iters, uint32_t *sink, void *stream);
 
 /* Per-kernel event timing (needs LWE_OPT_TIMING = 1; synchronises). */

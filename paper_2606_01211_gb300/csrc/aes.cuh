@@ -126,6 +126,71 @@ LWE_DEV uint4 aes_ctr_block(const AesTab &tab, const uint32_t rk[44], uint64_t d
   return make_uint4(s0, s1, s2, s3);
 }
 
+// Counter blocks that differ only in the low byte of the index.  Inside a
+// 256-aligned window of indices the input block varies in its last byte
+// alone, which is byte 3 of s3.  After ShiftRows that byte feeds one column
+// of round 1 (t0, through T3), and t0 feeds one lookup of each column of
+// round 2.  So 15 of round 1's 16 lookups and 12 of round 2's are the same
+// for the whole window: AesCtrRun holds their XORs (with the round keys),
+// and a block of the window costs 1 + 4 + 8 x 16 = 133 lookups instead of
+// 160.  The result is the same AES-128 encryption, bit for bit.
+struct AesCtrRun {
+  uint32_t s3;      // s3 ^ rk[3] of the window's first index (low byte 0)
+  uint32_t k0;      // round 1, column 0 without the varying lookup
+  uint32_t k1, k2, k3, k4;  // round 2, columns 0..3 without the varying lookup
+};
+
+// Window of `index` (its low byte ignored) in stream `domain`.
+LWE_DEV AesCtrRun aes_ctr_run(const AesTab &tab, const uint32_t rk[44], uint64_t domain,
+                              uint64_t index) {
+  const uint32_t s0 = bswap32((uint32_t)(domain >> 32)) ^ rk[0];
+  const uint32_t s1 = bswap32((uint32_t)domain) ^ rk[1];
+  const uint32_t s2 = bswap32((uint32_t)(index >> 32)) ^ rk[2];
+  const uint32_t s3 = bswap32((uint32_t)index & ~0xffu) ^ rk[3];
+  AesCtrRun w;
+  w.s3 = s3;
+  w.k0 = tab.T<0, 0>(s0) ^ tab.T<1, 1>(s1) ^ tab.T<2, 2>(s2) ^ rk[4];
+  const uint32_t t1 = tab.T<0, 0>(s1) ^ tab.T<1, 1>(s2) ^ tab.T<2, 2>(s3) ^ tab.T<3, 3>(s0) ^ rk[5];
+  const uint32_t t2 = tab.T<0, 0>(s2) ^ tab.T<1, 1>(s3) ^ tab.T<2, 2>(s0) ^ tab.T<3, 3>(s1) ^ rk[6];
+  const uint32_t t3 = tab.T<0, 0>(s3) ^ tab.T<1, 1>(s0) ^ tab.T<2, 2>(s1) ^ tab.T<3, 3>(s2) ^ rk[7];
+  w.k1 = tab.T<1, 1>(t1) ^ tab.T<2, 2>(t2) ^ tab.T<3, 3>(t3) ^ rk[8];
+  w.k2 = tab.T<0, 0>(t1) ^ tab.T<1, 1>(t2) ^ tab.T<2, 2>(t3) ^ rk[9];
+  w.k3 = tab.T<0, 0>(t2) ^ tab.T<1, 1>(t3) ^ tab.T<3, 3>(t1) ^ rk[10];
+  w.k4 = tab.T<0, 0>(t3) ^ tab.T<2, 2>(t1) ^ tab.T<3, 3>(t2) ^ rk[11];
+  return w;
+}
+
+// Keystream block of index (window base | x), x < 256; equal to
+// aes_ctr_block for that index.
+LWE_DEV uint4 aes_ctr_run_block(const AesTab &tab, const uint32_t rk[44], const AesCtrRun &w,
+                                uint32_t x) {
+  const uint32_t t0 = w.k0 ^ tab.T<3, 3>(w.s3 ^ (x << 24));
+  uint32_t s0 = tab.T<0, 0>(t0) ^ w.k1;
+  uint32_t s1 = tab.T<3, 3>(t0) ^ w.k2;
+  uint32_t s2 = tab.T<2, 2>(t0) ^ w.k3;
+  uint32_t s3 = tab.T<1, 1>(t0) ^ w.k4;
+#pragma unroll
+  for (int r = 3; r < 10; r++) {
+    const uint32_t t0 = tab.T<0, 0>(s0) ^ tab.T<1, 1>(s1) ^ tab.T<2, 2>(s2) ^ tab.T<3, 3>(s3) ^ rk[4 * r + 0];
+    const uint32_t t1 = tab.T<0, 0>(s1) ^ tab.T<1, 1>(s2) ^ tab.T<2, 2>(s3) ^ tab.T<3, 3>(s0) ^ rk[4 * r + 1];
+    const uint32_t t2 = tab.T<0, 0>(s2) ^ tab.T<1, 1>(s3) ^ tab.T<2, 2>(s0) ^ tab.T<3, 3>(s1) ^ rk[4 * r + 2];
+    const uint32_t t3 = tab.T<0, 0>(s3) ^ tab.T<1, 1>(s0) ^ tab.T<2, 2>(s1) ^ tab.T<3, 3>(s2) ^ rk[4 * r + 3];
+    s0 = t0;
+    s1 = t1;
+    s2 = t2;
+    s3 = t3;
+  }
+  const uint32_t o0 = (tab.T<3, 0>(s0) & 0x000000ffu) | (tab.T<0, 1>(s1) & 0x0000ff00u) |
+                      (tab.T<1, 2>(s2) & 0x00ff0000u) | (tab.T<2, 3>(s3) & 0xff000000u);
+  const uint32_t o1 = (tab.T<3, 0>(s1) & 0x000000ffu) | (tab.T<0, 1>(s2) & 0x0000ff00u) |
+                      (tab.T<1, 2>(s3) & 0x00ff0000u) | (tab.T<2, 3>(s0) & 0xff000000u);
+  const uint32_t o2 = (tab.T<3, 0>(s2) & 0x000000ffu) | (tab.T<0, 1>(s3) & 0x0000ff00u) |
+                      (tab.T<1, 2>(s0) & 0x00ff0000u) | (tab.T<2, 3>(s1) & 0xff000000u);
+  const uint32_t o3 = (tab.T<3, 0>(s3) & 0x000000ffu) | (tab.T<0, 1>(s0) & 0x0000ff00u) |
+                      (tab.T<1, 2>(s1) & 0x00ff0000u) | (tab.T<2, 3>(s2) & 0xff000000u);
+  return make_uint4(o0 ^ rk[40], o1 ^ rk[41], o2 ^ rk[42], o3 ^ rk[43]);
+}
+
 // Load a 16-byte key from memory as four little-endian words.
 LWE_DEV void aes_load_key(const uint8_t *key, uint32_t k[4]) {
   if ((reinterpret_cast<uintptr_t>(key) & 15) == 0) {

@@ -49,14 +49,30 @@ __global__ void __launch_bounds__(512, 1) k_expand_A(const uint8_t *__restrict__
   const uint32_t mm = m | (m << 16);
   const uint64_t nblk = (uint64_t)n * n / 8;
   uint4 *out = reinterpret_cast<uint4 *>(A + (size_t)e * a_stride);
-  for (uint64_t b = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; b < nblk;
-       b += (uint64_t)gridDim.x * blockDim.x) {
-    uint4 v = aes_ctr_block(tab, rk, 0, b);
-    v.x &= mm;
-    v.y &= mm;
-    v.z &= mm;
-    v.w &= mm;
-    out[b] = v;
+  // a warp takes runs of 128 consecutive blocks (4 per lane, two at a time);
+  // a run lies inside one 256-aligned counter window (aes_ctr_run)
+  const uint32_t lane = threadIdx.x & 31;
+  const uint64_t nruns = (nblk + 127) / 128, nw = (uint64_t)gridDim.x * (blockDim.x >> 5);
+  for (uint64_t run = (uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); run < nruns;
+       run += nw) {
+    const uint64_t first = run * 128;
+    const AesCtrRun win = aes_ctr_run(tab, rk, 0, first);
+    const uint32_t x0 = (uint32_t)(first & 255u) + lane;
+    if (first + 128 <= nblk) {
+#pragma unroll
+      for (uint32_t j = 0; j < 4; j += 2) {
+        uint4 va = aes_ctr_run_block(tab, rk, win, x0 + 32 * j);
+        uint4 vb = aes_ctr_run_block(tab, rk, win, x0 + 32 * j + 32);
+        out[first + lane + 32 * j] = make_uint4(va.x & mm, va.y & mm, va.z & mm, va.w & mm);
+        out[first + lane + 32 * j + 32] = make_uint4(vb.x & mm, vb.y & mm, vb.z & mm, vb.w & mm);
+      }
+    } else {
+#pragma unroll 1
+      for (uint32_t x = x0; first + (x - x0) + lane < nblk; x += 32) {
+        const uint4 v = aes_ctr_run_block(tab, rk, win, x);
+        out[first + (x - x0) + lane] = make_uint4(v.x & mm, v.y & mm, v.z & mm, v.w & mm);
+      }
+    }
   }
 }
 
@@ -156,20 +172,23 @@ LWE_DEV void noise_runs(const NoiseArgs &a, const AesTab &tab, const char *smem,
     }
     const uint32_t nblk = (o.nsamples + 7) / 8;
     uint8_t *base = reinterpret_cast<uint8_t *>(o.base) + (size_t)e * o.item_stride;
-    const uint32_t b0 = r * NOISE_RUN + lane;
-    if (r * NOISE_RUN + NOISE_RUN <= nblk) {
+    // a run lies inside one 256-aligned window of counter indices, so the
+    // window's first two AES rounds are computed once (aes_ctr_run)
+    const uint32_t first = r * NOISE_RUN, b0 = first + lane, x0 = (first & 255u) + lane;
+    const AesCtrRun win = aes_ctr_run(tab, rk, o.domain, first);
+    if (first + NOISE_RUN <= nblk) {
       // full run: two independent blocks in flight per lane
 #pragma unroll
       for (uint32_t j = 0; j < NOISE_RUN / 32; j += 2) {
-        const uint32_t ba = b0 + 32 * j, bb = ba + 32;
-        const uint4 va = aes_ctr_block(tab, rk, o.domain, ba);
-        const uint4 vb = aes_ctr_block(tab, rk, o.domain, bb);
-        noise_store(smem, o, base, ba, va);
-        noise_store(smem, o, base, bb, vb);
+        const uint4 va = aes_ctr_run_block(tab, rk, win, x0 + 32 * j);
+        const uint4 vb = aes_ctr_run_block(tab, rk, win, x0 + 32 * j + 32);
+        noise_store(smem, o, base, b0 + 32 * j, va);
+        noise_store(smem, o, base, b0 + 32 * j + 32, vb);
       }
     } else {
 #pragma unroll 1
-      for (uint32_t b = b0; b < nblk; b += 32) noise_store(smem, o, base, b, aes_ctr_block(tab, rk, o.domain, b));
+      for (uint32_t b = b0; b < nblk; b += 32)
+        noise_store(smem, o, base, b, aes_ctr_run_block(tab, rk, win, x0 + (b - b0)));
     }
   }
 }
@@ -1263,6 +1282,32 @@ __global__ void __launch_bounds__(512, 1) k_probe_aes(uint32_t iters, uint32_t *
   sink[gid] = acc;
 }
 
+// The windowed sequence of k_noise: per lane, NOISE_RUN / 32 blocks of one
+// run (window set up once), two at a time.
+__global__ void __launch_bounds__(512, 1) k_probe_aes_run(uint32_t iters, uint32_t *sink) {
+  extern __shared__ uint32_t sT[];
+  aes_fill_smem(sT, g_aes_T0);
+  __syncthreads();
+  const AesTab tab = aes_tab(sT);
+  const uint32_t gid = blockIdx.x * blockDim.x + threadIdx.x, lane = threadIdx.x & 31;
+  uint32_t key[4] = {gid, gid * 0x9E3779B9u, ~gid, gid ^ 0x5A5A5A5Au}, rk[44];
+  aes_key_expand(tab, key, rk);
+  uint32_t acc = 0;
+  const uint64_t base = (uint64_t)(gid >> 5) * iters * 32;
+  for (uint32_t b = 0; b < iters; b += NOISE_RUN / 32) {
+    const uint64_t first = base + 32 * (uint64_t)b;
+    const AesCtrRun win = aes_ctr_run(tab, rk, 3, first);
+    const uint32_t x0 = (uint32_t)(first & 255u) + lane;
+#pragma unroll
+    for (uint32_t j = 0; j < NOISE_RUN / 32; j += 2) {
+      const uint4 v = aes_ctr_run_block(tab, rk, win, x0 + 32 * j);
+      const uint4 w = aes_ctr_run_block(tab, rk, win, x0 + 32 * j + 32);
+      acc ^= v.x ^ v.y ^ v.z ^ v.w ^ w.x ^ w.y ^ w.z ^ w.w;
+    }
+  }
+  sink[gid] = acc;
+}
+
 __global__ void __launch_bounds__(32) k_probe_keccak_warp(uint32_t iters, uint32_t *sink) {
   const uint32_t lane = threadIdx.x, t = lane % 25;
   const KeccakWarpMap km = keccak_warp_map(lane);
@@ -1282,6 +1327,10 @@ int launch_probe(int kind, uint32_t ctas, uint32_t iters, uint32_t *sink, cudaSt
   }
   if (kind == 2) {
     k_probe_keccak_warp<<<ctas, 32, 0, st>>>(iters, sink);
+    return 0;
+  }
+  if (kind == 3) {
+    k_probe_aes_run<<<ctas, 512, AES_SMEM_BYTES, st>>>(iters, sink);
     return 0;
   }
   return -1;
@@ -1313,6 +1362,8 @@ cudaError_t lwe_kernel_smem_setup() {
   e = cudaFuncSetAttribute(k_sa_fused<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, fused_smem);
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_probe_aes, cudaFuncAttributeMaxDynamicSharedMemorySize, AES_SMEM_BYTES);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_probe_aes_run, cudaFuncAttributeMaxDynamicSharedMemorySize, AES_SMEM_BYTES);
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_pp_expand_A, cudaFuncAttributeMaxDynamicSharedMemorySize, AES_SMEM_BYTES);
   if (e != cudaSuccess) return e;

@@ -14,6 +14,7 @@ enum { NOISE_I8 = 0, NOISE_BF16 = 1 };
 // one warp generates one run (4 blocks per lane), so one item's round keys
 // serve a whole warp and the stores of a warp are contiguous.
 #define NOISE_RUN 128
+static_assert(256 % NOISE_RUN == 0, "a noise run lies inside one 256-block counter window");
 
 struct NoiseOut {
   void *base;            // item e writes at base + e * item_stride (bytes)

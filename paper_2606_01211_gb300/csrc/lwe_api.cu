@@ -1072,8 +1072,9 @@ int lwe_encaps_noalloc(const lwe_params *p, const uint8_t *pk, const uint16_t *A
 }
 
 int lwe_probe(int kind, uint32_t ctas, uint32_t iters, uint32_t *sink, void *stream) {
-  if (kind < LWE_PROBE_KECCAK || kind > LWE_PROBE_KECCAK_WARP || ctas == 0 || !sink ||
-      (kind == LWE_PROBE_AES && (iters & 1)))
+  if (kind < LWE_PROBE_KECCAK || kind > LWE_PROBE_AES_RUN || ctas == 0 || !sink ||
+      (kind == LWE_PROBE_AES && (iters & 1)) ||
+      (kind == LWE_PROBE_AES_RUN && (iters % (NOISE_RUN / 32))))
     return LWE_EINVAL;
   int rc = current_device_setup(nullptr, nullptr);
   if (rc) return rc;

@@ -354,7 +354,7 @@ def kernel_names():
     return [_lib.lwe_kernel_name(i).decode() for i in range(_lib.lwe_num_kernels())]
 
 
-PROBE_KECCAK, PROBE_AES, PROBE_KECCAK_WARP = 0, 1, 2
+PROBE_KECCAK, PROBE_AES, PROBE_KECCAK_WARP, PROBE_AES_RUN = 0, 1, 2, 3
 
 
 def probe(kind: int, ctas: int, iters: int, sink: torch.Tensor, stream=None):

@@ -101,8 +101,24 @@ def _aes_probe_word(gid, iters):
     return acc
 
 
+def _aes_run_probe_word(gid, iters):
+    """The windowed probe: thread gid's block i has counter index
+    32 (warp iters + i) + lane, so a warp's 32 lanes cover runs of
+    consecutive indices, as a warp of the noise kernel does."""
+    kw = [gid, (gid * 0x9E3779B9) & 0xFFFFFFFF, ~gid & 0xFFFFFFFF, gid ^ 0x5A5A5A5A]
+    key = b"".join(w.to_bytes(4, "little") for w in kw)
+    acc = 0
+    for i in range(iters):
+        b = 32 * ((gid >> 5) * iters + i) + (gid & 31)
+        blk = O.aes128_encrypt(key, (3).to_bytes(8, "big") + b.to_bytes(8, "big"))
+        for k in range(4):
+            acc ^= int.from_bytes(blk[4 * k:4 * k + 4], "little")
+    return acc
+
+
 @pytest.mark.gpu
-@pytest.mark.parametrize("kind,threads,iters", [(0, 256, 1), (0, 256, 3), (1, 512, 2), (1, 512, 6)])
+@pytest.mark.parametrize("kind,threads,iters", [(0, 256, 1), (0, 256, 3), (1, 512, 2), (1, 512, 6),
+                                                (3, 512, 8), (3, 512, 16)])
 def test_probe_matches_definition(kind, threads, iters):
     import torch
     from paper_2606_01211_gb300 import lwe
@@ -112,8 +128,9 @@ def test_probe_matches_definition(kind, threads, iters):
     lwe.probe(kind, ctas, iters, sink)
     torch.cuda.synchronize()
     got = sink.cpu().numpy().view(np.uint32)
-    ref = _keccak_probe_word if kind == lwe.PROBE_KECCAK else _aes_probe_word
-    for gid in (0, 1, 37, threads, ctas * threads - 1):
+    ref = {lwe.PROBE_KECCAK: _keccak_probe_word, lwe.PROBE_AES: _aes_probe_word,
+           lwe.PROBE_AES_RUN: _aes_run_probe_word}[kind]
+    for gid in (0, 1, 37, threads, 8 * 32 + 31, ctas * threads - 1):
         assert int(got[gid]) == ref(gid, iters), (kind, gid)
 
 
