@@ -252,8 +252,17 @@ __global__ void __launch_bounds__(512, 1) k_mul_as_fused(MulAsArgs a) {
   const int8_t *St = a.St + (size_t)e * a.st_stride;
   for (uint32_t i = blockIdx.x * 16 + warp; i < n; i += gridDim.x * 16) {
     int acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    // a lane's blocks step by 32 through the row: its 256-aligned counter
+    // window (the first two AES rounds, aes_ctr_run) changes every 8 blocks
+    AesCtrRun win;
+    uint64_t wcur = ~0ull;
     for (uint32_t jc = lane; jc < n / 8; jc += 32) {
-      uint4 x = aes_ctr_block(tab, rk, 0, (uint64_t)i * (n / 8) + jc);
+      const uint64_t b = (uint64_t)i * (n / 8) + jc;
+      if ((b >> 8) != wcur) {
+        wcur = b >> 8;
+        win = aes_ctr_run(tab, rk, 0, b);
+      }
+      uint4 x = aes_ctr_run_block(tab, rk, win, (uint32_t)b & 255u);
       x.x &= mm;
       x.y &= mm;
       x.z &= mm;

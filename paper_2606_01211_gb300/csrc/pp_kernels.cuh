@@ -33,8 +33,39 @@ LWE_DEV int32_t centre(uint32_t a, uint32_t q) {
 // A (Alg. 1 line 1) uniform mod q by rejection: entry (i, j) is 32-bit word
 // i n + j of the stream (seedA, domain 16 + t), accepted when below the
 // largest multiple of q under 2^32; a rejected word moves to the next try.
-// A thread takes one counter block = 4 consecutive entries of a row.
+// A counter block holds 4 consecutive entries of a row; a warp takes runs
+// of 128 blocks (4 per lane, two at a time) inside one 256-aligned counter
+// window of the first try's stream (aes_ctr_run).
 // ---------------------------------------------------------------------------
+// Entries of blocks ba (w[0..3]) and bb (w[4..7]): the rare rejected words
+// are replaced from the next tries (one AES block each), then all reduced
+// mod q; an entry rejected by every try is 0.
+LWE_DEV void pp_a_accept(const AesTab &tab, const uint32_t rk[44], uint64_t ba, uint64_t bb,
+                         uint32_t limit, ModQ M, uint32_t w[8]) {
+  uint32_t bad = 0;
+#pragma unroll
+  for (int c = 0; c < 8; c++) bad |= (w[c] >= limit ? 1u : 0u) << c;
+  uint32_t zero = 0;
+  while (bad) {  // probability < q / 2^32 per entry
+    const int c = __ffs(bad) - 1;
+    bad &= bad - 1;
+    bool ok = false;
+    for (uint32_t t = 1; !ok && t < PP_A_TRIES; t++) {
+      const uint4 u = aes_ctr_block(tab, rk, PP_A_DOMAIN + t, c < 4 ? ba : bb);
+      const uint32_t x = (c & 3) == 0 ? u.x : (c & 3) == 1 ? u.y : (c & 3) == 2 ? u.z : u.w;
+      if (x < limit) {
+#pragma unroll
+        for (int d = 0; d < 8; d++)
+          if (d == c) w[d] = x;
+        ok = true;
+      }
+    }
+    if (!ok) zero |= 1u << c;
+  }
+#pragma unroll
+  for (int c = 0; c < 8; c++) w[c] = (zero >> c) & 1u ? 0u : mod_u32(w[c], M);
+}
+
 __global__ void __launch_bounds__(512, 1) k_pp_expand_A(const uint8_t *__restrict__ seedA,
                                                      uint32_t n, ModQ M, uint32_t *__restrict__ A) {
   extern __shared__ uint32_t sT[];
@@ -49,24 +80,25 @@ __global__ void __launch_bounds__(512, 1) k_pp_expand_A(const uint8_t *__restric
   const uint32_t limit = (uint32_t)((0x100000000ull / M.q) * M.q);
   const uint64_t nblk = (uint64_t)n * n / 4;
   uint4 *out = reinterpret_cast<uint4 *>(A);
-  for (uint64_t b = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; b < nblk;
-       b += (uint64_t)gridDim.x * blockDim.x) {
-    const uint4 v = aes_ctr_block(tab, rk, PP_A_DOMAIN, b);
-    uint32_t w[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-    for (int c = 0; c < 4; c++) {
-      bool ok = w[c] < limit;
-      for (uint32_t t = 1; !ok && t < PP_A_TRIES; t++) {  // rare: probability < q / 2^32
-        const uint4 u = aes_ctr_block(tab, rk, PP_A_DOMAIN + t, b);
-        const uint32_t x = c == 0 ? u.x : c == 1 ? u.y : c == 2 ? u.z : u.w;
-        if (x < limit) {
-          w[c] = x;
-          ok = true;
-        }
-      }
-      w[c] = ok ? mod_u32(w[c], M) : 0u;
+  const uint32_t lane = threadIdx.x & 31;
+  const uint64_t nruns = (nblk + 127) / 128, nw = (uint64_t)gridDim.x * (blockDim.x >> 5);
+  for (uint64_t run = (uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); run < nruns;
+       run += nw) {
+    const uint64_t first = run * 128;
+    const AesCtrRun win = aes_ctr_run(tab, rk, PP_A_DOMAIN, first);
+    const uint32_t x0 = (uint32_t)(first & 255u) + lane;
+#pragma unroll 1
+    for (uint32_t j = 0; j < 4; j += 2) {
+      const uint64_t ba = first + lane + 32 * j, bb = ba + 32;
+      if (ba >= nblk) break;
+      const uint4 va = aes_ctr_run_block(tab, rk, win, x0 + 32 * j);
+      const uint4 vb = bb < nblk ? aes_ctr_run_block(tab, rk, win, x0 + 32 * j + 32)
+                                 : make_uint4(0, 0, 0, 0);
+      uint32_t w[8] = {va.x, va.y, va.z, va.w, vb.x, vb.y, vb.z, vb.w};
+      pp_a_accept(tab, rk, ba, bb, limit, M, w);
+      out[ba] = make_uint4(w[0], w[1], w[2], w[3]);
+      if (bb < nblk) out[bb] = make_uint4(w[4], w[5], w[6], w[7]);
     }
-    out[b] = make_uint4(w[0], w[1], w[2], w[3]);
   }
 }
 
