@@ -182,6 +182,36 @@ def test_decaps_of_many_tampered_bits_never_accepts():
     assert np.array_equal(host(K2), host(K))
 
 
+@pytest.mark.parametrize("path", [lwe.PATH_SKINNY, lwe.PATH_TENSOR])
+def test_decaps_batch_above_warp_hash_threshold_matches_oracle(path):
+    """Above the one-state-per-warp threshold (one item per SM) Decaps'
+    H(c) is the batched tree on the side stream: the implicit-rejection
+    keys H(z || H(c)) of tampered ciphertexts equal the oracle's, the
+    untouched ones decapsulate, and the serial schedule (side-stream work
+    on the caller's stream) gives the same keys."""
+    count = 200
+    ctx, p, po, pk_o, sk_o, A_o, cs, ct, K, K2, pk, sk, A = _kem_case(
+        "P640", count, path, True)
+    assert count > torch.cuda.get_device_properties(0).multi_processor_count
+    bad = ct.clone()
+    tampered = list(range(0, count, 7))
+    for i in tampered:
+        bad[i, (131 * i) % p.ct_bytes] ^= 2
+    Kb = torch.empty_like(K)
+    ctx.decaps(sk, bad, Kb, A=A)
+    Kb_h, bad_h, K_h = host(Kb), host(bad), host(K)
+    for i in (0, 7, 154, 196):
+        assert np.array_equal(Kb_h[i], O.decaps(po, sk_o, bad_h[i], A=A_o)), i
+    for i in range(count):
+        assert np.array_equal(Kb_h[i], K_h[i]) == (i not in tampered), i
+    assert np.array_equal(host(K2), K_h)
+    ctx.set_option(lwe.OPT_SERIAL, 1)
+    Ks = torch.empty_like(K)
+    ctx.decaps(sk, bad, Ks, A=A)
+    assert np.array_equal(host(Ks), Kb_h)
+    assert ctx.device_error() == 0
+
+
 # ------------------------------------------------------ standalone products --
 
 @pytest.mark.parametrize("n,logq", [(16, 16), (48, 15), (208, 16), (976, 16)])
