@@ -189,7 +189,6 @@ def keccak_perms(length: int, chunk: int = 1024) -> int:
 #    (three-input XORs / chi as LOP3, 64-bit rotations as funnel-shift pairs),
 #    64 ALU lanes per clock per SM  ->  152 * 2.07e9 * 64 / (190 * 24)
 #    = 4.42 G permutations/s
-AES_PEAK_GBS = 152 * 2.070e9 * 32 / 160 * 16 / 1e9
 AES_RUN_PEAK_GBS = 152 * 2.070e9 * 32 / (133 + 27 / 4) * 16 / 1e9
 KECCAK_PEAK_GPERMS = 152 * 2.070e9 * 64 / (190 * 24) / 1e9
 
@@ -538,14 +537,14 @@ def run_ours(args, rank, world, local_rank):
 def probe_peaks(torch, stream):
     """Practical peaks of the two integer-bound instruction sequences on
     this GPU: Keccak-f[1600] in registers (k_tree's permutation) and AES
-    counter blocks with the shared-memory round tables (k_noise's
-    generator), no memory traffic (lwe_probe).  Best of three launches."""
+    counter blocks with the shared-memory round tables, in runs whose first
+    two rounds are shared (k_noise's generator), no memory traffic
+    (lwe_probe).  Best of three launches."""
     from paper_2606_01211_gb300 import lwe
     sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
     out = {}
     for kind, ctas, threads, iters, scale, key in (
             (lwe.PROBE_KECCAK, 3 * sms, 256, 512, 1e9, "keccak_gperms"),
-            (lwe.PROBE_AES, sms, 512, 16384, 1e9 / 16, "aes_gbs"),
             (lwe.PROBE_AES_RUN, sms, 512, 16384, 1e9 / 16, "aes_run_gbs")):
         sink = torch.empty(ctas * 512, dtype=torch.int32, device="cuda")
         lwe.probe(kind, ctas, iters, sink, stream)
