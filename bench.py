@@ -52,7 +52,9 @@ def peaks():
 
 # --------------------------------------------------------------- clocks ---
 class ClockSampler:
-    """nvidia-smi clock / throttle sampling during the timed region."""
+    """nvidia-smi clock / throttle sampling during the timed region.  Each
+    sample carries nvidia-smi's timestamp, so that stop(t0, t1) keeps the
+    samples taken between two host wall-clock times (the timed region)."""
 
     def __init__(self, index: int, period_ms: int = 200):
         self.index = index
@@ -60,8 +62,10 @@ class ClockSampler:
         self.proc = None
         self.lines = []
 
-    def start(self):
-        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    def start(self, wait_first: bool = False):
+        """wait_first: return once the first sample has arrived, so that
+        sampling is live when the timed region begins (at most 5 s)."""
+        q = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
         try:
@@ -72,41 +76,76 @@ class ClockSampler:
             threading.Thread(target=self._read, daemon=True).start()
         except Exception:
             self.proc = None
+            return
+        t_end = time.time() + 5.0
+        while wait_first and not self.lines and time.time() < t_end and self.proc.poll() is None:
+            time.sleep(0.01)
 
     def _read(self):
         for line in self.proc.stdout:
             self.lines.append(line.strip())
 
-    def stop(self):
+    @staticmethod
+    def _when(stamp: str):
+        import datetime
+        for fmt in ("%Y/%m/%d %H:%M:%S.%f", "%Y/%m/%d %H:%M:%S"):
+            try:
+                return datetime.datetime.strptime(stamp, fmt).timestamp()
+            except ValueError:
+                pass
+        return None
+
+    def stop(self, t0: float | None = None, t1: float | None = None):
+        """Median SM clock, the maximum clock and the throttle reasons seen.
+        With t0, t1 (time.time() around the timed region) only the samples
+        inside it count; when the region is shorter than the sampling
+        period, the samples just before and after it stand in and
+        `in_region` says so."""
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
-        time.sleep(0.25)
+        time.sleep(max(0.25, 2 * self.period_ms / 1e3))
         self.proc.terminate()
         try:
             self.proc.wait(timeout=2)
         except Exception:
             self.proc.kill()
-        sm, smax, reasons, watts = [], None, set(), []
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        rows = []
         for ln in self.lines:
             f = [x.strip() for x in ln.split(",")]
-            if len(f) < 9:
-                continue
+            if len(f) >= 10:
+                rows.append((self._when(f[0]), f))
+        picked, in_region = rows, None
+        if t0 is not None and t1 is not None:
+            inside = [r for r in rows if r[0] is not None and t0 <= r[0] <= t1]
+            in_region = len(inside)
+            if inside:
+                picked = inside
+            else:  # the nearest sample on each side of a short region
+                before = [r for r in rows if r[0] is not None and r[0] < t0][-1:]
+                after = [r for r in rows if r[0] is not None and r[0] > t1][:1]
+                picked = before + after
+        sm, smax, reasons, watts = [], None, set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for _, f in picked:
             try:
-                sm.append(float(f[1]))
-                smax = float(f[2])
+                sm.append(float(f[2]))
+                smax = float(f[3])
             except ValueError:
                 continue
             try:
-                watts.append(float(f[3]))
+                watts.append(float(f[4]))
             except ValueError:
                 pass
-            for nm, v in zip(names, f[5:9]):
+            for nm, v in zip(names, f[6:10]):
                 if v.lower() == "active":
                     reasons.add(nm)
         self.watts = watts
-        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
-                "reasons": sorted(reasons), "samples": len(sm)}
+        out = {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+               "reasons": sorted(reasons), "samples": len(sm)}
+        if in_region is not None:
+            out["in_region"] = in_region
+            out["period_ms"] = self.period_ms
+        return out
 
 
 # ------------------------------------------------------------ reference ---
@@ -376,8 +415,9 @@ def run_ours(args, rank, world, local_rank):
         dist.barrier()
     torch.cuda.synchronize()
     launches0 = kem.ctx.launches()
-    clk = ClockSampler(local_rank)
-    clk.start()
+    clk = ClockSampler(local_rank, period_ms=50)
+    clk.start(wait_first=True)
+    t_region0 = time.time()
     evs = []
     for i in range(args.warmup, nsteps):
         flush.fill_(i)  # L2 flush, outside the timed events
@@ -388,7 +428,8 @@ def run_ours(args, rank, world, local_rank):
         b.record(stream)
         evs.append((a, b))
     torch.cuda.synchronize()
-    clocks = clk.stop()
+    t_region1 = time.time()
+    clocks = clk.stop(t_region0, t_region1)
     tot_ms = sum(a.elapsed_time(b) for a, b in evs)
     # kernels launched by the replays (the graph's nodes, counted at capture)
     launches = kem.launches_per_step * args.steps + (kem.ctx.launches() - launches0)
@@ -806,7 +847,7 @@ def large_n(lwe, torch, dev, batch: int = 1024):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-e2e", action="store_true")
