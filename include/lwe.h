@@ -302,11 +302,13 @@ int lwe_selftest_bounded_wait(lwe_ctx *ctx, uint32_t limit_us, void *stream);
  *     permutation of k_tree).  Work: ctas * 256 * iters permutations.
  *   LWE_PROBE_AES: `ctas` CTAs of 512 threads with the AES round tables in
  *     shared memory; each thread encrypts `iters` (even) counter blocks, two
- *     at a time (the generator of A).  Work: ctas * 512 * iters blocks.
+ *     at a time, every round in full (the generator of the kernels whose
+ *     blocks do not run along one counter window, e.g. S' A with A
+ *     regenerated).  Work: ctas * 512 * iters blocks.
  *   LWE_PROBE_AES_RUN: as LWE_PROBE_AES with the blocks of a warp taken
  *     four per lane from one 128-block run of counter indices, whose first
- *     two rounds are shared (the generator of k_noise); iters a multiple
- *     of 4.
+ *     two rounds are shared (the generator of the noise and of A); iters a
+ *     multiple of 4.
  *   LWE_PROBE_KECCAK_WARP: `ctas` CTAs of one warp; each warp applies
  *     Keccak-f[1600] `iters` times to one state spread over its lanes (the
  *     permutation of k_tree_warp).  Work: ctas * iters permutations.

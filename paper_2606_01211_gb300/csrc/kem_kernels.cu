@@ -29,7 +29,8 @@
 __device__ uint32_t g_aes_T0[256];
 
 // ---------------------------------------------------------------------------
-// A expansion: thread per 16-byte block, grid-stride; one key per grid.y.
+// A expansion: a warp per run of 128 counter blocks (16-byte blocks of A),
+// grid-stride over the runs; one key per grid.y.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(512, 1) k_expand_A(const uint8_t *__restrict__ seeds,
                                                   uint32_t seed_stride, uint32_t n,
@@ -1283,7 +1284,7 @@ __global__ void __launch_bounds__(512, 1) k_probe_aes(uint32_t iters, uint32_t *
   aes_key_expand(tab, key, rk);
   uint32_t acc = 0;
   const uint64_t base = (uint64_t)gid * iters;
-  for (uint32_t b = 0; b < iters; b += 2) {  // two blocks in flight, as in k_noise
+  for (uint32_t b = 0; b < iters; b += 2) {  // two blocks in flight, the plain sequence
     const uint4 v = aes_ctr_block(tab, rk, 3, base + b);
     const uint4 w = aes_ctr_block(tab, rk, 3, base + b + 1);
     acc ^= v.x ^ v.y ^ v.z ^ v.w ^ w.x ^ w.y ^ w.z ^ w.w;
