@@ -253,7 +253,9 @@ def algorithmic_bytes(p, count):
 # instruction-throughput bound measured against lwe_probe, not HBM or tensor
 LIMITER = {
     "k_noise": "shared-memory pipe: AES round-table lookups plus the sampler's table",
-    "k_tree": "integer ALU pipe: Keccak-f XORs, rotations and chi",
+    "k_tree": "integer ALU pipe: Keccak-f XORs, rotations and chi; at 4096 x P976 an SM's "
+              "13.5 leaf warps split 4/4/3/3 over its sub-partitions, then one warp hashes "
+              "the roots: 37 warp-permutations on the critical path against 29 of work",
     "k_gemm_tc": "tensor pipe (bf16 tcgen05, CTA pairs)",
 }
 
