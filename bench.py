@@ -149,15 +149,18 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------ reference ---
-def cpu_oracle_rate(target_s: float = 12.0, max_pairs: int | None = None):
-    """The plain oracle (as it stands) on all host cores over a bounded
-    sample of the workload: Encaps + Decaps pairs per second."""
+def cpu_oracle_rate(target_s: float = 12.0, max_pairs: int | None = None,
+                    single_thread: bool = False):
+    """The plain oracle (as it stands) on all host cores (or on one) over a
+    bounded sample of the workload: Encaps + Decaps pairs per second."""
     from oracle import oracle as O
     cfg = PRESETS[PRESET]
     po = O.Params(**cfg)
     pk, sk, A = O.keygen(po, bytes(master_seeds(1, seed=1)[0]), want_A=True)
     threads = len(os.sched_getaffinity(0))
     threads = min(threads, O.max_threads()) if O.max_threads() > 1 else 1
+    if single_thread:
+        threads = 1
     n = max(threads, 8)
     elapsed, done = 0.0, 0
     while True:
@@ -205,6 +208,72 @@ def run_reference(args, rank, world):
     }
     print(json.dumps(line))
     return 0
+
+
+def cpu_large_n(threads: int, batch: int = 1024):
+    """The oracle at n = 16384 and 32768 (the sizes the paper calls
+    impractical on the CPU, Sec. 4.3): one Encaps + Decaps pair per host
+    thread, timed once on all threads, with A given.  pk, sk and A are
+    random bytes of the right sizes: the oracle's work (S' A, S' B, the
+    noise, the hashes, the re-encryption and compare) does not depend on
+    their values, and expanding a 2 GiB A with its byte-wise AES would
+    dominate the sample.  The batch of `batch` Encaps + Decaps is then
+    extrapolated linearly from that sample (labelled)."""
+    from oracle import oracle as O
+    out = {}
+    r = np.random.default_rng(12)
+    for name in ("P16384", "P32768"):
+        po = O.Params(**PRESETS[name])
+        n = po.n
+        pkb, skb, _, _ = O.sizes(po)
+        A = r.integers(0, 1 << 16, size=(n, n), dtype=np.uint16)
+        pk = r.integers(0, 256, size=pkb, dtype=np.uint8)
+        sk = r.integers(0, 256, size=skb, dtype=np.uint8)
+        sk[: 8 * n] = r.integers(-2, 3, size=8 * n, dtype=np.int8).view(np.uint8)
+        sk[8 * n + 64:] = pk
+        cs = coins(threads, seed=77)
+        t0 = time.perf_counter()
+        ct, _ = O.encaps_batch(po, pk, cs, A=A, nthreads=threads)
+        O.decaps_batch(po, sk, ct, A=A, nthreads=threads)
+        el = time.perf_counter() - t0
+        rate = threads / el
+        out[name] = {"pairs_per_s": rate, "sample_pairs": threads, "sample_s": el,
+                     "batch_%d_s_extrapolated" % batch: batch / rate}
+        del A
+    out["cores"] = threads
+    out["kind"] = "oracle, timed sample; batch time extrapolated linearly in the batch size"
+    return out
+
+
+def per_request_rate(kem, lwe, torch, stream, pairs: int = 2048):
+    """The plain per-request GPU path: one P976 Encaps and then its Decaps
+    per call (count = 1, CUDA-core kernels, the key bound as in the batched
+    step), back to back on one stream, host wall-clock from the first launch
+    to the final synchronisation; the coins are the batched step's, and the
+    keys are checked identical to the batched step's."""
+    p = kem.params
+    ctx = lwe.Ctx(p, max_batch=1, device=kem.dev.index)
+    ctx.set_path(lwe.PATH_SKINNY)
+    ctx.bind_key(kem.pk, kem.sk, kem.A)
+    pairs = min(pairs, kem.count)
+    ct = ctx.empty_ct(pairs)
+    K = torch.empty((pairs, 32), dtype=torch.uint8, device=kem.dev)
+    K2 = torch.empty_like(K)
+
+    def run(m):
+        for i in range(m):
+            ctx.encaps(kem.pk, kem.coins[i:i + 1], ct[i:i + 1], K[i:i + 1], A=kem.A)
+            ctx.decaps(kem.sk, ct[i:i + 1], K2[i:i + 1], A=kem.A)
+
+    run(16)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    run(pairs)
+    torch.cuda.synchronize()
+    el = time.perf_counter() - t0
+    same = torch.equal(K, kem.K[:pairs]) and torch.equal(K2, K) and torch.equal(ct, kem.ct[:pairs])
+    ctx.close()
+    return pairs / el, bool(same), pairs
 
 
 # ----------------------------------------------------------------- ours ---
@@ -509,8 +578,9 @@ def run_ours(args, rank, world, local_rank):
     extras = world == 1
     energy = energy_measure(kem, torch, stream, local_rank) if extras and not args.no_energy else None
 
-    # the same step with direct launches (no graph), and on the plain
-    # per-request path (CUDA cores, one item per row of CTAs)
+    # the same 4096-item step with direct launches (no graph) on the
+    # CUDA-core product instead of the tensor cores (still one batched call
+    # per operation)
     def direct_rate(path):
         kem.ctx.set_path(path)
         for i in range(2):
@@ -529,7 +599,16 @@ def run_ours(args, rank, world, local_rank):
         kem.ctx.set_path(lwe.PATH_TENSOR)
         return COUNT / (statistics.median(ts) / 1e3)
 
-    plain = direct_rate(lwe.PATH_SKINNY) if extras and not args.no_plain else None
+    cuda_core = direct_rate(lwe.PATH_SKINNY) if extras and not args.no_plain else None
+    # the last graph replay left the batched results of cs_all[-1] in place
+    per_req = None
+    if extras and not args.no_plain:
+        kem.replay(cs_all[nsteps - 1])
+        torch.cuda.synchronize()
+        rate, same, m = per_request_rate(kem, lwe, torch, stream)
+        per_req = {"value": rate, "unit": UNIT, "pairs": m, "identical_to_batched": same,
+                   "how": "one Encaps and its Decaps per call (count = 1, CUDA-core path), "
+                          "back to back on one stream, host wall-clock"}
     kem.close()
 
     served = serve_measure(torch) if extras and not args.no_serve else None
@@ -541,8 +620,12 @@ def run_ours(args, rank, world, local_rank):
     cpu = None
     if extras and not args.no_cpu:
         rate, threads, pairs, el = cpu_oracle_rate(target_s=args.cpu_s)
+        rate1, _, pairs1, el1 = cpu_oracle_rate(target_s=args.cpu_s / 3, single_thread=True)
         cpu = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
-               "sample": "%d Encaps+Decaps pairs of the P976 workload (A given), %.1f s" % (pairs, el)}
+               "sample": "%d Encaps+Decaps pairs of the P976 workload (A given), %.1f s" % (pairs, el),
+               "single_thread": {"value": rate1, "unit": UNIT, "cores": 1,
+                                 "sample": "%d pairs, %.1f s" % (pairs1, el1)},
+               "large_n": None if args.no_large else cpu_large_n(threads)}
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -559,8 +642,10 @@ def run_ours(args, rank, world, local_rank):
         "e2e": e2e,
         "clocks": clocks,
         "serial_timed_value": serial_value,
-        "plain_path_value": plain,
-        "batched_vs_plain": (value / world / plain) if plain else None,
+        "per_request": per_req,
+        "batched_vs_per_request": (value / world / per_req["value"]) if per_req else None,
+        "cuda_core_batched_value": cuda_core,
+        "batched_vs_cuda_core_batched": (value / world / cuda_core) if cuda_core else None,
         "kernels_ms_per_step": {k: v[1] / args.steps for k, v in stats.items()},
         "autotune": {"gemm_pair": tuned["gemm_pair"], "gemm_bn": tuned["gemm_bn"],
                      "tensor_min": tuned["tensor_min"]},
@@ -658,7 +743,8 @@ def serve_measure(torch, rates=(1e3, 1e4, 1e5, 1e6), requests: int = 20000):
             st = eng.run()
             row["plain" if plain else "batched"] = {k: st[k] for k in
                                                    ("ops_per_s", "p50_ms", "p99_ms", "mean_batch",
-                                                    "requests")}
+                                                    "requests", "gpu_busy", "tensor_batches",
+                                                    "host_launch_s", "makespan_s")}
         row["served_vs_plain"] = row["batched"]["ops_per_s"] / row["plain"]["ops_per_s"]
         sweep.append(row)
     out = dict(next(r for r in sweep if r["rate"] == 1e5)) if 1e5 in rates else dict(sweep[-1])

@@ -60,7 +60,8 @@ extern "C" {
 #define LWE_ECUDA (-3)        /* a CUDA runtime call or launch failed       */
 #define LWE_ETIMEOUT (-4)     /* a bounded device wait ran out              */
 #define LWE_EUNSUPPORTED (-5) /* not supported on this device               */
-#define LWE_ECAPACITY (-6)    /* count exceeds the context's max_batch      */
+#define LWE_ECAPACITY (-6)    /* count exceeds the context's max_batch, or
+                                 (lwe_encaps_noalloc) the built-in scratch  */
 
 /* ---- parameters (Sec. 2.2; the values of the presets are the workloads'
  *      parameter sets, each with nbar = mbar = 8) -------------------------- */
@@ -218,6 +219,29 @@ int lwe_decaps_multi(lwe_ctx *ctx, const uint8_t *const *sk_ptrs,
                      const uint16_t *const *A_ptrs, const uint8_t *ct,
                      uint32_t count, uint8_t *K, void *stream);
 
+/* Per-key precomputation for repeated calls against one key pair.  Encaps
+ * (Alg. 4) needs H(pk) for every call, and the tensor path multiplies by the
+ * limb split of [A | B]; both depend on the key only.  Binding a key makes
+ * them once, on `stream`; later lwe_encaps calls whose (pk, A) pointers
+ * equal the bound (pk, A), and lwe_decaps calls whose (sk, A) equal the
+ * bound (sk, A), reuse them instead of recomputing.  Results are identical
+ * with and without a binding.
+ *   pk  [pk_bytes] nullable;  sk [sk_bytes] nullable (at least one given;
+ *       when both are given they must be the two halves of one key pair);
+ *   A   [n][n] uint16 nullable, as in lwe_encaps.
+ * pk = sk = NULL unbinds.  The binding refers to the BUFFERS: while a key is
+ * bound their contents must not change (bind again after rewriting them).
+ * Other calls on the context that need the limb workspace (a tensor-path
+ * call for another key, lwe_matmul_modq) overwrite it; the next bound call
+ * then makes the limbs again, on its own.  A CUDA graph captured from
+ * bound calls reads the limbs the binding left in the workspace: do not let
+ * another call overwrite them while such a graph is replayed.  Order later
+ * calls after this call's work (same stream, or synchronise).  Allocates
+ * nothing.
+ * LWE_EINVAL for a NULL context or a misaligned pointer. */
+int lwe_ctx_bind_key(lwe_ctx *ctx, const uint8_t *pk, const uint8_t *sk,
+                     const uint16_t *A, void *stream);
+
 /* ---- standalone hot-path kernels --------------------------------------- */
 
 /* sample(seedA) of Alg. 1: A[i][j..j+7] = the eight little-endian 16-bit
@@ -293,6 +317,14 @@ uint64_t lwe_ctx_launches(const lwe_ctx *ctx);
  * error word and the kernel returns normally -- nothing faults or hangs, and
  * the next lwe_ctx_device_error() returns LWE_ETIMEOUT (and clears it). */
 int lwe_selftest_bounded_wait(lwe_ctx *ctx, uint32_t limit_us, void *stream);
+
+/* The noise sampler's word table exactly as the noise kernel builds and
+ * reads it (Sec. 2.2, Tab. 1: the rounded-Gaussian inverse sampling of
+ * lwe_cdf_table): out[w] = e for every 16-bit word w, 65536 int8 values
+ * (device).  A check of the device-side table against the sampler's
+ * definition; one CTA, asynchronous on `stream`.  LWE_EINVAL for invalid
+ * parameters or a NULL out. */
+int lwe_noise_table(const lwe_params *p, int8_t *out, void *stream);
 
 /* Measurement probes (no counterpart in the paper): the instruction
  * sequences of the two integer-bound kernels without memory traffic, to

@@ -5,8 +5,10 @@ BatchedKem holds one key pair, its expanded A and static input/output
 buffers for a fixed batch; its step (Encaps of the batch followed by the
 Decaps of the produced ciphertexts) is captured once into a CUDA graph and
 replayed, so a step costs one graph launch on the host instead of ~30
-kernel launches.  Batching many encapsulations against one key is what
-turns S' A into one tensor-core contraction (the paper batches the 256
+kernel launches.  The key is bound to the context (lwe_ctx_bind_key), so its
+H(pk) and the limb split of [A | B] are made once, not in every step.
+Batching many encapsulations against one key is what turns S' A into one
+tensor-core contraction (the paper batches the 256
 per-bit encryptions of one Encaps into one launch, Sec. 3.2).
 
 autotune() times the candidate GEMM kernels (CTA pairs on 256 x 128 tiles,
@@ -31,7 +33,7 @@ CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_autotune.json
 class BatchedKem:
     def __init__(self, name: str = "P976", count: int = 4096, seed: int = 1, device=None,
                  path: int = lwe.PATH_TENSOR, gemm_bn: int | None = None,
-                 gemm_pair: int | None = None):
+                 gemm_pair: int | None = None, bind: bool = True):
         self.dev = torch.device("cuda", torch.cuda.current_device() if device is None else device)
         self.params = p = lwe.Params(**PRESETS[name])
         self.count = count
@@ -45,6 +47,8 @@ class BatchedKem:
         self.A = torch.empty((p.n, p.n), dtype=torch.int16, device=self.dev)
         self.ctx.keygen(torch.from_numpy(master_seeds(1, seed=seed)).to(self.dev), self.pk, self.sk,
                         A_out=self.A)
+        if bind:  # H(pk) and the limbs of [A | B], made once for the key
+            self.ctx.bind_key(self.pk, self.sk, self.A)
         self.coins = torch.from_numpy(make_coins(count, seed=seed)).to(self.dev)
         self.ct = self.ctx.empty_ct(count)
         self.K = torch.empty((count, 32), dtype=torch.uint8, device=self.dev)

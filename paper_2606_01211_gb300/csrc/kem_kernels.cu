@@ -207,6 +207,17 @@ __global__ void __launch_bounds__(512, 1) k_noise(NoiseArgs a) {
              (uint64_t)gridDim.x * (blockDim.x >> 5));
 }
 
+// The sampler table exactly as k_noise builds and reads it, for all 65536
+// words: out[w] = the sample of word w (a check of the table against the
+// definition of the sampler; one CTA).
+__global__ void __launch_bounds__(512, 1) k_noise_table(NoiseArgs a, int8_t *out) {
+  extern __shared__ uint32_t sT[];
+  noise_fill_table(sT + NOISE_TAB_OFF / 4, a);
+  __syncthreads();
+  const char *smem = reinterpret_cast<const char *>(sT);
+  for (uint32_t w = threadIdx.x; w < 65536; w += blockDim.x) out[w] = (int8_t)tab_sample(smem, w);
+}
+
 // ---------------------------------------------------------------------------
 // Rows times S^T: out[r][l] = sum_j X[r][j] * St[l][j] for l < 8.
 // A warp owns a row; a lane takes 8-element chunks (16 bytes of X, one AES
@@ -1362,7 +1373,9 @@ cudaError_t lwe_kernel_smem_setup() {
   e = cudaFuncSetAttribute(k_expand_A, cudaFuncAttributeMaxDynamicSharedMemorySize, AES_SMEM_BYTES);
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_noise, cudaFuncAttributeMaxDynamicSharedMemorySize, NOISE_SMEM_BYTES);
-
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_noise_table, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           NOISE_SMEM_BYTES);
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_mul_as_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, AES_SMEM_BYTES);
   if (e != cudaSuccess) return e;
@@ -1389,6 +1402,10 @@ void launch_expand_A(const uint8_t *seeds, uint32_t seed_stride, uint32_t count,
   const int gx = grid_for(nblk, 512 * 4, num_sms);
   launch_k(k_expand_A, dim3(gx, count), 512, AES_SMEM_BYTES, st, seeds, seed_stride, n, logq, A,
            a_stride);
+}
+
+void launch_noise_table(const NoiseArgs &a, int8_t *out, cudaStream_t st) {
+  launch_k(k_noise_table, 1, 512, NOISE_SMEM_BYTES, st, a, out);
 }
 
 void launch_noise(const NoiseArgs &a, int num_sms, cudaStream_t st) {

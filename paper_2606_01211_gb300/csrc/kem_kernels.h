@@ -160,6 +160,7 @@ cudaError_t lwe_kernel_smem_setup();
 void launch_expand_A(const uint8_t *seeds, uint32_t seed_stride, uint32_t count, uint32_t n,
                      uint32_t logq, uint16_t *A, uint64_t a_stride, int num_sms, cudaStream_t st);
 void launch_noise(const NoiseArgs &a, int num_sms, cudaStream_t st);
+void launch_noise_table(const NoiseArgs &a, int8_t *out, cudaStream_t st);
 void launch_mul_as(const MulAsArgs &a, uint32_t count, bool fused, int num_sms, cudaStream_t st);
 void launch_decrypt(const DecryptArgs &a, uint32_t count, cudaStream_t st);
 void launch_mul_sa(const MulSaArgs &a, uint32_t items, bool fused, bool cmp, int num_sms,

@@ -181,6 +181,13 @@ struct lwe_ctx {
   uint16_t *partial = nullptr; // K-split running sums, [8 max_batch][n + 8]
   uint32_t kchunk = 0;         // exact K per GEMM pass
   bool has_tensor = false;
+  // the key bound by lwe_ctx_bind_key: its buffers, H(pk) (bpkh) and
+  // whether `limbs` still holds the limb split of its [A | B]
+  bool bound = false;
+  const uint8_t *bound_pk = nullptr, *bound_sk = nullptr;
+  const uint16_t *bound_A = nullptr;
+  uint8_t *bpkh = nullptr;
+  bool limbs_bound = false;
   // side stream for work independent of the re-encryption (Decaps' H(c))
   cudaStream_t side = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_limbs = nullptr;
@@ -342,7 +349,9 @@ bool use_tensor(const lwe_ctx *c, uint32_t count, const ItemKeys *ik) {
 
 // The GEMM's B operand: limbs of the columns of [A | B] (A stored, or
 // regenerated from seedA = pk[0:16]).  Depends on the key only.
-void launch_limbs(lwe_ctx *c, const uint8_t *pk, const uint16_t *A, cudaStream_t st) {
+void launch_limbs(lwe_ctx *c, const uint8_t *pk, const uint16_t *A, cudaStream_t st,
+                  bool for_bound = false) {
+  c->limbs_bound = for_bound;
   GemmLimbArgs la;
   la.A = A;
   la.seedA = pk;
@@ -353,9 +362,14 @@ void launch_limbs(lwe_ctx *c, const uint8_t *pk, const uint16_t *A, cudaStream_t
   LAUNCH(c, KID_LIMBS, st, launch_gemm_limbs(la, c->num_sms, st));
 }
 
+// Where the tensor path's limbs come from: made here on the main stream,
+// made by the caller on the side stream (ev_limbs), or already in place (the
+// bound key's).
+enum LimbsFrom { LIMBS_HERE = 0, LIMBS_SIDE = 1, LIMBS_READY = 2 };
+
 int run_encrypt(lwe_ctx *c, const uint8_t *pk, const uint16_t *A, uint32_t count, uint8_t *ct,
                 bool cmp, cudaStream_t st, const ItemKeys *ik = nullptr,
-                bool limbs_on_side = false) {
+                int limbs_from = LIMBS_HERE) {
   const uint32_t n = c->p.n;
   const bool tensor = use_tensor(c, count, ik);
 
@@ -371,9 +385,9 @@ int run_encrypt(lwe_ctx *c, const uint8_t *pk, const uint16_t *A, uint32_t count
   LAUNCH(c, KID_NOISE, st, launch_noise(na, c->num_sms, st));
 
   if (tensor) {
-    if (limbs_on_side)  // made on the side stream by the caller
+    if (limbs_from == LIMBS_SIDE)  // made on the side stream by the caller
       CUDA_TRY(cudaStreamWaitEvent(st, c->ev_limbs, 0));
-    else
+    else if (limbs_from == LIMBS_HERE)
       launch_limbs(c, pk, A, st);
     GemmSaArgs ga;
     memset(&ga, 0, sizeof ga);
@@ -513,6 +527,7 @@ std::mutex g_noalloc_mu;
 uint8_t *g_noalloc_addr[128];
 
 int noalloc_scratch(int dev, uint8_t **out) {
+  if (dev < 0 || dev >= 128) return LWE_EUNSUPPORTED;
   std::lock_guard<std::mutex> lk(g_noalloc_mu);
   if (!g_noalloc_addr[dev]) {
     void *ptr = nullptr;
@@ -592,6 +607,7 @@ int lwe_ctx_create(const lwe_params *p, uint32_t max_batch, int device, lwe_ctx 
   };
   const size_t o_seeds = carve(32 * Bm), o_mu = carve(32 * Bm), o_kp = carve(32 * Bm);
   const size_t o_flags = carve(4 * Bm), o_err = carve(16), o_pkh = carve(32);
+  const size_t o_bpkh = carve(32);
   const size_t o_rk = carve(176 * Bm), o_pkhs = carve(32 * Bm);
   const size_t o_hc = carve(32 * Bm);
   const size_t o_sp8 = carve(8 * n * Bm), o_ep8 = carve(8 * n * Bm), o_epp = carve(64 * Bm);
@@ -618,6 +634,7 @@ int lwe_ctx_create(const lwe_params *p, uint32_t max_batch, int device, lwe_ctx 
   c->rk = reinterpret_cast<uint32_t *>(c->ws + o_rk);
   c->pkhs = c->ws + o_pkhs;
   c->pkh = c->ws + o_pkh;
+  c->bpkh = c->ws + o_bpkh;
   c->hc = c->ws + o_hc;
   c->sp8 = reinterpret_cast<int8_t *>(c->ws + o_sp8);
   c->ep8 = reinterpret_cast<int8_t *>(c->ws + o_ep8);
@@ -786,21 +803,32 @@ int lwe_encaps(lwe_ctx *c, const uint8_t *pk, const uint16_t *A, const uint8_t *
   const lwe_params &p = c->p;
   const size_t pkb = pk_bytes(p), ctb = ct_bytes(p);
 
-  // tensor path: the limbs of [A | B] are made on the side stream while
-  // the main stream hashes pk (one message: a latency-bound launch)
-  const bool side = use_tensor(c, count, nullptr);
-  if (side) {
+  // The bound key's H(pk) and limbs are made once, at lwe_ctx_bind_key.
+  // Otherwise, on the tensor path, the limbs of [A | B] are made on the side
+  // stream while the main stream hashes pk (one message: a latency-bound
+  // launch).
+  const bool bound = c->bound && pk == c->bound_pk && A == c->bound_A;
+  const bool tensor = use_tensor(c, count, nullptr);
+  int limbs_from = LIMBS_HERE;
+  if (tensor && bound && c->limbs_bound) {
+    limbs_from = LIMBS_READY;
+  } else if (tensor) {
     cudaStream_t ss = side_stream(c, st);
     CUDA_TRY(cudaEventRecord(c->ev_fork, st));
     CUDA_TRY(cudaStreamWaitEvent(ss, c->ev_fork, 0));
-    launch_limbs(c, pk, A, ss);
+    launch_limbs(c, pk, A, ss, bound);
     CUDA_TRY(cudaEventRecord(c->ev_limbs, ss));
+    limbs_from = LIMBS_SIDE;
   }
-  rc = hash_tree(c, pk, pkb, (uint32_t)pkb, 1, TREE_DIGEST, c->pkh, 32, nullptr, 0, st);
-  if (rc) return rc;
-  DeriveArgs da = derive_args(c, coins, c->pkh, count);
+  const uint8_t *pkh = c->bpkh;
+  if (!bound) {
+    rc = hash_tree(c, pk, pkb, (uint32_t)pkb, 1, TREE_DIGEST, c->pkh, 32, nullptr, 0, st);
+    if (rc) return rc;
+    pkh = c->pkh;
+  }
+  DeriveArgs da = derive_args(c, coins, pkh, count);
   LAUNCH(c, KID_DERIVE, st, launch_derive(da, warp_hash_max(c), st));
-  rc = run_encrypt(c, pk, A, count, ct, false, st, nullptr, side);
+  rc = run_encrypt(c, pk, A, count, ct, false, st, nullptr, limbs_from);
   if (rc) return rc;
   return hash_tree(c, ct, ctb, (uint32_t)ctb, count, TREE_ENC_KEY, K, 32, nullptr, 0, st);
 }
@@ -830,10 +858,15 @@ int lwe_decaps(lwe_ctx *c, const uint8_t *sk, const uint16_t *A, const uint8_t *
   cudaStream_t ss = side_stream(c, st);
   CUDA_TRY(cudaEventRecord(c->ev_fork, st));
   CUDA_TRY(cudaStreamWaitEvent(ss, c->ev_fork, 0));
-  const bool side = use_tensor(c, count, nullptr);
-  if (side) {
-    launch_limbs(c, pk, A, ss);
+  const bool bound = c->bound && sk == c->bound_sk && A == c->bound_A;
+  const bool tensor = use_tensor(c, count, nullptr);
+  int limbs_from = LIMBS_HERE;
+  if (tensor && bound && c->limbs_bound) {
+    limbs_from = LIMBS_READY;
+  } else if (tensor) {
+    launch_limbs(c, pk, A, ss, bound);
     CUDA_TRY(cudaEventRecord(c->ev_limbs, ss));
+    limbs_from = LIMBS_SIDE;
   }
   tree_hash(c, ct, ctb, (uint32_t)ctb, count, TREE_DIGEST, c->hc, 32, nullptr, 0, ss);
   CUDA_TRY(cudaEventRecord(c->ev_join, ss));
@@ -841,7 +874,7 @@ int lwe_decaps(lwe_ctx *c, const uint8_t *sk, const uint16_t *A, const uint8_t *
   LAUNCH(c, KID_DECRYPT, st, launch_decrypt(dca, count, st));
   DeriveArgs da = derive_args(c, nullptr, pkh, count);
   LAUNCH(c, KID_DERIVE, st, launch_derive(da, warp_hash_max(c), st));
-  rc = run_encrypt(c, pk, A, count, const_cast<uint8_t *>(ct), true, st, nullptr, side);
+  rc = run_encrypt(c, pk, A, count, const_cast<uint8_t *>(ct), true, st, nullptr, limbs_from);
   if (rc) return rc;
   CUDA_TRY(cudaStreamWaitEvent(st, c->ev_join, 0));
   final_key(c, z, nullptr, 0, count, K, st);
@@ -919,6 +952,38 @@ int lwe_decaps_multi(lwe_ctx *c, const uint8_t *const *sk_ptrs, const uint16_t *
   return check_launch();
 }
 
+int lwe_ctx_bind_key(lwe_ctx *c, const uint8_t *pk, const uint8_t *sk, const uint16_t *A,
+                     void *stream) {
+  if (!c) return LWE_EINVAL;
+  if (!pk && !sk) {
+    c->bound = false;
+    c->bound_pk = c->bound_sk = nullptr;
+    c->bound_A = nullptr;
+    return LWE_OK;
+  }
+  if ((pk && !aligned16(pk)) || (sk && !aligned16(sk)) || (A && !aligned16(A))) return LWE_EINVAL;
+  int rc = set_device_of(c);
+  if (rc) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  const lwe_params &p = c->p;
+  const size_t pkb = pk_bytes(p);
+  c->bound = false;
+  // pk of the pair: the given one, else the copy inside sk
+  const uint8_t *key_pk = pk ? pk : sk + 8 * (size_t)p.n + 64;
+  rc = hash_tree(c, key_pk, pkb, (uint32_t)pkb, 1, TREE_DIGEST, c->bpkh, 32, nullptr, 0, st);
+  if (rc) return rc;
+  if (c->has_tensor) {
+    launch_limbs(c, key_pk, A, st, true);
+    rc = check_launch();
+    if (rc) return rc;
+  }
+  c->bound = true;
+  c->bound_pk = pk;
+  c->bound_sk = sk;
+  c->bound_A = A;
+  return LWE_OK;
+}
+
 int lwe_expand_A(const uint8_t *seedA, uint32_t n, uint32_t logq, uint16_t *A_out,
                  void *stream) {
   if (!seedA || !A_out || !aligned16(A_out) || n < 16 || n > 65536 || (n % 16) || logq < 1 ||
@@ -973,6 +1038,7 @@ int lwe_matmul_modq(lwe_ctx *c, int side, const uint16_t *A, const uint8_t *seed
     la.n = n;
     la.logq = logq;
     la.limbs = c->limbs;
+    c->limbs_bound = false;  // the bound key's limbs are overwritten
     LAUNCH(c, KID_LIMBS, st, launch_gemm_limbs(la, c->num_sms, st));
     LAUNCH(c, KID_LIMBS, st, launch_s_to_bf16(S, (uint64_t)k * n, c->spbf, c->num_sms, st));
     GemmSaArgs ga;
@@ -1071,6 +1137,19 @@ int lwe_encaps_noalloc(const lwe_params *p, const uint8_t *pk, const uint16_t *A
   return hash_tree(&c, ct, ctb, (uint32_t)ctb, count, TREE_ENC_KEY, K, 32, nullptr, 0, st);
 }
 
+int lwe_noise_table(const lwe_params *p, int8_t *out, void *stream) {
+  if (params_check(p) != LWE_OK || !out) return LWE_EINVAL;
+  int rc = current_device_setup(nullptr, nullptr);
+  if (rc) return rc;
+  NoiseArgs a;
+  memset(&a, 0, sizeof a);
+  uint16_t T[16];
+  cdf_table(p->sigma, p->clip, T);
+  for (int i = 0; i < 16; i++) a.T[i] = T[i];
+  launch_noise_table(a, out, (cudaStream_t)stream);
+  return check_launch();
+}
+
 int lwe_probe(int kind, uint32_t ctas, uint32_t iters, uint32_t *sink, void *stream) {
   if (kind < LWE_PROBE_KECCAK || kind > LWE_PROBE_AES_RUN || ctas == 0 || !sink ||
       (kind == LWE_PROBE_AES && (iters & 1)) ||
@@ -1098,7 +1177,8 @@ const char *lwe_strerror(int code) {
     case LWE_ECUDA: return "CUDA error";
     case LWE_ETIMEOUT: return "device wait timed out";
     case LWE_EUNSUPPORTED: return "unsupported device or configuration";
-    case LWE_ECAPACITY: return "count exceeds the context's max_batch";
+    case LWE_ECAPACITY:
+      return "count exceeds the context's max_batch or the built-in scratch area";
     default: return "unknown error";
   }
 }

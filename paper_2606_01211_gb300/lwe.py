@@ -24,6 +24,7 @@ LWE_ECUDA = -3
 LWE_ETIMEOUT = -4
 LWE_EUNSUPPORTED = -5
 LWE_ECAPACITY = -6
+LWE_NOALLOC_SCRATCH_BYTES = 1024 * 1024  # the built-in scratch of lwe_encaps_noalloc
 
 PATH_AUTO, PATH_SKINNY, PATH_TENSOR = 0, 1, 2
 (OPT_PATH, OPT_TENSOR_MIN, OPT_TIMING, OPT_GEMM_BN, OPT_GEMM_KCHUNK, OPT_GEMM_PAIR,
@@ -75,11 +76,13 @@ def _load():
         "lwe_decaps": (i32, [vp, vp, vp, vp, u32, vp, vp]),
         "lwe_encaps_multi": (i32, [vp, vp, vp, vp, vp, u32, vp, vp, vp]),
         "lwe_decaps_multi": (i32, [vp, vp, vp, vp, u32, vp, vp]),
+        "lwe_ctx_bind_key": (i32, [vp, vp, vp, vp, vp]),
         "lwe_expand_A": (i32, [vp, u32, u32, vp, vp]),
         "lwe_matmul_modq": (i32, [vp, i32, vp, vp, vp, u32, u32, u32, vp, vp, vp]),
         "lwe_encaps_noalloc": (i32, [P, vp, vp, vp, u32, vp, vp, vp]),
         "lwe_selftest_bounded_wait": (i32, [vp, u32, vp]),
         "lwe_probe": (i32, [i32, u32, u32, vp, vp]),
+        "lwe_noise_table": (i32, [P, vp, vp]),
         "lwe_strerror": (C.c_char_p, [i32]),
         "lwe_last_cuda_error": (C.c_char_p, []),
         "lwe_ctx_device_error": (i32, [vp]),
@@ -258,6 +261,16 @@ class Ctx:
     def empty_ct(self, count: int = 1) -> torch.Tensor:
         return torch.empty((count, self.params.ct_bytes), dtype=torch.uint8, device="cuda")
 
+    def bind_key(self, pk: torch.Tensor | None, sk: torch.Tensor | None = None,
+                 A: torch.Tensor | None = None, stream=None):
+        """Make H(pk) and the tensor path's limbs of [A | B] once for calls
+        with these (pk, A) / (sk, A) buffers; bind_key(None) unbinds."""
+        p = self.params
+        rc = _lib.lwe_ctx_bind_key(
+            self._h, _ptr(pk, torch.uint8, p.pk_bytes, "pk"), _ptr(sk, torch.uint8, p.sk_bytes, "sk"),
+            _ptr(A, torch.int16, p.n * p.n * 2, "A"), _stream(stream))
+        _check(rc, "lwe_ctx_bind_key")
+
     # ---- KEM -----------------------------------------------------------
     def keygen(self, seeds: torch.Tensor, pk: torch.Tensor, sk: torch.Tensor,
                A_out: torch.Tensor | None = None, stream=None):
@@ -348,6 +361,14 @@ def matmul_modq(side: int, S: torch.Tensor, out: torch.Tensor, n: int, logq: int
         _ptr(S, torch.int8, k * n, "S"), n, k, logq, _ptr(E, torch.int8, k * n, "E"),
         _ptr(out, torch.int16, k * n * 2, "out"), _stream(stream))
     _check(rc, "lwe_matmul_modq")
+
+
+def noise_table(params: Params, out: torch.Tensor, stream=None):
+    """The noise kernel's word table: out[w] = the sample of 16-bit word w
+    (out: 65536 int8 on the device)."""
+    cp = params.c()
+    _check(_lib.lwe_noise_table(C.byref(cp), _ptr(out, torch.int8, 65536, "out"), _stream(stream)),
+           "lwe_noise_table")
 
 
 def kernel_names():

@@ -13,9 +13,14 @@ observed through CUDA events; latency is measured from a request's arrival
 to the moment its batch is seen complete.
 
 Keys (pk, sk) stay on the device.  The expanded matrix A of a key is kept
-in an LRU cache bounded by a byte budget (admission by device memory); a
-key whose A is not cached is served with A regenerated inside the kernels
-from its seed (the paper's on-demand generation, Sec. 4.3).
+in an LRU cache that grows while the device has free memory: a miss takes a
+free slot, else a new chunk of slots when the live free device memory (read
+at that moment) stays above a reserve and the byte budget allows, else it
+evicts the least recently used A.  A key whose A is not cached is served
+with A regenerated inside the kernels from its seed (the paper's on-demand
+generation, Sec. 4.3).  A batch of one key (one request at low load, or a
+hot key) is one single-key library call; only batches that mix keys take
+the per-item key pointers.
 
 The engine only moves buffers and orders calls: every step of KeyGen,
 Encaps and Decaps runs in liblwe.so's kernels.
@@ -45,7 +50,8 @@ class ServeConfig:
     requests: int = 20000
     max_batch: int = 512
     slots: int = 4
-    a_budget_bytes: int | None = None          # None: half the free device memory
+    a_budget_bytes: int | None = None          # None: no cap beyond the live free memory
+    reserve_bytes: int = 8 << 30               # free device memory the A cache leaves alone
     seed: int = 1
     plain: bool = False                        # per-request launches (baseline)
 
@@ -68,37 +74,31 @@ def zipf_keys(count: int, n_keys: int, s: float, r: np.random.Generator) -> np.n
 class KeyStore:
     """Resident key pairs per dimension and an LRU cache of expanded A.
 
-    The cache is an arena allocated once, one fixed slot of 2 n^2 bytes per
-    cached A, so admitting a key never allocates device memory while
-    serving.  Its budget (by default half the device memory free at start)
-    is water-filled over the dimensions: each gets what all its keys need
-    or an equal share of what is left, smallest need first.  A slot that is
+    The cache holds fixed slots of 2 n^2 bytes per dimension, in chunks of
+    CHUNK_BYTES.  A miss takes a free slot; with none free, a new chunk is
+    allocated if the device's free memory, read live, stays above the
+    reserve after it and the byte budget (if any) allows; otherwise the
+    least recently used A of that dimension is evicted (a dimension that
+    holds no slot then serves the key with A regenerated).  A slot that is
     reused waits, on the stream that refills it, for the last batch that
-    read it.  The most popular keys are expanded up front."""
+    read it.  The most popular keys are expanded up front, up to an even
+    share per dimension of what the budget or the free memory allows."""
+
+    CHUNK_BYTES = 256 << 20
 
     def __init__(self, cfg: ServeConfig, device: torch.device, prefill: bool = True):
         self.dev = device
+        self.cfg = cfg
         self.params = {}
         self.pk, self.sk = {}, {}
-        self.hits = self.misses = self.fills = 0
-        self.arena, self.slot_of, self.lru, self.free, self.last_use = {}, {}, {}, {}, {}
+        self.hits = self.misses = self.fills = self.grows = 0
+        self.chunks, self.slot_at, self.slot_of, self.lru, self.free, self.last_use = \
+            {}, {}, {}, {}, {}, {}
         self.ready = {}
-        budget = cfg.a_budget_bytes
-        if budget is None:
-            free, _total = torch.cuda.mem_get_info(device)
-            budget = free // 2
-        need = {}
-        for name in cfg.presets:
-            n = PRESETS[name]["n"]
-            need[name] = cfg.keys_per_n * 2 * n * n
-        share_of, left = {}, budget
-        order = sorted(cfg.presets, key=lambda nm: need[nm])
-        for k, name in enumerate(order):
-            share_of[name] = min(need[name], left // (len(order) - k))
-            left -= share_of[name]
-        self.budget = budget
+        self.budget = cfg.a_budget_bytes
+        self.reserve = cfg.reserve_bytes
+        self.used = 0
         for i, name in enumerate(cfg.presets):
-            share = share_of[name]
             p = lwe.Params(**PRESETS[name])
             n = p.n
             self.params[n] = p
@@ -111,20 +111,60 @@ class KeyStore:
                 ctx.keygen(ms[a:b], pk[a:b], sk[a:b])
             self.pk[n], self.sk[n] = pk, sk
             ctx.close()
-            slots = int(min(cfg.keys_per_n, share // (2 * n * n)))
-            self.arena[n] = torch.empty((max(slots, 0), n, n), dtype=torch.int16, device=device)
+            self.chunks[n], self.slot_at[n] = [], []
             self.slot_of[n] = {}
             self.lru[n] = collections.OrderedDict()
-            self.free[n] = list(range(slots - 1, -1, -1))
-            self.last_use[n] = [None] * slots
-            self.ready[n] = [None] * slots
-            if prefill:  # key k is the (k+1)-th most popular (Zipf rank)
-                for k in range(slots):
-                    self._fill(n, k, torch.cuda.current_stream(device))
+            self.free[n], self.last_use[n], self.ready[n] = [], [], []
+        if prefill:  # key k is the (k+1)-th most popular (Zipf rank)
+            share = self._share()
+            for n in self.params:
+                for k in range(min(cfg.keys_per_n, share // (2 * n * n))):
+                    if self._fill(n, k, torch.cuda.current_stream(device)) is None:
+                        break
         torch.cuda.synchronize(device)
         self.hits = self.misses = self.fills = 0
 
+    def _share(self) -> int:
+        """Each dimension's fair share of the cache: the budget, or what the
+        device could hold now above the reserve, split evenly."""
+        free, _ = torch.cuda.mem_get_info(self.dev)
+        room = self.used + max(0, free - self.reserve)
+        if self.budget is not None:
+            room = min(room, self.budget)
+        return room // max(1, len(self.params))
+
+    def _grow(self, n) -> bool:
+        """One more chunk of slots for dimension n, if live free memory and
+        the budget allow."""
+        slot_bytes = 2 * n * n
+        per = max(1, self.CHUNK_BYTES // slot_bytes)
+        per = min(per, self.cfg.keys_per_n - len(self.slot_at[n]))
+        if per <= 0:
+            return False
+        nbytes = per * slot_bytes
+        if self.budget is not None and self.used + nbytes > self.budget:
+            per = (self.budget - self.used) // slot_bytes
+            nbytes = per * slot_bytes
+            if per <= 0:
+                return False
+        free, _ = torch.cuda.mem_get_info(self.dev)
+        if free - nbytes < self.reserve:
+            return False
+        chunk = torch.empty((per, n, n), dtype=torch.int16, device=self.dev)
+        self.chunks[n].append(chunk)
+        base = len(self.slot_at[n])
+        for j in range(per):
+            self.slot_at[n].append(chunk[j])
+            self.last_use[n].append(None)
+            self.ready[n].append(None)
+        self.free[n].extend(range(base + per - 1, base - 1, -1))
+        self.used += nbytes
+        self.grows += 1
+        return True
+
     def _fill(self, n, key, stream):
+        if not self.free[n] and not self._grow(n) and not self.lru[n]:
+            return None
         self.fills += 1
         if self.free[n]:
             s = self.free[n].pop()
@@ -134,7 +174,8 @@ class KeyStore:
             if self.last_use[n][s] is not None:
                 stream.wait_event(self.last_use[n][s])
         with torch.cuda.stream(stream):
-            lwe.expand_A(self.pk[n][key, :16], n, self.params[n].logq, self.arena[n][s], stream=stream)
+            lwe.expand_A(self.pk[n][key, :16], n, self.params[n].logq, self.slot_at[n][s],
+                         stream=stream)
             ev = torch.cuda.Event()
             ev.record(stream)
         self.ready[n][s] = ev
@@ -154,11 +195,12 @@ class KeyStore:
             self.lru[n].move_to_end(key)
             self.hits += 1
             stream.wait_event(self.ready[n][s])  # filled, possibly on another stream
-            return self.arena[n][s]
+            return self.slot_at[n][s]
         self.misses += 1
-        if not admit or self.arena[n].shape[0] == 0:
+        if not admit:
             return None
-        return self.arena[n][self._fill(n, key, stream)]
+        s = self._fill(n, key, stream)
+        return None if s is None else self.slot_at[n][s]
 
     def used_by(self, n: int, keys, event: torch.cuda.Event):
         """Record the batch that reads these keys' cached A."""
@@ -201,6 +243,8 @@ class Engine:
         self.store = store or KeyStore(cfg, self.dev)
         mb = 1 if cfg.plain else cfg.max_batch
         self.slots = [Slot(self.store, mb, self.dev, cfg.plain) for _ in range(cfg.slots)]
+        self.spans = []
+        self.n_single = self.n_multi = self.n_tensor = 0
         self._make_requests()
 
     # ---- workload --------------------------------------------------------
@@ -254,6 +298,7 @@ class Engine:
     # ---- serving ---------------------------------------------------------
     HOT = 64          # waiting requests of one key that justify a single-key batch
     ADMIT = 8         # cache misses admitted (A expanded) per dispatch
+    TENSOR_MIN = 64   # the contexts' default LWE_OPT_TENSOR_MIN (AUTO path)
 
     def _key_ptrs(self, n: int, keys: np.ndarray, what: str) -> np.ndarray:
         p = self.store.params[n]
@@ -270,7 +315,15 @@ class Engine:
         rows = torch.tensor([P["row"][q.rid] for q in group], dtype=torch.long)
         cnt = len(group)
         st = slot.stream
+        if op != "keygen":
+            if single_key:
+                self.n_single += 1
+                self.n_tensor += int(cnt >= self.TENSOR_MIN and not self.cfg.plain)
+            else:
+                self.n_multi += 1
         with torch.cuda.stream(st):
+            t_start = torch.cuda.Event(enable_timing=True)
+            t_start.record(st)
             rows_d = rows.to(self.dev, non_blocking=True)
             if op == "keygen":
                 torch.index_select(P["seeds"], 0, rows_d, out=B["seeds"][:cnt])
@@ -331,11 +384,12 @@ class Engine:
                 if op == "encaps":
                     P["ct"].index_copy_(0, rows_d, B["ct"][:cnt])
                 P["K"].index_copy_(0, rows_d, B["K"][:cnt])
-            ev = torch.cuda.Event()
+            ev = torch.cuda.Event(enable_timing=True)
             ev.record(st)
         if op != "keygen":
             self.store.used_by(n, {q.key for q in group}, ev)
         slot.event, slot.reqs = ev, group
+        self.spans.append((t_start, ev))
 
     def _take(self, fifo: collections.deque, per_key: collections.Counter, mb: int):
         """The batch to launch from one (operation, n) queue."""
@@ -352,7 +406,8 @@ class Engine:
         group = [fifo.popleft() for _ in range(min(mb, len(fifo)))]
         for q in group:
             per_key[q.key] -= 1
-        return group, self.cfg.plain
+        # one key (a lone request at low load): the plain single-key call
+        return group, self.cfg.plain or len({q.key for q in group}) == 1
 
     def warmup(self):
         """Push one small batch of every kind (KeyGen; single-key and
@@ -378,6 +433,27 @@ class Engine:
                             slot.event, slot.reqs = None, []
         torch.cuda.synchronize(self.dev)
         self.store.hits = self.store.misses = 0
+        self.spans = []
+        self.n_single = self.n_multi = self.n_tensor = 0
+
+    def _gpu_busy(self) -> float:
+        """Fraction of the span from the first batch's start to the last
+        batch's end during which at least one batch was on the device (its
+        slot stream between the batch's first and last command)."""
+        if not self.spans:
+            return 0.0
+        ref = self.spans[0][0]
+        iv = sorted((ref.elapsed_time(a), ref.elapsed_time(b)) for a, b in self.spans)
+        busy, cur_a, cur_b = 0.0, iv[0][0], iv[0][1]
+        for a, b in iv[1:]:
+            if a > cur_b:
+                busy += cur_b - cur_a
+                cur_a, cur_b = a, b
+            else:
+                cur_b = max(cur_b, b)
+        busy += cur_b - cur_a
+        total = max(b for _, b in iv) - iv[0][0]
+        return busy / total if total > 0 else 0.0
 
     def run(self) -> dict:
         cfg = self.cfg
@@ -424,7 +500,10 @@ class Engine:
                "batches": batches, "mean_batch": N / max(batches, 1),
                "a_cache_hits": self.store.hits, "a_cache_misses": self.store.misses,
                "a_cache_fills": self.store.fills - fills0, "host_launch_s": host_launch,
-               "makespan_s": makespan, "plain": cfg.plain}
+               "makespan_s": makespan, "plain": cfg.plain,
+               "single_key_batches": self.n_single, "multi_key_batches": self.n_multi,
+               "tensor_batches": self.n_tensor, "a_cache_bytes": self.store.used,
+               "gpu_busy": self._gpu_busy()}
         by_op = {}
         for i, name in enumerate(OPS):
             li = np.array([q.t_done - q.t_arr for q in self.reqs if q.op == i])
@@ -459,7 +538,8 @@ def main():
     ap.add_argument("--max-batch", type=int, default=512)
     ap.add_argument("--slots", type=int, default=4)
     ap.add_argument("--a-budget-gb", type=float, default=None,
-                    help="A cache budget (default: half the free device memory)")
+                    help="A cache cap (default: none; the cache grows while the live free "
+                         "device memory stays above the reserve)")
     ap.add_argument("--no-plain", action="store_true")
     args = ap.parse_args()
     torch.cuda.set_device(0)

@@ -15,11 +15,31 @@ from paper_2606_01211_gb300 import serve
 pytestmark = pytest.mark.gpu
 
 
+NAMES = {640: "P640", 976: "P976", 1344: "P1344", 4096: "P4096"}
+
+
 @pytest.fixture(scope="module")
 def served():
+    """The served mix over all four dimensions, with an A cache far too
+    small for the keys (cache pressure: regenerated A and evictions)."""
     torch.cuda.set_device(0)
-    cfg = serve.ServeConfig(presets=("P640", "P976"), keys_per_n=24, requests=700, rate=3e4,
-                            max_batch=96, slots=3, a_budget_bytes=3 << 20, seed=5)
+    cfg = serve.ServeConfig(presets=("P640", "P976", "P1344", "P4096"), keys_per_n=24,
+                            requests=700, rate=3e4, max_batch=96, slots=3,
+                            a_budget_bytes=40 << 20, seed=5)
+    eng = serve.Engine(cfg)
+    eng.warmup()
+    stats = eng.run()
+    torch.cuda.synchronize()
+    return eng, stats
+
+
+@pytest.fixture(scope="module")
+def hot():
+    """Few keys and a burst of arrivals: one key has many waiting requests,
+    so single-key batches of at least 64 items take the tensor-core path."""
+    torch.cuda.set_device(0)
+    cfg = serve.ServeConfig(presets=("P640", "P976"), keys_per_n=3, requests=1500, rate=1e7,
+                            max_batch=256, slots=2, seed=6)
     eng = serve.Engine(cfg)
     eng.warmup()
     stats = eng.run()
@@ -32,11 +52,18 @@ def test_serving_completes_with_batching_and_cache_pressure(served):
     assert st["requests"] == 700 and st["ops_per_s"] > 0
     assert st["mean_batch"] > 1.0          # requests were actually batched
     assert st["a_cache_misses"] > 0        # cache pressure: some A regenerated
+    assert st["multi_key_batches"] > 0
+    assert 0.0 < st["gpu_busy"] <= 1.0
     assert all(q.t_done >= q.t_arr for q in eng.reqs)
 
 
-def test_every_served_result_equals_its_standalone_result(served):
-    eng, _ = served
+def test_hot_key_batches_take_the_tensor_path(hot):
+    eng, st = hot
+    assert st["tensor_batches"] > 0
+    assert st["single_key_batches"] > 0
+
+
+def _check_standalone(eng):
     ctxs = {}
     for q in eng.reqs:
         n = q.n
@@ -66,6 +93,14 @@ def test_every_served_result_equals_its_standalone_result(served):
             assert torch.equal(got_K, want_K), q
 
 
+def test_hot_key_results_equal_their_standalone_results(hot):
+    _check_standalone(hot[0])
+
+
+def test_every_served_result_equals_its_standalone_result(served):
+    _check_standalone(served[0])
+
+
 def test_sampled_served_results_equal_the_oracle(served):
     eng, _ = served
     seen = set()
@@ -74,7 +109,7 @@ def test_sampled_served_results_equal_the_oracle(served):
         if (op, q.n) in seen or op == "decaps":
             continue
         seen.add((op, q.n))
-        name = {640: "P640", 976: "P976"}[q.n]
+        name = NAMES[q.n]
         po = O.Params(**PRESETS[name])
         row = eng.pool[q.n]["row"][q.rid]
         if op == "keygen":
@@ -88,7 +123,7 @@ def test_sampled_served_results_equal_the_oracle(served):
             ct_o, K_o = O.encaps(po, pk, c)
             got_ct, got_K = eng.result(q)
             assert np.array_equal(host(got_ct), ct_o) and np.array_equal(host(got_K), K_o)
-    assert len(seen) == 4
+    assert len(seen) == 2 * len(eng.cfg.presets)
 
 
 def test_plain_per_request_serving_gives_the_same_results(served):

@@ -98,10 +98,11 @@ def test_kem_tensor_path_matches_oracle(name, count, stored, pair):
     assert ctx.device_error() == 0
 
 
-def test_batched_4096_tensor_equals_skinny_and_oracle_samples():
+def test_batched_4096_tensor_equals_skinny_and_oracle():
     """The benchmarked workload: one P976 key, 4096 encapsulations then the
     4096 decapsulations, on the tensor path; every item equals the CUDA-core
-    path's, and sampled items equal the oracle's."""
+    path's and the oracle's (all 4096 ciphertexts and both key sets, the
+    oracle's batch run on every host core)."""
     name, count = "P976", 4096
     cfg = PRESETS[name]
     p, po = params(name)
@@ -126,10 +127,56 @@ def test_batched_4096_tensor_equals_skinny_and_oracle_samples():
     assert np.array_equal(K_t, K_s)
     assert np.array_equal(K2_t, K_t)
     assert np.array_equal(K2_s, K_s)
-    for i in [0, 1, 777, 2048, 4095]:
-        ct_o, K_o = O.encaps(po, pk_o, bytes(cs[i]), A=A_o)
-        assert np.array_equal(ct_t[i], ct_o), i
-        assert np.array_equal(K_t[i], K_o), i
+    ct_o, K_o = O.encaps_batch(po, pk_o, cs, A=A_o, nthreads=O.max_threads())
+    bad = np.nonzero((ct_t != ct_o).any(axis=1))[0]
+    assert bad.size == 0, "ciphertexts differ from the oracle at %s" % bad[:8]
+    assert np.array_equal(K_t, K_o)
+    K2_o = O.decaps_batch(po, sk_o, ct_t, A=A_o, nthreads=O.max_threads())
+    assert np.array_equal(K2_t, K2_o)
+    assert ctx.device_error() == 0
+
+
+@pytest.mark.parametrize("path", [lwe.PATH_TENSOR, lwe.PATH_SKINNY])
+def test_bound_key_gives_the_same_results(path):
+    """lwe_ctx_bind_key makes H(pk) and the limbs once; bound calls equal
+    unbound ones, also after a tensor-path call for another key has
+    overwritten the limb workspace, and after unbinding."""
+    name, count = "P976", 80
+    p, po = params(name)
+    ctx = lwe.Ctx(p, max_batch=count)
+    ctx.set_path(path)
+    keys = []
+    for s in (41, 42):
+        pk, sk = ctx.empty_pk(1), ctx.empty_sk(1)
+        A = torch.empty((p.n, p.n), dtype=torch.int16, device="cuda")
+        ctx.keygen(dev(master_seeds(1, seed=s)), pk, sk, A_out=A)
+        keys.append((pk, sk, A))
+    (pk, sk, A), (pk2, sk2, A2) = keys
+    cs = dev(coins(count, seed=43))
+
+    def run(pk, sk, A):
+        ct = ctx.empty_ct(count)
+        K = torch.empty((count, 32), dtype=torch.uint8, device="cuda")
+        ctx.encaps(pk, cs, ct, K, A=A)
+        K2 = torch.empty_like(K)
+        ctx.decaps(sk, ct, K2, A=A)
+        return host(ct), host(K), host(K2)
+
+    ref = run(pk, sk, A)
+    ref2 = run(pk2, sk2, A2)
+    ctx.bind_key(pk, sk, A)
+    # bound, another key in between (overwrites the limbs), bound again
+    for keyset, want in (((pk, sk, A), ref), ((pk2, sk2, A2), ref2), ((pk, sk, A), ref)):
+        for x, y in zip(run(*keyset), want):
+            assert np.array_equal(x, y)
+    ctx.bind_key(None, sk, None)  # sk only, stored A not bound: regenerated A
+    c_fused = run(pk, sk, None)
+    ctx.bind_key(None)
+    d_fused = run(pk, sk, None)
+    for x, y in zip(c_fused, d_fused):
+        assert np.array_equal(x, y)
+    for x, y in zip(c_fused, ref):
+        assert np.array_equal(x, y)
     assert ctx.device_error() == 0
 
 

@@ -53,6 +53,72 @@ def test_encaps_noalloc_equals_encaps_on_two_calls(name, count):
         assert torch.equal(K2, K)
 
 
+def _scratch_bytes(n, count):
+    """The documented size of the scratch a call needs: its parts (seeds,
+    mu, K', flags, H(pk), round keys, S', E', E'') each rounded up to 256
+    bytes."""
+    up = lambda b: (b + 255) // 256 * 256
+    parts = [32 * count, 32 * count, 32 * count, 4 * count, 32, 176 * count,
+             8 * n * count, 8 * n * count, 64 * count]
+    return sum(up(b) for b in parts)
+
+
+def test_encaps_noalloc_equals_tensor_path_up_to_the_largest_count():
+    """A default (AUTO) context takes the tensor-core GEMM from 64 items on;
+    the no-alloc call (CUDA cores) must still give the same bytes, up to the
+    largest count that fits the area, and refuse one item more."""
+    torch.cuda.set_device(0)
+    p = lwe.Params(**PRESETS["P640"])
+    cap = lwe.LWE_NOALLOC_SCRATCH_BYTES
+    top = max(c for c in range(1, 200) if _scratch_bytes(p.n, c) <= cap)
+    assert top >= 64
+    ctx = lwe.Ctx(p, max_batch=top + 1)
+    pk, sk = ctx.empty_pk(1), ctx.empty_sk(1)
+    A = torch.empty((p.n, p.n), dtype=torch.int16, device="cuda")
+    ctx.keygen(torch.from_numpy(master_seeds(1, seed=8)).cuda(), pk, sk, A_out=A)
+    for count in (64, 96, top):
+        cs = torch.from_numpy(coins(count, seed=700 + count)).cuda()
+        ct_ref = ctx.empty_ct(count)
+        K_ref = torch.empty((count, 32), dtype=torch.uint8, device="cuda")
+        ctx.encaps(pk, cs, ct_ref, K_ref, A=A)
+        ct = torch.full_like(ct_ref, 0x3C)
+        K = torch.full_like(K_ref, 0xC3)
+        assert _noalloc(p, pk, A, cs, count, ct, K) == lwe.LWE_OK
+        torch.cuda.synchronize()
+        assert torch.equal(ct, ct_ref), "ciphertexts differ at %d items" % count
+        assert torch.equal(K, K_ref), "keys differ at %d items" % count
+    count = top + 1
+    cs = torch.zeros((count, 32), dtype=torch.uint8, device="cuda")
+    ct = torch.zeros((count, p.ct_bytes), dtype=torch.uint8, device="cuda")
+    K = torch.zeros((count, 32), dtype=torch.uint8, device="cuda")
+    assert _noalloc(p, pk, A, cs, count, ct, K) == lwe.LWE_ECAPACITY
+    ctx.close()
+
+
+def test_encaps_noalloc_allocates_no_device_memory():
+    """After a first call (which does the one-time set-up), a further call
+    changes neither the device's free memory nor torch's allocation count."""
+    torch.cuda.set_device(0)
+    p = lwe.Params(**PRESETS["P976"])
+    count = 8
+    ctx = lwe.Ctx(p, max_batch=1)
+    pk, sk = ctx.empty_pk(1), ctx.empty_sk(1)
+    ctx.keygen(torch.from_numpy(master_seeds(1, seed=9)).cuda(), pk, sk)
+    cs = torch.from_numpy(coins(count, seed=9)).cuda()
+    ct = ctx.empty_ct(count)
+    K = torch.empty((count, 32), dtype=torch.uint8, device="cuda")
+    assert _noalloc(p, pk, None, cs, count, ct, K) == lwe.LWE_OK
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    alloc0 = torch.cuda.memory_allocated()
+    assert _noalloc(p, pk, None, cs, count, ct, K) == lwe.LWE_OK
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
+    assert torch.cuda.memory_allocated() == alloc0
+    ctx.close()
+
+
 def test_encaps_noalloc_rejects_what_does_not_fit():
     torch.cuda.set_device(0)
     p = lwe.Params(**PRESETS["P4096"])
