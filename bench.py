@@ -924,12 +924,40 @@ def large_n(lwe, torch, dev, batch: int = 1024):
         ctx.decaps(sk, ct, K2, A=A)
         torch.cuda.synchronize()
         assert torch.equal(K, K2)
+        r["row_split"] = row_split_times(lwe, torch, stream, A, n)
         res[name] = r
         ctx.close()
         del A
         torch.cuda.empty_cache()
     res["unit"] = "ms per call"
     return res
+
+
+def row_split_times(lwe, torch, stream, A, n, worlds=(2, 4)):
+    """One GPU's share of a row-split product (lwe_matmul_modq_rows over rank
+    0's block of rows, A stored or regenerated) against the whole product on
+    one GPU, CUDA-event ms (median of 3).  The collectives (an all-gather of
+    16 n bytes, a sum-reduction of 32 n bytes) are not timed here: every run
+    of this benchmark has one GPU."""
+    from paper_2606_01211_gb300 import rowsplit
+    dev = A.device
+    St = torch.randint(-6, 7, (8, n), dtype=torch.int8, device=dev)
+    seed = torch.arange(16, dtype=torch.uint8, device=dev)
+    o_as = torch.empty((n, 8), dtype=torch.int16, device=dev)
+    o_sa = torch.empty((8, n), dtype=torch.int16, device=dev)
+    out = {}
+    for world in (1,) + tuple(worlds):
+        r0, r1 = rowsplit.row_block(n, world, 0)
+        blk = A[r0:r1]
+        t = {}
+        for mode, Ar, sd in (("stored", blk, None), ("fused", None, seed)):
+            t["AS_" + mode] = _event_ms(torch, stream, lambda: lwe.matmul_modq_rows(
+                lwe.SIDE_AS, St, o_as, n, 16, r0, r1, A_rows=Ar, seedA=sd), reps=3)
+            t["SA_" + mode] = _event_ms(torch, stream, lambda: lwe.matmul_modq_rows(
+                lwe.SIDE_SA, St, o_sa, n, 16, r0, r1, A_rows=Ar, seedA=sd), reps=3)
+        out["world%d_rank0" % world] = t
+    out["unit"] = "ms per call on one GPU (its rows only)"
+    return out
 
 
 def main():

@@ -269,6 +269,30 @@ int lwe_matmul_modq(lwe_ctx *ctx, int side, const uint16_t *A,
                     uint32_t k, uint32_t logq, const int8_t *E,
                     uint16_t *out, void *stream);
 
+/* The same products restricted to a block of rows of A, for one huge-n
+ * operation split over several GPUs (the paper names multi-GPU execution
+ * as future work, Sec. 5; Sec. 4.3 shows the large-n products are bound by
+ * A's memory traffic or its regeneration).  Each GPU holds or regenerates
+ * only rows [row0, row1) of A:
+ *   side LWE_SIDE_AS:  out[row1 - row0][8] = rows row0 .. row1-1 of A S + E,
+ *                      E given for those rows only ([row1 - row0][8],
+ *                      nullable); the blocks of all GPUs, gathered in row
+ *                      order, are B = A S + E.
+ *   side LWE_SIDE_SA:  out[k][n] = (S[:, row0:row1] A[row0:row1, :] + E)
+ *                      mod q, a partial sum over the block's rows (E
+ *                      nullable, k x n: give it on one GPU only); summing
+ *                      the partials of all GPUs (as integers) and reducing
+ *                      mod q gives S A + E.
+ * A_rows [row1 - row0][n] uint16: the block of rows (row row0 first), or
+ * NULL to regenerate those rows from seedA [16] (device).  S as in
+ * lwe_matmul_modq (S^T [8][n] for AS, S [k][n] for SA, full width).  row0
+ * and row1 multiples of 16 with row0 < row1 <= n.  CUDA-core kernels;
+ * needs no context.  LWE_EINVAL for bad sizes or pointers. */
+int lwe_matmul_modq_rows(int side, const uint16_t *A_rows, const uint8_t *seedA,
+                         const int8_t *S, uint32_t n, uint32_t k, uint32_t logq,
+                         uint32_t row0, uint32_t row1, const int8_t *E, uint16_t *out,
+                         void *stream);
+
 /* ---- Encaps without any device allocation ------------------------------ */
 
 /* Size of the library's built-in scratch area.  Every GPU that loads

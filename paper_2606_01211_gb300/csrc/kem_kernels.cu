@@ -262,14 +262,15 @@ __global__ void __launch_bounds__(512, 1) k_mul_as_fused(MulAsArgs a) {
   const uint32_t n = a.n;
   const uint32_t m = (1u << a.logq) - 1u, mm = m | (m << 16);
   const int8_t *St = a.St + (size_t)e * a.st_stride;
-  for (uint32_t i = blockIdx.x * 16 + warp; i < n; i += gridDim.x * 16) {
+  const uint32_t rows = a.rows ? a.rows : n;
+  for (uint32_t i = blockIdx.x * 16 + warp; i < rows; i += gridDim.x * 16) {
     int acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     // a lane's blocks step by 32 through the row: its 256-aligned counter
     // window (the first two AES rounds, aes_ctr_run) changes every 8 blocks
     AesCtrRun win;
     uint64_t wcur = ~0ull;
     for (uint32_t jc = lane; jc < n / 8; jc += 32) {
-      const uint64_t b = (uint64_t)i * (n / 8) + jc;
+      const uint64_t b = (uint64_t)(a.row0 + i) * (n / 8) + jc;
       if ((b >> 8) != wcur) {
         wcur = b >> 8;
         win = aes_ctr_run(tab, rk, 0, b);
@@ -335,7 +336,7 @@ __global__ void __launch_bounds__(256) k_mul_as_rows(MulAsArgs a) {
   const uint32_t e = blockIdx.y;
   const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t n = a.n, nch = n / 8;
-  const uint32_t tasks = n / AS_ROWS;  // n is a multiple of AS_ROWS
+  const uint32_t tasks = (a.rows ? a.rows : n) / AS_ROWS;  // rows: a multiple of AS_ROWS
   const int8_t *St = a.St + (size_t)e * a.st_stride;
   for (uint32_t task = blockIdx.x + gridDim.x * warp; task < tasks; task += gridDim.x * 8) {
   const uint32_t i0 = task * AS_ROWS;
@@ -590,17 +591,19 @@ __global__ void __launch_bounds__(256) k_sa(MulSaArgs a) {
   const bool jv = j0 < n;  // n and j0 are multiples of 8: a chunk is all in or all out
   for (uint32_t i = tid; i < 2048; i += 256) red[i] = 0;
   const int8_t *S = a.S + (size_t)e * a.s_stride;
+  const uint32_t p0 = a.row0 / 2, p1 = (a.row1 ? a.row1 : n) / 2;
+  // a stored row block starts at row row0
   const uint16_t *Aitem = a.A_ptrs ? a.A_ptrs[e] : a.A;
-  const uint32_t npairs = n / 2;
-  const uint32_t per = (npairs + R - 1) / R;
-  const uint32_t pb = min(npairs, rsplit * per), pe = min(npairs, pb + per);
+  const uint32_t r0 = a.row0;
+  const uint32_t per = (p1 - p0 + R - 1) / R;
+  const uint32_t pb = min(p1, p0 + rsplit * per), pe = min(p1, pb + per);
   int acc[8][8];
 #pragma unroll
   for (int k = 0; k < 8; k++)
 #pragma unroll
     for (int c = 0; c < 8; c++) acc[k][c] = 0;
   auto row_chunk = [&](uint32_t i) -> uint4 {
-    return jv ? ld_nc_u4(Aitem + (size_t)i * n + j0) : make_uint4(0, 0, 0, 0);
+    return jv ? ld_nc_u4(Aitem + (size_t)(i - r0) * n + j0) : make_uint4(0, 0, 0, 0);
   };
   auto mac_pair = [&](const uint4 x0, const uint4 x1, const uint4 sp) {
     const uint32_t w0[4] = {x0.x, x0.y, x0.z, x0.w}, w1[4] = {x1.x, x1.y, x1.z, x1.w};
@@ -682,9 +685,9 @@ __global__ void __launch_bounds__(512, 1) k_sa_fused(MulSaArgs a) {
   aes_key_expand(tab, key, rk);
   const uint32_t mq = (1u << a.logq) - 1u, mm = mq | (mq << 16);
   const int8_t *S = a.S + (size_t)e * a.s_stride;
-  const uint32_t npairs = n / 2;
-  const uint32_t per = (npairs + R - 1) / R;
-  const uint32_t pb = min(npairs, rsplit * per), pe = min(npairs, pb + per);
+  const uint32_t p0 = a.row0 / 2, p1 = (a.row1 ? a.row1 : n) / 2;
+  const uint32_t per = (p1 - p0 + R - 1) / R;
+  const uint32_t pb = min(p1, p0 + rsplit * per), pe = min(p1, pb + per);
   int acc[8][4];
 #pragma unroll
   for (int k = 0; k < 8; k++)
@@ -1414,16 +1417,17 @@ void launch_noise(const NoiseArgs &a, int num_sms, cudaStream_t st) {
 }
 
 void launch_mul_as(const MulAsArgs &a, uint32_t count, bool fused, int num_sms, cudaStream_t st) {
+  const uint32_t rows = a.rows ? a.rows : a.n;
   if (fused) {
     const uint32_t per_item = std::max<uint32_t>(1u, (uint32_t)std::max(num_sms, 1) / count);
-    dim3 grid(std::min((a.n + 15) / 16, per_item), count);
+    dim3 grid(std::min((rows + 15) / 16, per_item), count);
     launch_k(k_mul_as_fused, grid, 512, AES_SMEM_BYTES, st, a);
-  } else if ((uint64_t)count * (a.n / AS_ROWS) < 4ull * 16 * (uint64_t)std::max(num_sms, 1)) {
+  } else if ((uint64_t)count * (rows / AS_ROWS) < 4ull * 16 * (uint64_t)std::max(num_sms, 1)) {
     // fewer than ~4 row groups per warp of the grid below: split columns
-    launch_k(k_mul_as_split, dim3(a.n / AS_ROWS, count), 256, 0, st, a);
+    launch_k(k_mul_as_split, dim3(rows / AS_ROWS, count), 256, 0, st, a);
   } else {
     // two CTAs per SM in all, spread over the items
-    const uint32_t want = (a.n / AS_ROWS + 7) / 8;
+    const uint32_t want = (rows / AS_ROWS + 7) / 8;
     const uint32_t share = std::max<uint32_t>(1u, 2u * (uint32_t)std::max(num_sms, 1) / count);
     dim3 grid(std::min(want, share), count);
     launch_k(k_mul_as_rows, grid, 256, 0, st, a);
@@ -1440,8 +1444,9 @@ void launch_mul_sa(const MulSaArgs &a, uint32_t items, bool fused, bool cmp, int
   // grid holds about two CTAs per SM (one with the AES tables)
   const uint32_t cbs = (a.n + 255) / 256;
   const uint32_t target = (fused ? 1u : 2u) * (uint32_t)std::max(num_sms, 1);
+  const uint32_t pairs = ((a.row1 ? a.row1 : a.n) - a.row0) / 2;
   uint32_t R = 1;
-  while (R < 8 && (uint64_t)cbs * items * R < target && a.n / 2 / (2 * R) >= 64) R <<= 1;
+  while (R < 8 && (uint64_t)cbs * items * R < target && pairs / (2 * R) >= 64) R <<= 1;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(cbs, R, items);
   cfg.dynamicSmemBytes = (fused ? AES_SMEM_BYTES : 0) + SA_PAIRS * 16 + 2048 * 4;

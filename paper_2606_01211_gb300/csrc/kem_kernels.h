@@ -42,6 +42,8 @@ struct MulAsArgs {
   uint32_t seed_stride;
   uint32_t n;
   uint32_t logq;
+  uint32_t row0;         // first row of A computed (A / E / out start at it)
+  uint32_t rows;         // rows computed (0 = n)
   uint32_t pad;
   const int8_t *St;      // S^T (8 x n) of item e at St + e * st_stride
   uint64_t st_stride;
@@ -77,6 +79,9 @@ struct MulSaArgs {
   const uint16_t *const *A_ptrs;  // per-item stored A (then A unused)
   const uint8_t *const *seed_ptrs;  // per-item seedA at seed_ptrs[e] + seed_off (fused)
   uint64_t seed_off;
+  // row block: the sum runs over rows [row0, row1) of A only (row1 = 0: n);
+  // a stored A then points at row row0 (rows of length n)
+  uint32_t row0, row1;
 };
 
 struct VEncArgs {

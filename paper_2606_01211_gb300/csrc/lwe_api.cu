@@ -1080,6 +1080,56 @@ int lwe_matmul_modq(lwe_ctx *c, int side, const uint16_t *A, const uint8_t *seed
   return check_launch();
 }
 
+int lwe_matmul_modq_rows(int side, const uint16_t *A_rows, const uint8_t *seedA,
+                         const int8_t *S, uint32_t n, uint32_t k, uint32_t logq, uint32_t row0,
+                         uint32_t row1, const int8_t *E, uint16_t *out, void *stream) {
+  if (!S || !out || (!A_rows && !seedA) || n < 16 || n > 65536 || (n % 16) || logq < 1 ||
+      logq > 16)
+    return LWE_EINVAL;
+  if (row0 >= row1 || row1 > n || (row0 % 16) || (row1 % 16)) return LWE_EINVAL;
+  if (!aligned16(S) || !aligned16(out) || (A_rows && !aligned16(A_rows)) || (E && !aligned16(E)))
+    return LWE_EINVAL;
+  int sms = 0;
+  int rc = current_device_setup(nullptr, &sms);
+  if (rc) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (side == LWE_SIDE_AS) {
+    if (k != 8) return LWE_EINVAL;
+    MulAsArgs ma;
+    memset(&ma, 0, sizeof ma);
+    ma.A = A_rows;
+    ma.seeds = seedA;
+    ma.seed_stride = 16;
+    ma.n = n;
+    ma.logq = logq;
+    ma.row0 = row0;
+    ma.rows = row1 - row0;
+    ma.St = S;
+    ma.E = E;
+    ma.out = reinterpret_cast<uint8_t *>(out);
+    LAUNCH(nullptr, KID_MUL_AS, st, launch_mul_as(ma, 1, A_rows == nullptr, sms, st));
+    return check_launch();
+  }
+  if (side != LWE_SIDE_SA || k == 0 || (k % 8)) return LWE_EINVAL;
+  MulSaArgs sa;
+  memset(&sa, 0, sizeof sa);
+  sa.A = A_rows;
+  sa.seedA = seedA;
+  sa.n = n;
+  sa.logq = logq;
+  sa.S = S;
+  sa.s_stride = 8ull * n;
+  sa.E = E;
+  sa.e_stride = 8ull * n;
+  sa.out = reinterpret_cast<uint8_t *>(out);
+  sa.out_stride = 16ull * n;
+  sa.row0 = row0;
+  sa.row1 = row1;
+  LAUNCH(nullptr, A_rows ? KID_MUL_SA : KID_MUL_SA_FUSED, st,
+         launch_mul_sa(sa, k / 8, A_rows == nullptr, false, sms, st));
+  return check_launch();
+}
+
 int lwe_encaps_noalloc(const lwe_params *p, const uint8_t *pk, const uint16_t *A,
                        const uint8_t *coins, uint32_t count, uint8_t *ct, uint8_t *K,
                        void *stream) {

@@ -79,6 +79,7 @@ def _load():
         "lwe_ctx_bind_key": (i32, [vp, vp, vp, vp, vp]),
         "lwe_expand_A": (i32, [vp, u32, u32, vp, vp]),
         "lwe_matmul_modq": (i32, [vp, i32, vp, vp, vp, u32, u32, u32, vp, vp, vp]),
+        "lwe_matmul_modq_rows": (i32, [i32, vp, vp, vp, u32, u32, u32, u32, u32, vp, vp, vp]),
         "lwe_encaps_noalloc": (i32, [P, vp, vp, vp, u32, vp, vp, vp]),
         "lwe_selftest_bounded_wait": (i32, [vp, u32, vp]),
         "lwe_probe": (i32, [i32, u32, u32, vp, vp]),
@@ -369,6 +370,28 @@ def noise_table(params: Params, out: torch.Tensor, stream=None):
     cp = params.c()
     _check(_lib.lwe_noise_table(C.byref(cp), _ptr(out, torch.int8, 65536, "out"), _stream(stream)),
            "lwe_noise_table")
+
+
+def matmul_modq_rows(side: int, S: torch.Tensor, out: torch.Tensor, n: int, logq: int,
+                     row0: int, row1: int, A_rows: torch.Tensor | None = None,
+                     seedA: torch.Tensor | None = None, E: torch.Tensor | None = None,
+                     stream=None):
+    """The products over rows [row0, row1) of A only (lwe_matmul_modq_rows):
+    side AS: out[row1 - row0][8] = those rows of A S + E (E: those rows);
+    side SA: out[k][n] = (S[:, row0:row1] A[row0:row1] + E) mod q.
+    A_rows is the row block (row1 - row0 x n) or None (regenerated)."""
+    k = S.shape[0]
+    nrows = row1 - row0
+    if side == SIDE_AS:
+        e_bytes, o_bytes = nrows * 8, nrows * 8 * 2
+    else:
+        e_bytes, o_bytes = k * n, k * n * 2
+    rc = _lib.lwe_matmul_modq_rows(
+        side, _ptr(A_rows, torch.int16, max(nrows, 0) * n * 2, "A_rows"),
+        _ptr(seedA, torch.uint8, 16, "seedA"), _ptr(S, torch.int8, k * n, "S"), n, k, logq,
+        row0, row1, _ptr(E, torch.int8, e_bytes, "E"), _ptr(out, torch.int16, o_bytes, "out"),
+        _stream(stream))
+    _check(rc, "lwe_matmul_modq_rows")
 
 
 def kernel_names():
