@@ -130,6 +130,67 @@ LWE_DEV void sha3_256_global(const uint8_t *msg, uint32_t len, uint64_t s[25]) {
   keccak_f1600(s);
 }
 
+// Absorb (and permute) blocks j0 .. j1-1 of the padded SHA3-256 input of a
+// `len`-byte message at global address msg (8-byte aligned): block j holds
+// bytes [136 j, 136 j + 136); block len / 136, the last, holds the rest with
+// the padding.  sha3_256_global is sha3_init and then blocks 0 .. len / 136;
+// a sponge can so be advanced in pieces, by different threads in turn.
+LWE_DEV void sha3_absorb_global(const uint8_t *msg, uint32_t len, uint32_t j0, uint32_t j1,
+                                uint64_t s[25]) {
+  const uint64_t *p = reinterpret_cast<const uint64_t *>(msg);
+  const uint32_t full = len / SHA3_RATE;
+  for (uint32_t j = j0; j < j1; j++) {
+    const uint32_t off = j * SHA3_RATE;
+    if (j < full) {
+#pragma unroll
+      for (int i = 0; i < SHA3_RATE / 8; i++) s[i] ^= __ldg(p + off / 8 + i);
+    } else {
+      const uint32_t rem = len - off;
+#pragma unroll
+      for (int i = 0; i < SHA3_RATE / 8; i++) {
+        const uint32_t base = 8 * i;
+        uint64_t lane = 0;
+        if (base + 8 <= rem) {
+          lane = __ldg(p + off / 8 + i);
+        } else if (base < rem) {
+          for (uint32_t b = 0; b < rem - base; b++)
+            lane |= (uint64_t)msg[off + base + b] << (8 * b);
+        }
+        if (base <= rem && rem < base + 8) lane ^= (uint64_t)0x06 << (8 * (rem - base));
+        if (i == SHA3_RATE / 8 - 1) lane ^= 0x8000000000000000ull;
+        s[i] ^= lane;
+      }
+    }
+    keccak_f1600(s);
+  }
+}
+
+// The same for a message in shared or global memory read with generic
+// loads (len a multiple of 8).
+LWE_DEV void sha3_absorb_mem(const uint8_t *msg, uint32_t len, uint32_t j0, uint32_t j1,
+                             uint64_t s[25]) {
+  const uint64_t *p = reinterpret_cast<const uint64_t *>(msg);
+  const uint32_t full = len / SHA3_RATE;
+  for (uint32_t j = j0; j < j1; j++) {
+    const uint32_t off = j * SHA3_RATE;
+    if (j < full) {
+#pragma unroll
+      for (int i = 0; i < SHA3_RATE / 8; i++) s[i] ^= p[off / 8 + i];
+    } else {
+      const uint32_t rem = len - off;
+#pragma unroll
+      for (int i = 0; i < SHA3_RATE / 8; i++) {
+        const uint32_t base = 8 * i;
+        uint64_t lane = (base + 8 <= rem) ? p[off / 8 + i] : 0;
+        if (base == rem) lane ^= 0x06;
+        if (i == SHA3_RATE / 8 - 1) lane ^= 0x8000000000000000ull;
+        s[i] ^= lane;
+      }
+    }
+    keccak_f1600(s);
+  }
+}
+
 // SHA3-256 of `len` bytes at an 8-byte aligned address in shared or global
 // memory (generic loads; len a multiple of 8).
 LWE_DEV void sha3_256_mem(const uint8_t *msg, uint32_t len, uint64_t s[25]) {

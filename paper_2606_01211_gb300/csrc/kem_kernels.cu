@@ -1109,6 +1109,148 @@ __global__ void __launch_bounds__(TREE_MAX_THREADS) k_tree(TreeArgs a) {
   sha3_digest(s, a.out + 32 * (size_t)e);
 }
 
+// Tree hash of batches whose full-length leaves need 13 warps per CTA (one
+// CTA per SM; e.g. 4096 ciphertexts of n = 976: 27 per CTA, 405 leaves of
+// 8 permutations).  With one leaf per thread, 13 leaf warps put 4 warps on
+// one SM sub-partition (SMSP) and 3 on the others: the loaded one needs 32
+// warp-permutations where the others need 24, and the roots then run alone.
+// Here, 16 warps with fixed roles:
+//   - warps 0, 4, 8, 12 (SMSP 0) take the 128 leaves with the highest chunk
+//     indices and run only TB_SPLIT of their 8 permutations; their sponge
+//     states go to shared memory ([25][128] words);
+//   - the nine other leaf warps (3 per SMSP 1-3) take the remaining leaves
+//     whole;
+//   - helper warps 14 and 15 (SMSPs 2, 3) finish the leaves of SMSP 0, two
+//     warps' worth each, once those have stopped;
+//   - warp 13 (SMSP 1) hashes the short last chunk of every message, then
+//     the root: the root's first blocks absorb digests of low chunk indices,
+//     which all come from SMSPs 1-3, so they run while the helpers work;
+//     the rest of the root (and the Encaps key) follows the helpers.
+// Named barriers (fixed thread counts, every warp meets each of its
+// barriers exactly once): 1 leaf warps of SMSPs 1-3 -> warp 13 (320);
+// 2 warps 0, 4 -> helper 14 (96); 4 warps 8, 12 -> helper 15 (96);
+// 3 helpers -> warp 13 (96).
+#define TB_SPLIT 6
+#define TB_SLOTS 128
+
+LWE_DEV void bar_arrive(uint32_t id, uint32_t n) {
+  asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(n) : "memory");
+}
+LWE_DEV void bar_sync(uint32_t id, uint32_t n) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
+}
+
+__global__ void __launch_bounds__(512, 1) k_tree_bal(TreeArgs a) {
+  extern __shared__ uint64_t sm[];
+  pdl_trigger();
+  pdl_wait();
+  const uint32_t words = 4 * a.m + 1;
+  uint64_t *sdig = sm;                              // [ipc][4 m + 1]
+  uint64_t *shand = sm + (size_t)a.ipc * words;     // [25][TB_SLOTS]
+  const uint32_t e0 = blockIdx.x * a.ipc;
+  const uint32_t nmsg = min(a.ipc, a.count - e0);
+  const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t ML = a.ml;                         // full-length chunks per message
+  const uint32_t NL = nmsg * ML;
+  const uint32_t fullp = LWE_TREE_CHUNK / SHA3_RATE + 1;  // permutations per full chunk
+  uint64_t s[25];
+  auto msg_of = [&](uint32_t li) -> const uint8_t * {
+    const uint32_t e = e0 + li;
+    return a.msg_ptrs ? a.msg_ptrs[e] : a.msgs + (size_t)e * a.stride;
+  };
+  // leaf k (k < NL): chunk ML - 1 - k / nmsg of message k % nmsg, so the
+  // first TB_SLOTS leaves are the highest chunk indices
+  auto put_digest = [&](uint32_t li, uint32_t c) {
+    uint64_t *d = sdig + (size_t)li * words + 4 * c;
+    d[0] = s[0];
+    d[1] = s[1];
+    d[2] = s[2];
+    d[3] = s[3];
+  };
+  if (warp < 13 && (warp & 3) == 0) {
+    // SMSP 0: the first TB_SPLIT permutations of leaves 0 .. TB_SLOTS-1
+    const uint32_t k = 32 * (warp >> 2) + lane;
+    if (k < NL) {
+      const uint32_t li = k % nmsg, c = ML - 1 - k / nmsg;
+      sha3_init(s);
+      sha3_absorb_global(msg_of(li) + (size_t)c * LWE_TREE_CHUNK, LWE_TREE_CHUNK, 0, TB_SPLIT, s);
+#pragma unroll
+      for (int i = 0; i < 25; i++) shand[i * TB_SLOTS + k] = s[i];
+    }
+    __syncwarp();
+    bar_arrive(warp < 8 ? 2 : 4, 96);
+  } else if (warp < 13) {
+    // SMSPs 1-3: whole leaves TB_SLOTS ..
+    const uint32_t idx = warp - 1 - (warp >> 2);  // 0 .. 8
+    const uint32_t k = TB_SLOTS + 32 * idx + lane;
+    if (k < NL) {
+      const uint32_t li = k % nmsg, c = ML - 1 - k / nmsg;
+      sha3_init(s);
+      sha3_absorb_global(msg_of(li) + (size_t)c * LWE_TREE_CHUNK, LWE_TREE_CHUNK, 0, fullp, s);
+      put_digest(li, c);
+    }
+    __syncwarp();
+    bar_arrive(1, 320);
+  } else if (warp >= 14) {
+    // helpers: the last permutations of two SMSP-0 warps' leaves each
+    bar_sync(warp == 14 ? 2 : 4, 96);
+    for (uint32_t g = 0; g < 2; g++) {
+      const uint32_t k = 32 * (2 * (warp - 14) + g) + lane;
+      if (k < NL) {
+        const uint32_t li = k % nmsg, c = ML - 1 - k / nmsg;
+#pragma unroll
+        for (int i = 0; i < 25; i++) s[i] = shand[i * TB_SLOTS + k];
+        sha3_absorb_global(msg_of(li) + (size_t)c * LWE_TREE_CHUNK, LWE_TREE_CHUNK, TB_SPLIT,
+                           fullp, s);
+        put_digest(li, c);
+      }
+    }
+    __syncwarp();
+    bar_arrive(3, 96);
+  } else {
+    // warp 13: the short last chunks, then the roots (and Encaps' key)
+    const uint32_t li = lane;
+    const bool mine = li < nmsg;
+    if (mine && ML < a.m) {
+      const uint32_t c = a.m - 1, off = c * LWE_TREE_CHUNK, len = a.len - off;
+      sha3_init(s);
+      sha3_absorb_global(msg_of(li) + off, len, 0, len / SHA3_RATE + 1, s);
+      put_digest(li, c);
+    }
+    // root blocks whose digests all come from chunks below the lowest
+    // chunk index held by SMSP 0 are absorbed before the helpers finish
+    const uint32_t held = min((uint32_t)TB_SLOTS, NL);
+    const uint32_t cmin = held ? ML - 1 - (held - 1) / nmsg : a.m;
+    const uint32_t rlen = 32 * a.m, nb = rlen / SHA3_RATE + 1;
+    uint32_t early = 0;
+    while (early < nb && min(rlen - 1, SHA3_RATE * early + SHA3_RATE - 1) / 32 < cmin) early++;
+    __syncwarp();
+    bar_sync(1, 320);
+    const uint8_t *root = reinterpret_cast<const uint8_t *>(sdig + (size_t)li * words);
+    sha3_init(s);
+    if (mine) sha3_absorb_mem(root, rlen, 0, early, s);
+    __syncwarp();
+    bar_sync(3, 96);
+    if (mine) {
+      sha3_absorb_mem(root, rlen, early, nb, s);
+      const uint32_t e = e0 + li;
+      if (a.mode == TREE_DIGEST) {
+        sha3_digest(s, a.out + (size_t)e * a.out_stride);
+        if (a.out2) sha3_digest(s, a.out2 + (size_t)e * a.out2_stride);
+      } else {
+        // Encaps (Alg. 4): K = H(K' || H(c))
+        uint64_t lanes[SHA3_RATE / 8];
+        lanes_zero(lanes);
+        const uint64_t *kp = reinterpret_cast<const uint64_t *>(a.kprime + 32 * (size_t)e);
+        for (int i = 0; i < 4; i++) lanes[i] = kp[i];
+        for (int i = 0; i < 4; i++) lanes[4 + i] = s[i];
+        sha3_256_lanes(lanes, 64, s);
+        sha3_digest(s, a.out + 32 * (size_t)e);
+      }
+    }
+  }
+}
+
 // Tree hash with one Keccak state per warp (keccak_warp.cuh), for launches
 // of few messages, where one state per thread would leave the GPU idle
 // behind a chain of sequential permutations.  A thread-block cluster of Q
@@ -1509,6 +1651,24 @@ void launch_tree(TreeArgs &a, int num_sms, uint32_t warp_max, cudaStream_t st) {
     launch_k_cluster(k_tree_warp, a.count * q, 32 * w, (size_t)a.m * 32, st, q, a);
     return;
   }
+  const uint32_t sms = num_sms > 0 ? (uint32_t)num_sms : 1u;
+  {
+    // the balanced schedule of k_tree_bal: leaves of full length filling
+    // more than 12 and at most 13 warps per CTA, every message's short
+    // chunk and root on one warp
+    const uint32_t last = a.len - (a.m - 1) * LWE_TREE_CHUNK;
+    const uint32_t ml = a.m - (last < LWE_TREE_CHUNK ? 1u : 0u);
+    const uint32_t ipc = (a.count + sms - 1) / sms;
+    const uint32_t nl = ipc * ml;
+    const size_t smem = ((size_t)ipc * (4 * a.m + 1) + 25 * TB_SLOTS) * 8;
+    if (a.m >= 2 && nl > 12 * 32 && nl <= 13 * 32 && ipc <= 32 && smem <= 48 * 1024 &&
+        (a.count + ipc - 1) / ipc <= sms) {
+      a.ipc = ipc;
+      a.ml = ml;
+      launch_k(k_tree_bal, (a.count + ipc - 1) / ipc, 512, smem, st, a);
+      return;
+    }
+  }
   uint32_t t = 1;
   while (t < a.m && t < 256) t <<= 1;
   a.tpi = t;
@@ -1516,7 +1676,6 @@ void launch_tree(TreeArgs &a, int num_sms, uint32_t warp_max, cudaStream_t st) {
   uint32_t cap = TREE_MAX_THREADS / t;
   cap = std::min<uint32_t>(cap, (48u * 1024u) / (8u * words));
   cap = std::max<uint32_t>(cap, 1u);
-  const uint32_t sms = num_sms > 0 ? (uint32_t)num_sms : 1u;
   a.ipc = std::min<uint32_t>(cap, (a.count + sms - 1) / sms);
   if (a.ipc == 0) a.ipc = 1;
   const uint32_t threads = (a.ipc * t + 31) / 32 * 32;
