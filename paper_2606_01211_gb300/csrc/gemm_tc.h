@@ -50,6 +50,7 @@ struct GemmSaArgs {
   // running sums are uint32 mod q (partial_in / partial_out reinterpreted),
   // and there are no V columns.
   uint32_t oddq_q, oddq_m;
+  uint32_t tma_store;     // set by the launcher: B' leaves by bulk tensor stores
 };
 
 cudaError_t lwe_gemm_setup();
