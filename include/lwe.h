@@ -350,6 +350,17 @@ int lwe_selftest_bounded_wait(lwe_ctx *ctx, uint32_t limit_us, void *stream);
  * parameters or a NULL out. */
 int lwe_noise_table(const lwe_params *p, int8_t *out, void *stream);
 
+/* Bounds-checked debug build (no counterpart in the paper; a stand-in for
+ * a memory checker): liblwe_check.so, the same library compiled with
+ * LWE_CHECK_BOUNDS, makes every kernel test the index arithmetic of its
+ * memory accesses against the sizes it was given and skip, instead of make,
+ * an access that would leave its buffer.  This call synchronises the
+ * device and returns in *count the number of accesses skipped since the
+ * previous call (then clears it) and in *first_site an id of the first
+ * failing site (0 if none).  The product build (liblwe.so) has no checks
+ * and returns LWE_EUNSUPPORTED; LWE_EINVAL for NULL pointers. */
+int lwe_bounds_violations(uint64_t *count, uint32_t *first_site);
+
 /* Measurement probes (no counterpart in the paper): the instruction
  * sequences of the two integer-bound kernels without memory traffic, to
  * measure their practical peak on the current device.

@@ -80,6 +80,42 @@ inline cudaError_t launch_k_cluster(void (*k)(KArgs...), dim3 grid, dim3 block, 
 // Device-side error word values (set by bounded waits that ran out).
 #define LWE_DEVERR_TIMEOUT 1u
 
+// ---- bounds-checked debug build ------------------------------------------
+// Built with -DLWE_CHECK_BOUNDS (build_lib.build(check_bounds=True), the
+// library liblwe_check.so), the kernels test the index arithmetic of their
+// memory accesses against the sizes they were given: an access that would
+// leave its buffer is skipped instead of made, and counted in this
+// translation unit's counters with the id of the first failing site
+// (lwe_bounds_violations reads and clears them).  A stand-in for a memory
+// checker.  In the product build LWE_BOUNDS(cond, site) is `true` and costs
+// nothing.
+#ifdef LWE_CHECK_BOUNDS
+static __device__ unsigned long long g_bounds_bad;
+static __device__ unsigned int g_bounds_site;
+LWE_DEV bool lwe_in_bounds(bool ok, unsigned site) {
+  if (!ok && atomicAdd(&g_bounds_bad, 1ull) == 0ull) g_bounds_site = site;
+  return ok;
+}
+#define LWE_BOUNDS(cond, site) lwe_in_bounds((cond), (site))
+// host: read and clear this translation unit's counters
+#define LWE_BOUNDS_READER(fn)                                                          \
+  cudaError_t fn(unsigned long long *count, unsigned *site) {                          \
+    unsigned long long zero = 0;                                                       \
+    cudaError_t e = cudaMemcpyFromSymbol(count, g_bounds_bad, sizeof *count);          \
+    if (e == cudaSuccess) e = cudaMemcpyFromSymbol(site, g_bounds_site, sizeof *site); \
+    if (e == cudaSuccess) e = cudaMemcpyToSymbol(g_bounds_bad, &zero, sizeof zero);    \
+    return e;                                                                          \
+  }
+#else
+#define LWE_BOUNDS(cond, site) true
+#define LWE_BOUNDS_READER(fn)                                     \
+  cudaError_t fn(unsigned long long *count, unsigned *site) {     \
+    *count = 0;                                                   \
+    *site = 0;                                                    \
+    return cudaSuccess;                                           \
+  }
+#endif
+
 LWE_DEV uint32_t bswap32(uint32_t x) { return __byte_perm(x, 0, 0x0123); }
 
 LWE_DEV uint32_t rotl32(uint32_t x, int r) { return __funnelshift_l(x, x, r); }

@@ -71,17 +71,12 @@ struct Cfg2 {
   static constexpr int B_BYTES = BN2 * BK * 2;       // 16 KB: one limb
   static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
   static constexpr int TMEM_COLS = 2 * (2 * BN2);    // two accumulators
-  // B' staging for the bulk tensor stores: two halves of the CTA's 128 x
-  // 128 output tile, 128 rows of 64 uint16 each (128-byte swizzle)
-  static constexpr int STG_OFF = STAGES2 * STAGE_BYTES;
-  static constexpr int STG_HALF = BM * (BN2 / 2) * 2;  // 16 KB
-  static constexpr int BAR_OFF = STG_OFF + 2 * STG_HALF;
+  static constexpr int BAR_OFF = STAGES2 * STAGE_BYTES;
   static constexpr int SMEM = BAR_OFF + 256 + 1024;
   static constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) |
                                     ((uint32_t)(2 * BN2 / 8) << 17) |
                                     ((uint32_t)(2 * BM / 16) << 24);
 };
-static_assert(Cfg2::SMEM <= 232448, "the CTA-pair kernel's shared memory exceeds 227 KB");
 
 LWE_DEV uint32_t smem_u32(const void *p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -176,40 +171,6 @@ LWE_DEV void tma_load_3d_pair(uint32_t dst, const CUtensorMap *map, int c0, int 
       " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(dst),
       "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(bar)
       : "memory");
-}
-
-// Bulk tensor store of a shared-memory box (the output map's 128-byte
-// swizzled layout) to global coordinates {c0, c1, c2}; tracked by the
-// issuing thread's bulk async-group.
-LWE_DEV void tma_store_3d(const CUtensorMap *map, uint32_t src, int c0, int c1, int c2) {
-  asm volatile(
-      "cp.async.bulk.tensor.3d.global.shared::cta.bulk_group [%0, {%1, %2, %3}], [%4];" ::"l"(
-          reinterpret_cast<uint64_t>(map)),
-      "r"(c0), "r"(c1), "r"(c2), "r"(src)
-      : "memory");
-}
-LWE_DEV void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
-// the bulk stores of this thread have read their shared-memory sources
-LWE_DEV void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
-// ... and have completed their global writes
-LWE_DEV void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
-// generic-proxy shared-memory writes become visible to the async proxy
-LWE_DEV void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
-// named barrier over n threads that also ANDs a predicate across them
-LWE_DEV bool bar_red_and(uint32_t id, uint32_t n, bool v) {
-  uint32_t r;
-  asm volatile(
-      "{\n\t.reg .pred p, q;\n\t"
-      "setp.ne.u32 p, %1, 0;\n\t"
-      "bar.red.and.pred q, %2, %3, p;\n\t"
-      "selp.u32 %0, 1, 0, q;\n\t}"
-      : "=r"(r)
-      : "r"((uint32_t)v), "r"(id), "r"(n)
-      : "memory");
-  return r != 0;
-}
-LWE_DEV void bar_sync_n(uint32_t id, uint32_t n) {
-  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
 }
 
 LWE_DEV uint32_t cluster_rank() {
@@ -426,14 +387,9 @@ LWE_DEV void epilogue_tile_oddq(const GemmSaArgs &a, uint32_t row, uint32_t n0, 
 // column, tl the TMEM address of the first lo column of its lane quarter.
 // The received B' comes from ov when given (prefetched with the E'), else
 // it is loaded here one chunk ahead of its use.
-// With stg (B' columns of a final pass that writes), the 16-byte chunks of
-// this thread's row go to the staging box instead (local row lr, chunk j at
-// j ^ (lr % 8): the 128-byte swizzle of the output map), which one thread
-// later writes with a bulk tensor store.
 template <int CHUNKS, bool ODDQ = false>
 LWE_DEV void epilogue_tile(const GemmSaArgs &a, uint32_t row, uint32_t n0, uint32_t tl,
-                           uint32_t hi_off, const uint4 *ev, const uint4 *ov,
-                           uint8_t *stg = nullptr, uint32_t lr = 0) {
+                           uint32_t hi_off, const uint4 *ev, const uint4 *ov) {
   if (ODDQ) {
     epilogue_tile_oddq<CHUNKS>(a, row, n0, tl, hi_off, ev);
     return;
@@ -517,13 +473,7 @@ LWE_DEV void epilogue_tile(const GemmSaArgs &a, uint32_t row, uint32_t n0, uint3
           diff |= (o_cur0.x ^ w[0]) | (o_cur0.y ^ w[1]) | (o_cur0.z ^ w[2]) |
                   (o_cur0.w ^ w[3]) | (o_cur1.x ^ w[4]) | (o_cur1.y ^ w[5]) |
                   (o_cur1.z ^ w[6]) | (o_cur1.w ^ w[7]);
-        } else if (stg) {
-          uint8_t *srow = stg + 128 * lr;
-          *reinterpret_cast<uint4 *>(srow + 16 * ((2 * cc) ^ (lr & 7))) =
-              make_uint4(w[0], w[1], w[2], w[3]);
-          *reinterpret_cast<uint4 *>(srow + 16 * ((2 * cc + 1) ^ (lr & 7))) =
-              make_uint4(w[4], w[5], w[6], w[7]);
-        } else {
+        } else if (LWE_BOUNDS(row < a.rows && c + 16 <= a.n, 202)) {
           uint4 *o = reinterpret_cast<uint4 *>(obase + 2 * ((size_t)kk * a.n + c));
           o[0] = make_uint4(w[0], w[1], w[2], w[3]);
           o[1] = make_uint4(w[4], w[5], w[6], w[7]);
@@ -721,7 +671,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 template <bool ODDQ>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHREADS2, 1)
     k_gemm_sa2(const __grid_constant__ CUtensorMap tmS, const __grid_constant__ CUtensorMap tmL,
-               const __grid_constant__ CUtensorMap tmO, const GemmSaArgs a) {
+               const GemmSaArgs a) {
   using C = Cfg2;
   extern __shared__ uint8_t smem_raw[];
   uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
@@ -765,8 +715,6 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHREADS2, 1)
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmS)) : "memory");
     asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmL)) : "memory");
-    if (a.tma_store)
-      asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmO)) : "memory");
   }
   if (warp == 1) {  // one warp of each CTA of the pair allocates together
     asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
@@ -875,46 +823,21 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHREADS2, 1)
     // the next tile's E' / received B' are loaded while this tile drains
     uint4 ev[BN2 / 32], ov[BN2 / 16];
     uint32_t it = 0;
-    // B' of a writing final pass goes through the staging box of this
-    // half: the 4 warps of the half fill it, one thread stores it with a
-    // bulk tensor copy.  Named barriers 1 + half (staging free, and the
-    // half's vote on going on) and 3 + half (staging full), 128 threads.
-    const bool tstore = !ODDQ && a.tma_store;
-    uint8_t *stg = tstore ? smem + C::STG_OFF + half * C::STG_HALF : nullptr;
-    const bool issuer = q == 0 && lane == 0;
     if (cluster < num_tiles)
       epilogue_prefetch<BN2 / 32, ODDQ>(a, row_of(cluster), col_of(cluster), ev, ov);
     for (uint32_t tile = cluster; tile < num_tiles; tile += nclusters, ++it) {
       const uint32_t acc = it & 1, use = it >> 1;
-      bool ok = wait_bar_warp(tfull(acc), use & 1, abort_flag, a.dev_err);
-      if (tstore) {
-        if (issuer) bulk_wait_read();  // the previous tile's store has read the staging
-        __syncwarp();
-        ok = bar_red_and(1 + half, 128, ok);  // the same decision in all 4 warps of the half
-      }
-      if (!ok) break;
+      if (!wait_bar_warp(tfull(acc), use & 1, abort_flag, a.dev_err)) break;
       tc_fence_after();
       epilogue_tile<BN2 / 32, ODDQ>(a, row_of(tile), col_of(tile),
                               tmem_base + ((32 * q) << 16) + acc * (2 * BN2) + half * (BN2 / 2),
-                              BN2, ev, ov, stg, 32 * q + lane);
+                              BN2, ev, ov);
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive_cluster(peer_addr(tempty(acc), 0));
-      if (tstore) {
-        fence_proxy_async_smem();
-        __syncwarp();
-        bar_sync_n(3 + half, 128);
-        const uint32_t x = col_of(tile);
-        const uint32_t r0 = (tile / num_n) * 2 * BM + rank * BM;
-        if (issuer && x < a.n && r0 < a.rows) {
-          tma_store_3d(&tmO, smem_u32(stg), (int)x, 0, (int)(r0 / 8));
-          bulk_commit();
-        }
-      }
       const uint32_t next = tile + nclusters;
       if (next < num_tiles) epilogue_prefetch<BN2 / 32, ODDQ>(a, row_of(next), col_of(next), ev, ov);
     }
-    if (tstore && issuer) bulk_wait_all();
   }
   tc_fence_before();
   __syncthreads();
@@ -945,11 +868,16 @@ __global__ void k_selftest_wait(uint32_t *dev_err, uint64_t limit_ns) {
 
 PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
 
+}  // namespace
+
+LWE_BOUNDS_READER(lwe_bounds_read_gemm)
+
+namespace {
+
 bool make_map(CUtensorMap *m, const void *base, int rank, const cuuint64_t *dims,
-              const cuuint64_t *strides, const cuuint32_t *box,
-              CUtensorMapDataType type = CU_TENSOR_MAP_DATA_TYPE_BFLOAT16) {
+              const cuuint64_t *strides, const cuuint32_t *box) {
   cuuint32_t es[3] = {1, 1, 1};
-  CUresult r = g_encode(m, type, rank, const_cast<void *>(base), dims,
+  CUresult r = g_encode(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, rank, const_cast<void *>(base), dims,
                         strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
                         CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
@@ -977,9 +905,8 @@ int launch_bn(const GemmSaArgs &a, int num_sms, cudaStream_t st) {
   return LWE_OK;
 }
 
-int launch_pair(const GemmSaArgs &a_in, int num_sms, cudaStream_t st) {
-  GemmSaArgs a = a_in;
-  CUtensorMap tmS, tmL, tmO;
+int launch_pair(const GemmSaArgs &a, int num_sms, cudaStream_t st) {
+  CUtensorMap tmS, tmL;
   const cuuint64_t dS[2] = {a.n, a.rows};
   const cuuint64_t sS[1] = {2ull * a.n};
   const cuuint32_t bS[2] = {BK, BM};
@@ -988,26 +915,13 @@ int launch_pair(const GemmSaArgs &a_in, int num_sms, cudaStream_t st) {
   const cuuint32_t bL[3] = {BK, BN2, 1};
   if (!make_map(&tmS, a.S, 2, dS, sS, bS)) return LWE_ECUDA;
   if (!make_map(&tmL, a.limbs, 3, dL, sL, bL)) return LWE_ECUDA;
-  // the final pass that writes B' stores it by bulk tensor copies: the
-  // output viewed as [items][8 rows][n columns] uint16, item stride
-  // out_stride, boxes of 16 items x 8 rows x 64 columns (128-byte rows)
-  a.tma_store = 0;
-  tmO = tmS;
-  if (!a.oddq_q && !a.cmp && !a.partial_out && a.rows % 8 == 0 && a.out_stride % 16 == 0 &&
-      (reinterpret_cast<uintptr_t>(a.out) & 15) == 0) {
-    const cuuint64_t dO[3] = {a.n, 8, a.rows / 8};
-    const cuuint64_t sO[2] = {2ull * a.n, a.out_stride};
-    const cuuint32_t bO[3] = {BN2 / 2, 8, BM / 8};
-    if (!make_map(&tmO, a.out, 3, dO, sO, bO, CU_TENSOR_MAP_DATA_TYPE_UINT16)) return LWE_ECUDA;
-    a.tma_store = 1;
-  }
   const uint32_t tiles = ((a.rows + 2 * BM - 1) / (2 * BM)) * ((a.ncols + BN2 - 1) / BN2);
   const uint32_t pairs = (uint32_t)(num_sms / 2);
   const uint32_t clusters = tiles < pairs ? tiles : pairs;
   if (a.oddq_q)
-    launch_k(k_gemm_sa2<true>, 2 * clusters, NTHREADS2, Cfg2::SMEM, st, tmS, tmL, tmO, a);
+    launch_k(k_gemm_sa2<true>, 2 * clusters, NTHREADS2, Cfg2::SMEM, st, tmS, tmL, a);
   else
-    launch_k(k_gemm_sa2<false>, 2 * clusters, NTHREADS2, Cfg2::SMEM, st, tmS, tmL, tmO, a);
+    launch_k(k_gemm_sa2<false>, 2 * clusters, NTHREADS2, Cfg2::SMEM, st, tmS, tmL, a);
   return LWE_OK;
 }
 

@@ -50,7 +50,6 @@ struct GemmSaArgs {
   // running sums are uint32 mod q (partial_in / partial_out reinterpreted),
   // and there are no V columns.
   uint32_t oddq_q, oddq_m;
-  uint32_t tma_store;     // set by the launcher: B' leaves by bulk tensor stores
 };
 
 cudaError_t lwe_gemm_setup();
@@ -64,3 +63,5 @@ void launch_gemm_limbs(const GemmLimbArgs &a, int num_sms, cudaStream_t st);
 void launch_s_to_bf16(const int8_t *S, uint64_t count, uint16_t *out, int num_sms,
                       cudaStream_t st);
 void launch_selftest_wait(uint32_t *dev_err, uint64_t limit_ns, cudaStream_t st);
+// bounds-checked build: skipped accesses of the GEMM kernels (read and clear)
+cudaError_t lwe_bounds_read_gemm(unsigned long long *count, unsigned *site);

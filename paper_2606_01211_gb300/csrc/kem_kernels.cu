@@ -155,6 +155,7 @@ LWE_DEV void noise_runs(const NoiseArgs &a, const AesTab &tab, const char *smem,
   for (uint64_t run = gwarp; run < nruns; run += nwarps) {
     const uint32_t e = (uint32_t)(run / a.runs_per_item);
     uint32_t r = (uint32_t)(run % a.runs_per_item);
+    if (!LWE_BOUNDS(e < a.count, 108)) continue;
     uint32_t s = 0;
     while (s + 1 < a.nout && r >= a.out[s].runs) {
       r -= a.out[s].runs;
@@ -206,6 +207,8 @@ __global__ void __launch_bounds__(512, 1) k_noise(NoiseArgs a) {
              (uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5),
              (uint64_t)gridDim.x * (blockDim.x >> 5));
 }
+
+LWE_BOUNDS_READER(lwe_bounds_read_kem)
 
 // The sampler table exactly as k_noise builds and reads it, for all 65536
 // words: out[w] = the sample of word w (a check of the table against the
@@ -340,6 +343,7 @@ __global__ void __launch_bounds__(256) k_mul_as_rows(MulAsArgs a) {
   const int8_t *St = a.St + (size_t)e * a.st_stride;
   for (uint32_t task = blockIdx.x + gridDim.x * warp; task < tasks; task += gridDim.x * 8) {
   const uint32_t i0 = task * AS_ROWS;
+  if (!LWE_BOUNDS(i0 + AS_ROWS <= (a.rows ? a.rows : n), 109)) continue;
   const uint16_t *A0 = a.A + (size_t)e * a.a_stride + (size_t)i0 * n;
   int acc[AS_ROWS][8];
 #pragma unroll
@@ -603,7 +607,9 @@ __global__ void __launch_bounds__(256) k_sa(MulSaArgs a) {
 #pragma unroll
     for (int c = 0; c < 8; c++) acc[k][c] = 0;
   auto row_chunk = [&](uint32_t i) -> uint4 {
-    return jv ? ld_nc_u4(Aitem + (size_t)(i - r0) * n + j0) : make_uint4(0, 0, 0, 0);
+    return jv && LWE_BOUNDS(i >= r0 && i < (a.row1 ? a.row1 : n), 110)
+               ? ld_nc_u4(Aitem + (size_t)(i - r0) * n + j0)
+               : make_uint4(0, 0, 0, 0);
   };
   auto mac_pair = [&](const uint4 x0, const uint4 x1, const uint4 sp) {
     const uint32_t w0[4] = {x0.x, x0.y, x0.z, x0.w}, w1[4] = {x1.x, x1.y, x1.z, x1.w};
@@ -1081,6 +1087,7 @@ __global__ void __launch_bounds__(TREE_MAX_THREADS) k_tree(TreeArgs a) {
       uint64_t s[25];
       for (uint32_t c = lt; c < a.m; c += a.tpi) {
         const uint32_t off = c * LWE_TREE_CHUNK;
+        if (!LWE_BOUNDS(off < a.len, 106)) continue;
         sha3_256_global(msg + off, min((uint32_t)LWE_TREE_CHUNK, a.len - off), s);
         mine[4 * c] = s[0];
         mine[4 * c + 1] = s[1];
@@ -1161,6 +1168,7 @@ __global__ void __launch_bounds__(512, 1) k_tree_bal(TreeArgs a) {
   // leaf k (k < NL): chunk ML - 1 - k / nmsg of message k % nmsg, so the
   // first TB_SLOTS leaves are the highest chunk indices
   auto put_digest = [&](uint32_t li, uint32_t c) {
+    if (!LWE_BOUNDS(li < nmsg && c < a.m, 102)) return;
     uint64_t *d = sdig + (size_t)li * words + 4 * c;
     d[0] = s[0];
     d[1] = s[1];
@@ -1170,10 +1178,11 @@ __global__ void __launch_bounds__(512, 1) k_tree_bal(TreeArgs a) {
   if (warp < 13 && (warp & 3) == 0) {
     // SMSP 0: the first TB_SPLIT permutations of leaves 0 .. TB_SLOTS-1
     const uint32_t k = 32 * (warp >> 2) + lane;
-    if (k < NL) {
+    if (k < NL && LWE_BOUNDS(k < TB_SLOTS, 101)) {
       const uint32_t li = k % nmsg, c = ML - 1 - k / nmsg;
       sha3_init(s);
-      sha3_absorb_global(msg_of(li) + (size_t)c * LWE_TREE_CHUNK, LWE_TREE_CHUNK, 0, TB_SPLIT, s);
+      if (LWE_BOUNDS((c + 1) * LWE_TREE_CHUNK <= a.len, 103))
+        sha3_absorb_global(msg_of(li) + (size_t)c * LWE_TREE_CHUNK, LWE_TREE_CHUNK, 0, TB_SPLIT, s);
 #pragma unroll
       for (int i = 0; i < 25; i++) shand[i * TB_SLOTS + k] = s[i];
     }
@@ -1186,7 +1195,8 @@ __global__ void __launch_bounds__(512, 1) k_tree_bal(TreeArgs a) {
     if (k < NL) {
       const uint32_t li = k % nmsg, c = ML - 1 - k / nmsg;
       sha3_init(s);
-      sha3_absorb_global(msg_of(li) + (size_t)c * LWE_TREE_CHUNK, LWE_TREE_CHUNK, 0, fullp, s);
+      if (LWE_BOUNDS((c + 1) * LWE_TREE_CHUNK <= a.len, 103))
+        sha3_absorb_global(msg_of(li) + (size_t)c * LWE_TREE_CHUNK, LWE_TREE_CHUNK, 0, fullp, s);
       put_digest(li, c);
     }
     __syncwarp();
@@ -1196,7 +1206,7 @@ __global__ void __launch_bounds__(512, 1) k_tree_bal(TreeArgs a) {
     bar_sync(warp == 14 ? 2 : 4, 96);
     for (uint32_t g = 0; g < 2; g++) {
       const uint32_t k = 32 * (2 * (warp - 14) + g) + lane;
-      if (k < NL) {
+      if (k < NL && LWE_BOUNDS(k < TB_SLOTS, 104)) {
         const uint32_t li = k % nmsg, c = ML - 1 - k / nmsg;
 #pragma unroll
         for (int i = 0; i < 25; i++) s[i] = shand[i * TB_SLOTS + k];
@@ -1214,7 +1224,8 @@ __global__ void __launch_bounds__(512, 1) k_tree_bal(TreeArgs a) {
     if (mine && ML < a.m) {
       const uint32_t c = a.m - 1, off = c * LWE_TREE_CHUNK, len = a.len - off;
       sha3_init(s);
-      sha3_absorb_global(msg_of(li) + off, len, 0, len / SHA3_RATE + 1, s);
+      if (LWE_BOUNDS(off < a.len && len <= LWE_TREE_CHUNK, 105))
+        sha3_absorb_global(msg_of(li) + off, len, 0, len / SHA3_RATE + 1, s);
       put_digest(li, c);
     }
     // root blocks whose digests all come from chunks below the lowest

@@ -176,6 +176,8 @@ void launch_v_encode(const VEncArgs &a, uint32_t count, bool cmp, cudaStream_t s
 void launch_keygen_seeds(const KeygenSeedArgs &a, uint32_t warp_max, cudaStream_t st);
 void launch_derive(const DeriveArgs &a, uint32_t warp_max, cudaStream_t st);
 void launch_tree(TreeArgs &a, int num_sms, uint32_t warp_max, cudaStream_t st);
+// bounds-checked build: skipped accesses of this unit's kernels (read and clear)
+cudaError_t lwe_bounds_read_kem(unsigned long long *count, unsigned *site);
 // measurement probes: kind 0 Keccak-f in registers (256-thread CTAs),
 // kind 1 AES counter blocks with the shared-memory tables (512 threads)
 int launch_probe(int kind, uint32_t ctas, uint32_t iters, uint32_t *sink, cudaStream_t st);

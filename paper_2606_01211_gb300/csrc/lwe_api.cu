@@ -4,6 +4,7 @@
 // contexts and their device workspaces, and the order of kernel launches
 // that makes up KeyGen, Encaps and Decaps (Alg. 1, 4, 5 of the paper).
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <cmath>
@@ -35,6 +36,15 @@ int cuda_fail(cudaError_t e) {
   } while (0)
 
 bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
+
+// An NVTX range around each work-enqueuing entry point, named after it, so
+// that a timeline profiler shows which library call issued which kernels
+// (no cost beyond a function-pointer call when no profiler is attached).
+struct NvtxScope {
+  explicit NvtxScope(const char *name) { nvtxRangePushA(name); }
+  ~NvtxScope() { nvtxRangePop(); }
+};
+#define LWE_TRACE(name) NvtxScope _nvtx_scope(name)
 
 // ---- AES round table T0, from the S-box of FIPS-197 ---------------------
 // S(x) = affine(x^-1) with the inverse taken through log / antilog tables
@@ -739,6 +749,7 @@ int lwe_ctx_set_option(lwe_ctx *c, int option, int64_t value) {
 
 int lwe_keygen(lwe_ctx *c, const uint8_t *seeds, uint32_t count, uint8_t *pk, uint8_t *sk,
                uint16_t *A_out, void *stream) {
+  LWE_TRACE("lwe_keygen");
   if (!c) return LWE_EINVAL;
   if (count == 0) return LWE_OK;
   if (count > c->max_batch) return LWE_ECAPACITY;
@@ -791,6 +802,7 @@ int lwe_keygen(lwe_ctx *c, const uint8_t *seeds, uint32_t count, uint8_t *pk, ui
 
 int lwe_encaps(lwe_ctx *c, const uint8_t *pk, const uint16_t *A, const uint8_t *coins,
                uint32_t count, uint8_t *ct, uint8_t *K, void *stream) {
+  LWE_TRACE("lwe_encaps");
   if (!c) return LWE_EINVAL;
   if (count == 0) return LWE_OK;
   if (count > c->max_batch) return LWE_ECAPACITY;
@@ -835,6 +847,7 @@ int lwe_encaps(lwe_ctx *c, const uint8_t *pk, const uint16_t *A, const uint8_t *
 
 int lwe_decaps(lwe_ctx *c, const uint8_t *sk, const uint16_t *A, const uint8_t *ct,
                uint32_t count, uint8_t *K, void *stream) {
+  LWE_TRACE("lwe_decaps");
   if (!c) return LWE_EINVAL;
   if (count == 0) return LWE_OK;
   if (count > c->max_batch) return LWE_ECAPACITY;
@@ -884,6 +897,7 @@ int lwe_decaps(lwe_ctx *c, const uint8_t *sk, const uint16_t *A, const uint8_t *
 int lwe_encaps_multi(lwe_ctx *c, const uint8_t *const *pk_ptrs, const uint8_t *const *pkh_ptrs,
                      const uint16_t *const *A_ptrs, const uint8_t *coins, uint32_t count,
                      uint8_t *ct, uint8_t *K, void *stream) {
+  LWE_TRACE("lwe_encaps_multi");
   if (!c) return LWE_EINVAL;
   if (count == 0) return LWE_OK;
   if (count > c->max_batch) return LWE_ECAPACITY;
@@ -917,6 +931,7 @@ int lwe_encaps_multi(lwe_ctx *c, const uint8_t *const *pk_ptrs, const uint8_t *c
 
 int lwe_decaps_multi(lwe_ctx *c, const uint8_t *const *sk_ptrs, const uint16_t *const *A_ptrs,
                      const uint8_t *ct, uint32_t count, uint8_t *K, void *stream) {
+  LWE_TRACE("lwe_decaps_multi");
   if (!c) return LWE_EINVAL;
   if (count == 0) return LWE_OK;
   if (count > c->max_batch) return LWE_ECAPACITY;
@@ -954,6 +969,7 @@ int lwe_decaps_multi(lwe_ctx *c, const uint8_t *const *sk_ptrs, const uint16_t *
 
 int lwe_ctx_bind_key(lwe_ctx *c, const uint8_t *pk, const uint8_t *sk, const uint16_t *A,
                      void *stream) {
+  LWE_TRACE("lwe_ctx_bind_key");
   if (!c) return LWE_EINVAL;
   if (!pk && !sk) {
     c->bound = false;
@@ -986,6 +1002,7 @@ int lwe_ctx_bind_key(lwe_ctx *c, const uint8_t *pk, const uint8_t *sk, const uin
 
 int lwe_expand_A(const uint8_t *seedA, uint32_t n, uint32_t logq, uint16_t *A_out,
                  void *stream) {
+  LWE_TRACE("lwe_expand_A");
   if (!seedA || !A_out || !aligned16(A_out) || n < 16 || n > 65536 || (n % 16) || logq < 1 ||
       logq > 16)
     return LWE_EINVAL;
@@ -1000,6 +1017,7 @@ int lwe_expand_A(const uint8_t *seedA, uint32_t n, uint32_t logq, uint16_t *A_ou
 int lwe_matmul_modq(lwe_ctx *c, int side, const uint16_t *A, const uint8_t *seedA,
                     const int8_t *S, uint32_t n, uint32_t k, uint32_t logq, const int8_t *E,
                     uint16_t *out, void *stream) {
+  LWE_TRACE("lwe_matmul_modq");
   if (!S || !out || (!A && !seedA) || n < 16 || n > 65536 || (n % 16) || logq < 1 || logq > 16)
     return LWE_EINVAL;
   if (!aligned16(S) || !aligned16(out) || (A && !aligned16(A)) || (E && !aligned16(E)))
@@ -1083,6 +1101,7 @@ int lwe_matmul_modq(lwe_ctx *c, int side, const uint16_t *A, const uint8_t *seed
 int lwe_matmul_modq_rows(int side, const uint16_t *A_rows, const uint8_t *seedA,
                          const int8_t *S, uint32_t n, uint32_t k, uint32_t logq, uint32_t row0,
                          uint32_t row1, const int8_t *E, uint16_t *out, void *stream) {
+  LWE_TRACE("lwe_matmul_modq_rows");
   if (!S || !out || (!A_rows && !seedA) || n < 16 || n > 65536 || (n % 16) || logq < 1 ||
       logq > 16)
     return LWE_EINVAL;
@@ -1133,6 +1152,7 @@ int lwe_matmul_modq_rows(int side, const uint16_t *A_rows, const uint8_t *seedA,
 int lwe_encaps_noalloc(const lwe_params *p, const uint8_t *pk, const uint16_t *A,
                        const uint8_t *coins, uint32_t count, uint8_t *ct, uint8_t *K,
                        void *stream) {
+  LWE_TRACE("lwe_encaps_noalloc");
   if (params_check(p) != LWE_OK) return LWE_EINVAL;
   if (count == 0) return LWE_OK;
   if (!pk || !coins || !ct || !K || !aligned16(pk) || !aligned16(coins) || !aligned16(ct) ||
@@ -1188,6 +1208,7 @@ int lwe_encaps_noalloc(const lwe_params *p, const uint8_t *pk, const uint16_t *A
 }
 
 int lwe_noise_table(const lwe_params *p, int8_t *out, void *stream) {
+  LWE_TRACE("lwe_noise_table");
   if (params_check(p) != LWE_OK || !out) return LWE_EINVAL;
   int rc = current_device_setup(nullptr, nullptr);
   if (rc) return rc;
@@ -1198,6 +1219,24 @@ int lwe_noise_table(const lwe_params *p, int8_t *out, void *stream) {
   for (int i = 0; i < 16; i++) a.T[i] = T[i];
   launch_noise_table(a, out, (cudaStream_t)stream);
   return check_launch();
+}
+
+int lwe_bounds_violations(uint64_t *count, uint32_t *first_site) {
+#ifndef LWE_CHECK_BOUNDS
+  (void)count;
+  (void)first_site;
+  return LWE_EUNSUPPORTED;
+#else
+  if (!count || !first_site) return LWE_EINVAL;
+  CUDA_TRY(cudaDeviceSynchronize());
+  unsigned long long c1 = 0, c2 = 0;
+  unsigned s1 = 0, s2 = 0;
+  CUDA_TRY(lwe_bounds_read_kem(&c1, &s1));
+  CUDA_TRY(lwe_bounds_read_gemm(&c2, &s2));
+  *count = c1 + c2;
+  *first_site = c1 ? s1 : (c2 ? s2 : 0);
+  return LWE_OK;
+#endif
 }
 
 int lwe_probe(int kind, uint32_t ctas, uint32_t iters, uint32_t *sink, void *stream) {
@@ -1584,6 +1623,7 @@ int lwe_pp_ctx_set_option(lwe_pp_ctx *c, int option, int64_t value) {
 }
 
 int lwe_pp_expand_A(const lwe_pp_params *p, const uint8_t *seedA, uint32_t *A, void *stream) {
+  LWE_TRACE("lwe_pp_expand_A");
   if (lwe_pp_params_check(p) != LWE_OK || !seedA || !A || !aligned16(A)) return LWE_EINVAL;
   int sms = 0;
   int rc = current_device_setup(nullptr, &sms);
@@ -1594,6 +1634,7 @@ int lwe_pp_expand_A(const lwe_pp_params *p, const uint8_t *seedA, uint32_t *A, v
 
 int lwe_pp_keygen(lwe_pp_ctx *c, const uint8_t *seed32, uint8_t *pk, uint8_t *sk, uint32_t *A,
                   void *stream) {
+  LWE_TRACE("lwe_pp_keygen");
   if (!c || !seed32 || !pk || !sk || !A || !aligned16(pk) || !aligned16(sk) || !aligned16(A))
     return LWE_EINVAL;
   CUDA_TRY(cudaSetDevice(c->device));
@@ -1637,6 +1678,7 @@ int lwe_pp_keygen(lwe_pp_ctx *c, const uint8_t *seed32, uint8_t *pk, uint8_t *sk
 
 int lwe_pp_encaps(lwe_pp_ctx *c, const uint8_t *pk, const uint32_t *A, const uint8_t *coins32,
                   uint8_t *ct, uint8_t *K, void *stream) {
+  LWE_TRACE("lwe_pp_encaps");
   if (!c || !pk || !A || !coins32 || !ct || !K || !aligned16(pk) || !aligned16(A) ||
       !aligned16(ct))
     return LWE_EINVAL;
@@ -1656,6 +1698,7 @@ int lwe_pp_encaps(lwe_pp_ctx *c, const uint8_t *pk, const uint32_t *A, const uin
 
 int lwe_pp_decaps(lwe_pp_ctx *c, const uint8_t *sk, const uint32_t *A, const uint8_t *ct,
                   uint8_t *K, void *stream) {
+  LWE_TRACE("lwe_pp_decaps");
   if (!c || !sk || !A || !ct || !K || !aligned16(sk) || !aligned16(A) || !aligned16(ct))
     return LWE_EINVAL;
   CUDA_TRY(cudaSetDevice(c->device));

@@ -14,7 +14,11 @@ from dataclasses import dataclass
 
 import torch
 
-from .build_lib import LIB
+from .build_lib import LIB, LIB_CHECK
+
+# LWE_CHECK_BOUNDS=1 selects the bounds-checked debug build of the library
+# (build it first with build_lib.build(check_bounds=True))
+_LIB_PATH = LIB_CHECK if os.environ.get("LWE_CHECK_BOUNDS") == "1" else LIB
 
 # status codes (include/lwe.h)
 LWE_OK = 0
@@ -54,10 +58,10 @@ class _PpParams(C.Structure):
 
 
 def _load():
-    if not os.path.exists(LIB):
-        raise ImportError("liblwe.so is not built (run __graft_entry__.build() or "
-                          "python -m paper_2606_01211_gb300.build_lib)")
-    lib = C.CDLL(LIB)
+    if not os.path.exists(_LIB_PATH):
+        raise ImportError("%s is not built (run __graft_entry__.build() or "
+                          "python -m paper_2606_01211_gb300.build_lib)" % os.path.basename(_LIB_PATH))
+    lib = C.CDLL(_LIB_PATH)
     vp, u32, i32, sz = C.c_void_p, C.c_uint32, C.c_int, C.c_size_t
     P = C.POINTER(_Params)
     PP = C.POINTER(_PpParams)
@@ -84,6 +88,7 @@ def _load():
         "lwe_selftest_bounded_wait": (i32, [vp, u32, vp]),
         "lwe_probe": (i32, [i32, u32, u32, vp, vp]),
         "lwe_noise_table": (i32, [P, vp, vp]),
+        "lwe_bounds_violations": (i32, [C.POINTER(C.c_uint64), C.POINTER(C.c_uint32)]),
         "lwe_strerror": (C.c_char_p, [i32]),
         "lwe_last_cuda_error": (C.c_char_p, []),
         "lwe_ctx_device_error": (i32, [vp]),
@@ -392,6 +397,17 @@ def matmul_modq_rows(side: int, S: torch.Tensor, out: torch.Tensor, n: int, logq
         row0, row1, _ptr(E, torch.int8, e_bytes, "E"), _ptr(out, torch.int16, o_bytes, "out"),
         _stream(stream))
     _check(rc, "lwe_matmul_modq_rows")
+
+
+def bounds_violations():
+    """(skipped accesses, first site id) of the bounds-checked build since
+    the last call; None for the product build (no checks)."""
+    n, site = C.c_uint64(), C.c_uint32()
+    rc = _lib.lwe_bounds_violations(C.byref(n), C.byref(site))
+    if rc == LWE_EUNSUPPORTED:
+        return None
+    _check(rc, "lwe_bounds_violations")
+    return int(n.value), int(site.value)
 
 
 def kernel_names():

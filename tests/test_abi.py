@@ -90,5 +90,6 @@ def test_argument_errors_need_no_gpu():
     assert not h.value
     assert L.lwe_ctx_destroy(None) == lwe.LWE_OK
     assert L.lwe_strerror(lwe.LWE_ECAPACITY).decode().startswith("count exceeds")
+    assert lwe.bounds_violations() is None  # the product build has no checks
     names = lwe.kernel_names()
     assert "k_gemm_tc" in names and "k_noise" in names
