@@ -322,9 +322,10 @@ def algorithmic_bytes(p, count):
 # instruction-throughput bound measured against lwe_probe, not HBM or tensor
 LIMITER = {
     "k_noise": "shared-memory pipe: AES round-table lookups plus the sampler's table",
-    "k_tree": "integer ALU pipe: Keccak-f XORs, rotations and chi; at 4096 x P976 an SM's "
-              "13.5 leaf warps split 4/4/3/3 over its sub-partitions, then one warp hashes "
-              "the roots: 37 warp-permutations on the critical path against 29 of work",
+    "k_tree": "integer ALU pipe: Keccak-f XORs, rotations and chi; the balanced schedule "
+              "(k_tree_bal) hands SM sub-partition 0's leaves to helper warps after 6 of 8 "
+              "permutations and absorbs the roots in two stages: about 33 warp-permutations "
+              "on the critical path against 29 of work",
     "k_gemm_tc": "tensor pipe (bf16 tcgen05, CTA pairs)",
 }
 
@@ -541,36 +542,43 @@ def run_ours(args, rank, world, local_rank):
         return 0
 
     # roofline of the dominant kernel (largest share of the step): its
-    # algorithmic work over the direct-launch steps / its summed event time
+    # algorithmic work over the direct-launch steps / its summed event time;
+    # the same for each of the three large kernels in `rooflines`
     kernel_total = {k: v[1] for k, v in stats.items()}
     dom = max(kernel_total, key=kernel_total.get)
     alg = algorithmic(p, COUNT)
-    roof = None
-    if dom in alg:
-        bound, work, unit, scale = alg[dom]
-        nl, ms_tot = stats[dom]
+    probe = None
+    if any(alg[k][0] == "alu" for k in alg if k in stats):
+        probe = probe_peaks(torch, stream)
+
+    def roof_of(kern):
+        bound, work, unit, scale = alg[kern]
+        nl, ms_tot = stats[kern]
         ach = work * args.steps / (ms_tot / 1e3) / scale
         if bound == "tensor":
             peak = pk_d.get("bf16_tflops_sustained", pk_d["bf16_tflops"])
-        elif dom == "k_noise":
+        elif kern == "k_noise":
             peak = AES_RUN_PEAK_GBS
         else:
             peak = KECCAK_PEAK_GPERMS
-        probe = probe_peaks(torch, stream) if bound == "alu" else None
-        if probe is not None:
-            mp = probe["aes_run_gbs"] if dom == "k_noise" else probe["keccak_gperms"]
-            probe = {"peak": mp, "frac": ach / mp, "unit": unit,
-                     "how": "lwe_probe: the kernel's instruction sequence without memory traffic, "
-                            "best of 3 launches; 'peak' is the figure derived from unit counts "
-                            "at the maximum SM clock"}
-        roof = {"bound": bound, "achieved": ach, "peak": peak, "unit": unit, "frac": ach / peak,
-                "measured_peak": probe,
-                "kernel": dom, "launches_per_step": nl / args.steps,
-                "share": kernel_total[dom] / sum(kernel_total.values()),
-                "algorithmic_bytes": algorithmic_bytes(p, COUNT).get(dom, 0.0) / (nl / args.steps),
-                "traffic": traffic_per_launch(dom),
+        mp = None
+        if bound == "alu" and probe is not None:
+            m = probe["aes_run_gbs"] if kern == "k_noise" else probe["keccak_gperms"]
+            mp = {"peak": m, "frac": ach / m, "unit": unit,
+                  "how": "lwe_probe: the kernel's instruction sequence without memory traffic, "
+                         "best of 3 launches; 'peak' is the figure derived from unit counts "
+                         "at the maximum SM clock"}
+        return {"bound": bound, "achieved": ach, "peak": peak, "unit": unit, "frac": ach / peak,
+                "measured_peak": mp,
+                "kernel": kern, "launches_per_step": nl / args.steps,
+                "share": kernel_total[kern] / sum(kernel_total.values()),
+                "algorithmic_bytes": algorithmic_bytes(p, COUNT).get(kern, 0.0) / (nl / args.steps),
+                "traffic": traffic_per_launch(kern),
                 "timing": "CUDA events around each launch of direct-launch steps, one stream",
-                "limiter": LIMITER.get(dom)}
+                "limiter": LIMITER.get(kern)}
+
+    roof = roof_of(dom) if dom in alg else None
+    rooflines = {k: roof_of(k) for k in alg if k in stats}
 
     # the per-GPU extras (energy, plain path, serving, latency, sweeps, the
     # CPU baseline) are measured at N = 1; a multi-GPU run reports the
@@ -638,6 +646,7 @@ def run_ours(args, rank, world, local_rank):
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "gpu_launches": launches,
         "roofline": roof,
+        "rooflines": rooflines,
         "cpu_baseline": cpu,
         "e2e": e2e,
         "clocks": clocks,
