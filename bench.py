@@ -355,17 +355,18 @@ def algorithmic(p, count):
 CSRC = os.path.join(ROOT, "paper_2606_01211_gb300", "csrc")
 TRAFFIC = {
     # kernel: (bytes per step, launches per step, [(file, function or None)], fingerprint, profile)
-    "k_tree": (129.488640e6, 2,
-               [("kem_kernels.cu", "k_tree"), ("kem_kernels.cu", "launch_tree"), ("keccak.cuh", None)],
-               "67134a7a529e4ea2", "profiles/k_tree_p976.md"),
-    "k_gemm_tc": (302.244608e6, 2, [("gemm_tc.cu", None)], "0e969b386a26680a",
+    "k_tree": (129.323008e6, 2,
+               [("kem_kernels.cu", "k_tree_bal"), ("kem_kernels.cu", "launch_tree"),
+                ("keccak.cuh", None)],
+               "51c2a06934e9a66f", "profiles/k_tree_p976.md"),
+    "k_gemm_tc": (298.362880e6, 2, [("gemm_tc.cu", None)], "ea95752300b5b2b2",
                   "profiles/k_gemm_sa2_p976.md"),
-    "k_noise": (71.262208e6, 2,
+    "k_noise": (67.432704e6, 2,
                 [("kem_kernels.cu", "k_noise"), ("kem_kernels.cu", "noise_runs"),
                  ("kem_kernels.cu", "noise_store"),
                  ("kem_kernels.cu", "noise_fill_table"), ("kem_kernels.cu", "launch_noise"),
                  ("aes.cuh", None)],
-                "34e557ac11c6e4f2", "profiles/k_noise_p976.md"),
+                "79a6292fadc67436", "profiles/k_noise_p976.md"),
 }
 
 
