@@ -156,3 +156,40 @@ def test_kem_round_trip_and_implicit_rejection():
     bad = bytes(bad)
     z = sk[p.n:p.n + 32]
     assert pp.decaps(p, sk, bad, A) == hashlib.sha3_256(z + pp.hash_ct(p, bad)).digest()
+
+
+@pytest.mark.parametrize("q", [3329, 12289, 65537])
+def test_expand_A_stream_layout_vs_library_ctr(q):
+    """The counter-stream layout of A: entry (i, j) is little-endian 32-bit
+    word i n + j of the AES-128-CTR stream of domain 16 (initial counter
+    BE64(16) || BE64(0)), reduced mod q when below the acceptance bound;
+    the keystream comes from an independent AES library here."""
+    ciphers = pytest.importorskip("cryptography.hazmat.primitives.ciphers")
+    n = 48
+    p = pp.PParams(n=n, q=q, sigma=2.3, k=3, clip=10)
+    seed = bytes(range(100, 116))
+    iv = pp.A_DOMAIN.to_bytes(8, "big") + bytes(8)
+    ks = ciphers.Cipher(ciphers.algorithms.AES(seed), ciphers.modes.CTR(iv)).encryptor().update(
+        bytes(4 * n * n))
+    w = np.frombuffer(ks, dtype="<u4").astype(np.int64)
+    limit = q * ((1 << 32) // q)
+    assert (w < limit).all()  # no entry of this seed falls through to domain 17
+    assert np.array_equal(pp.expand_A(seed, p), (w % q).reshape(n, n))
+
+
+def test_noise_stream_layout_vs_library_ctr():
+    """The samplers' inputs: byte k (binomial s, domain 1) and little-endian
+    16-bit word k (Gaussian e, r, e1 and uniform e2, domains 2-5) of the
+    AES-128-CTR stream of their domain, taken from an independent AES
+    library here."""
+    ciphers = pytest.importorskip("cryptography.hazmat.primitives.ciphers")
+    key = bytes(range(7, 23))
+    for d in (1, 2, 3, 4, 5):
+        iv = d.to_bytes(8, "big") + bytes(8)
+        ks = ciphers.Cipher(ciphers.algorithms.AES(key), ciphers.modes.CTR(iv)).encryptor().update(
+            bytes(1000))
+        assert np.array_equal(pp._bytes(key, d, 999), np.frombuffer(ks, np.uint8)[:999])
+        assert np.array_equal(pp._words16(key, d, 499), np.frombuffer(ks, "<u2")[:499])
+        T = O.cdf_table(2.3, 10)
+        assert np.array_equal(pp.gaussian(key, d, 499, TINY),
+                              pp.gaussian_from_words(np.frombuffer(ks, "<u2")[:499], T, 10))
