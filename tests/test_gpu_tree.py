@@ -9,7 +9,7 @@ import numpy as np
 import pytest
 import torch
 
-from gpu_util import O, PRESETS, cfg_key, coins, dev, host, lwe, oracle_keys, params
+from gpu_util import O, PRESETS, cfg_key, coins, dev, host, lwe, master_seeds, oracle_keys, params
 
 pytestmark = pytest.mark.gpu
 
@@ -41,4 +41,58 @@ def test_batched_hashes_match_the_oracle(name, count):
     assert np.array_equal(K2_h, K2_o)
     assert np.array_equal(K2_h[0::2], K_h[0::2])      # untouched ciphertexts
     assert not (K2_h[1::2] == K_h[1::2]).all(axis=1).any()  # rejected ones
+    assert ctx.device_error() == 0
+
+
+def test_keygen_of_a_large_batch_hashes_every_pk():
+    """KeyGen of 4096 P976 key pairs: H(pk) of all of them in one batched
+    tree launch (the balanced schedule, digest mode, written into sk);
+    every digest equals the oracle's tree hash of the GPU's pk, and sampled
+    key pairs equal the oracle's in full."""
+    torch.cuda.set_device(0)
+    name, count = "P976", 4096
+    p, po = params(name)
+    ms = master_seeds(count, seed=77)
+    ctx = lwe.Ctx(p, max_batch=count)
+    pk, sk = ctx.empty_pk(count), ctx.empty_sk(count)
+    ctx.keygen(dev(ms), pk, sk)
+    pk_h, sk_h = host(pk), host(sk)
+    off = 8 * p.n + 32
+    for i in range(count):
+        assert sk_h[i, off:off + 32].tobytes() == O.htree(pk_h[i].tobytes()), i
+    for i in (0, 1, 2047, 4050, count - 1):   # 4050: the last, smaller CTA
+        pk_o, sk_o = O.keygen(po, bytes(ms[i]))
+        assert np.array_equal(pk_h[i], pk_o) and np.array_equal(sk_h[i], sk_o), i
+    assert ctx.device_error() == 0
+
+
+def test_multi_key_encaps_hashes_each_pk_in_one_batch():
+    """lwe_encaps_multi over 4096 items with per-item public keys and no
+    precomputed H(pk): the keys are hashed by pointer in one batched tree
+    launch (the balanced schedule); the results equal those of the same call
+    given each key's stored H(pk), and sampled items equal the oracle's."""
+    torch.cuda.set_device(0)
+    name, count, nk = "P976", 4096, 3
+    p, po = params(name)
+    ms = master_seeds(nk, seed=78)
+    ctx = lwe.Ctx(p, max_batch=count)
+    ctx.set_path(lwe.PATH_SKINNY)
+    pk, sk = ctx.empty_pk(nk), ctx.empty_sk(nk)
+    ctx.keygen(dev(ms), pk, sk)
+    keys = np.random.default_rng(79).integers(0, nk, size=count)
+    pk_ptrs = torch.tensor([pk[k].data_ptr() for k in keys], dtype=torch.int64, device="cuda")
+    pkh_ptrs = torch.tensor([sk[k].data_ptr() + 8 * p.n + 32 for k in keys], dtype=torch.int64,
+                            device="cuda")
+    cs = coins(count, seed=80)
+    out = []
+    for give in (None, pkh_ptrs):
+        ct = ctx.empty_ct(count)
+        K = torch.empty((count, 32), dtype=torch.uint8, device="cuda")
+        ctx.encaps_multi(pk_ptrs, dev(cs), ct, K, pkh_ptrs=give)
+        out.append((host(ct), host(K)))
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
+    for i in (0, 3000, count - 1):
+        pk_o, _ = O.keygen(po, bytes(ms[keys[i]]))
+        ct_o, K_o = O.encaps(po, pk_o, bytes(cs[i]))
+        assert np.array_equal(out[0][0][i], ct_o) and np.array_equal(out[0][1][i], K_o), i
     assert ctx.device_error() == 0
