@@ -622,6 +622,8 @@ def run_ours(args, rank, world, local_rank):
 
     served = serve_measure(torch) if extras and not args.no_serve else None
     latency = single_request_latency(lwe, torch, dev) if extras and not args.no_latency else None
+    latency_1344 = (single_request_latency(lwe, torch, dev, name="P1344")
+                    if extras and not args.no_latency else None)
     sweep = kernel_sweep(lwe, torch, dev, flush) if extras and not args.no_sweep else None
     large = large_n(lwe, torch, dev) if extras and not args.no_large else None
     ppr = paper_profile(lwe, torch, dev, cpu=not args.no_cpu) if extras and not args.no_pp else None
@@ -662,6 +664,7 @@ def run_ours(args, rank, world, local_rank):
         "energy": energy,
         "served": served,
         "latency_p640_us": latency,
+        "latency_p1344_us": latency_1344,
         "as_gbs": sweep["AS_stored"] if sweep else None,
         "kernel_sweep": sweep,
         "large_n": large,
@@ -762,10 +765,10 @@ def serve_measure(torch, rates=(1e3, 1e4, 1e5, 1e6), requests: int = 20000):
     return out
 
 
-def single_request_latency(lwe, torch, dev, reps: int = 300):
-    """One P640 KeyGen, Encaps, Decaps per call (stored A), host wall-clock
-    per call including the synchronisation: p50 / p99 in microseconds."""
-    p = lwe.Params(**PRESETS["P640"])
+def single_request_latency(lwe, torch, dev, reps: int = 300, name: str = "P640"):
+    """One KeyGen, Encaps, Decaps per call (stored A), host wall-clock per
+    call including the synchronisation: p50 / p99 in microseconds."""
+    p = lwe.Params(**PRESETS[name])
     ctx = lwe.Ctx(p, max_batch=1, device=dev.index)
     ctx.set_path(lwe.PATH_SKINNY)
     pk, sk = ctx.empty_pk(1), ctx.empty_sk(1)
