@@ -91,6 +91,19 @@ int lwe_pp_keygen(lwe_pp_ctx *ctx, const uint8_t *seed32, uint8_t *pk, uint8_t *
  * 32-byte key K. */
 int lwe_pp_encaps(lwe_pp_ctx *ctx, const uint8_t *pk, const uint32_t *A, const uint8_t *coins32,
                   uint8_t *ct, uint8_t *K, void *stream);
+/* Per-key precomputation for repeated calls against one key: H(pk) (Alg.
+ * 4 hashes pk in every Encaps) and, on the tensor path, the bf16 limb split
+ * of A (4 n^2 bytes read and written per call otherwise: 8 GiB of memory
+ * traffic at n = 32768).  Later lwe_pp_encaps calls with this pk pointer
+ * skip H(pk), and lwe_pp_encaps / lwe_pp_decaps calls with this A pointer
+ * skip the limb split; results are identical.  pk and A nullable (both NULL
+ * unbinds).  The binding refers to the buffers: their contents must not
+ * change while bound.  A call with another A overwrites the limbs and the
+ * next call with the bound A makes them again.  Order later calls after
+ * this call's work; allocates nothing.  LWE_EINVAL for a NULL context or
+ * misaligned pointers. */
+int lwe_pp_ctx_bind_key(lwe_pp_ctx *ctx, const uint8_t *pk, const uint32_t *A, void *stream);
+
 /* Decaps (Alg. 5): K = H(K' || H(c)) when the re-encryption reproduces ct,
  * else H(z || H(c)) (implicit rejection, not an error). */
 int lwe_pp_decaps(lwe_pp_ctx *ctx, const uint8_t *sk, const uint32_t *A, const uint8_t *ct,

@@ -1380,6 +1380,12 @@ struct lwe_pp_ctx {
   uint32_t *partial = nullptr; // K-split running sums, [256][n] mod q
   bool tensor = false;         // LWE_PP_OPT_TENSOR (set when the GEMM supports n)
   bool pdl = false;            // LWE_PP_OPT_PDL
+  // the key bound by lwe_pp_ctx_bind_key: its pk and A buffers, H(pk)
+  // (bpkh), and whether `limbs` still holds the limbs of its A
+  const uint8_t *bound_pk = nullptr;
+  const uint32_t *bound_A = nullptr;
+  uint8_t *bpkh = nullptr;
+  bool limbs_bound = false;
 };
 
 namespace {
@@ -1433,8 +1439,12 @@ int pp_encrypt(lwe_pp_ctx *c, const uint32_t *t, const uint32_t *A, uint8_t *ct,
   const uint32_t n = c->p.n;
   const ModQ M = modq(c->p.q);
   if (c->tensor) {
-    // U^T = R^T A + E1^T on the tensor cores
-    launch_pp_limbs(A, n, c->p.q, c->limbs, st);
+    // U^T = R^T A + E1^T on the tensor cores; the bound key's limbs are
+    // made once
+    if (!(A == c->bound_A && c->limbs_bound)) {
+      launch_pp_limbs(A, n, c->p.q, c->limbs, st);
+      c->limbs_bound = A == c->bound_A;
+    }
     launch_s_to_bf16(c->Rt, (uint64_t)PP_MBITS * n, c->Rbf, c->num_sms, st);
     GemmSaArgs ga;
     memset(&ga, 0, sizeof ga);
@@ -1547,6 +1557,7 @@ int lwe_pp_ctx_create(const lwe_pp_params *p, int device, lwe_pp_ctx **out) {
     return o;
   };
   const size_t o_seeds = carve(32), o_mu = carve(32), o_kp = carve(32), o_pkh = carve(32);
+  const size_t o_bpkh = carve(32);
   const size_t o_hc = carve(32), o_dig = carve(32 * (PP_MBITS + 1)), o_rk = carve(176);
   const size_t o_flags = carve(16), o_e = carve(n), o_Rt = carve(PP_MBITS * n);
   const size_t o_E1t = carve(PP_MBITS * n), o_e2 = carve(4 * PP_MBITS), o_err = carve(16);
@@ -1568,6 +1579,7 @@ int lwe_pp_ctx_create(const lwe_pp_params *p, int device, lwe_pp_ctx **out) {
   c->mu = c->ws + o_mu;
   c->kp = c->ws + o_kp;
   c->pkh = c->ws + o_pkh;
+  c->bpkh = c->ws + o_bpkh;
   c->hc = c->ws + o_hc;
   c->digests = c->ws + o_dig;
   c->rk = reinterpret_cast<uint32_t *>(c->ws + o_rk);
@@ -1686,14 +1698,41 @@ int lwe_pp_encaps(lwe_pp_ctx *c, const uint8_t *pk, const uint32_t *A, const uin
   cudaStream_t st = (cudaStream_t)stream;
   const lwe_pp_params &p = c->p;
   PdlOn pdl(c->pdl);
-  pp_tree(c, pk, pp_pk_bytes(p), (uint32_t)pp_pk_bytes(p), 1, TREE_DIGEST, c->pkh, 32, st);
+  const uint8_t *pkh = c->bpkh;  // the bound key's H(pk), made once
+  if (pk != c->bound_pk) {
+    pp_tree(c, pk, pp_pk_bytes(p), (uint32_t)pp_pk_bytes(p), 1, TREE_DIGEST, c->pkh, 32, st);
+    pkh = c->pkh;
+  }
   // m = H(0x4D || coins), K' = H(H(pk) || m), seedSE' and its key schedule
-  launch_derive(pp_derive_args(c, coins32, c->pkh), (uint32_t)c->num_sms, st);
+  launch_derive(pp_derive_args(c, coins32, pkh), (uint32_t)c->num_sms, st);
   pp_encrypt_noise(c, st);
   const int rc = pp_encrypt(c, reinterpret_cast<const uint32_t *>(pk + 16), A, ct, false, st);
   if (rc != LWE_OK) return rc;
   pp_hash_ct(c, ct, TREE_ENC_KEY, K, st);  // K = H(K' || H(c))
   return check_launch();
+}
+
+int lwe_pp_ctx_bind_key(lwe_pp_ctx *c, const uint8_t *pk, const uint32_t *A, void *stream) {
+  LWE_TRACE("lwe_pp_ctx_bind_key");
+  if (!c) return LWE_EINVAL;
+  c->bound_pk = nullptr;
+  c->bound_A = nullptr;
+  c->limbs_bound = false;
+  if (!pk && !A) return LWE_OK;
+  if ((pk && !aligned16(pk)) || (A && !aligned16(A))) return LWE_EINVAL;
+  CUDA_TRY(cudaSetDevice(c->device));
+  cudaStream_t st = (cudaStream_t)stream;
+  const lwe_pp_params &p = c->p;
+  if (pk) pp_tree(c, pk, pp_pk_bytes(p), (uint32_t)pp_pk_bytes(p), 1, TREE_DIGEST, c->bpkh, 32, st);
+  if (A && c->tensor) {
+    launch_pp_limbs(A, p.n, p.q, c->limbs, st);
+    c->limbs_bound = true;
+  }
+  const int rc = check_launch();
+  if (rc) return rc;
+  c->bound_pk = pk;
+  c->bound_A = A;
+  return LWE_OK;
 }
 
 int lwe_pp_decaps(lwe_pp_ctx *c, const uint8_t *sk, const uint32_t *A, const uint8_t *ct,

@@ -111,6 +111,7 @@ def _load():
         "lwe_pp_keygen": (i32, [vp, vp, vp, vp, vp, vp]),
         "lwe_pp_encaps": (i32, [vp, vp, vp, vp, vp, vp, vp]),
         "lwe_pp_decaps": (i32, [vp, vp, vp, vp, vp, vp]),
+        "lwe_pp_ctx_bind_key": (i32, [vp, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -484,6 +485,14 @@ class PpCtx:
 
     def set_option(self, option: int, value: int):
         _check(_lib.lwe_pp_ctx_set_option(self._h, option, int(value)), "lwe_pp_ctx_set_option")
+
+    def bind_key(self, pk=None, A=None, stream=None):
+        """Make H(pk) and A's limbs once for later calls with these buffers;
+        bind_key() unbinds."""
+        p = self.params
+        _check(_lib.lwe_pp_ctx_bind_key(self._h, _ptr(pk, torch.uint8, p.pk_bytes, "pk"),
+                                        _ptr(A, torch.int32, 4 * p.n * p.n, "A"),
+                                        _stream(stream)), "lwe_pp_ctx_bind_key")
 
     def empty_pk(self):
         return torch.empty(self.params.pk_bytes, dtype=torch.uint8, device="cuda")

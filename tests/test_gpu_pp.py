@@ -159,3 +159,34 @@ def test_round_trips_over_many_coins(name):
             ctx.decaps(sk, A, ct, K2)
             assert not torch.equal(K, K2), j
     ctx.close()
+
+
+@pytest.mark.parametrize("name", ["PP1024", "PP4096"])
+def test_bound_key_gives_the_same_results(name):
+    """lwe_pp_ctx_bind_key makes H(pk) and A's limbs once; bound calls equal
+    unbound ones, also after a call with another A overwrote the limbs."""
+    p, po = _params(name)
+    ctx = lwe.PpCtx(p)
+    keys = []
+    for s in (3, 4):
+        pk, sk, A = ctx.empty_pk(), ctx.empty_sk(), ctx.empty_A()
+        ctx.keygen(_dev(bytes([s]) * 32), pk, sk, A)
+        keys.append((pk, sk, A))
+    coins = _dev(bytes(range(60, 92)))
+
+    def run(pk, sk, A):
+        ct = ctx.empty_ct()
+        K = torch.empty(32, dtype=torch.uint8, device="cuda")
+        K2 = torch.empty_like(K)
+        ctx.encaps(pk, A, coins, ct, K)
+        ctx.decaps(sk, A, ct, K2)
+        return _host(ct), _host(K), _host(K2)
+
+    want = [run(*k) for k in keys]
+    ctx.bind_key(keys[0][0], keys[0][2])
+    for i in (0, 1, 0):
+        assert run(*keys[i]) == want[i], i
+    ctx.bind_key()
+    assert run(*keys[0]) == want[0]
+    assert want[0][1] == want[0][2]
+    ctx.close()
