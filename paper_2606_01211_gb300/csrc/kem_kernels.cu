@@ -1136,7 +1136,9 @@ __global__ void __launch_bounds__(TREE_MAX_THREADS) k_tree(TreeArgs a) {
 // Named barriers (fixed thread counts, every warp meets each of its
 // barriers exactly once): 1 leaf warps of SMSPs 1-3 -> warp 13 (320);
 // 2 warps 0, 4 -> helper 14 (96); 4 warps 8, 12 -> helper 15 (96);
-// 3 helpers -> warp 13 (96).
+// 3 helpers -> warp 13 (96).  At most 96 registers per thread (no spills):
+// a CTA then leaves room in the SM's register file for the CTAs of Decaps'
+// small kernels, which run beside its H(c) on the other stream.
 #define TB_SPLIT 6
 #define TB_SLOTS 128
 
@@ -1147,7 +1149,7 @@ LWE_DEV void bar_sync(uint32_t id, uint32_t n) {
   asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
 }
 
-__global__ void __launch_bounds__(512, 1) k_tree_bal(TreeArgs a) {
+__global__ void __maxnreg__(96) k_tree_bal(TreeArgs a) {
   extern __shared__ uint64_t sm[];
   pdl_trigger();
   pdl_wait();
