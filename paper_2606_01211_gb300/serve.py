@@ -95,6 +95,9 @@ class KeyStore:
         self.chunks, self.slot_at, self.slot_of, self.lru, self.free, self.last_use = \
             {}, {}, {}, {}, {}, {}
         self.ready = {}
+        # vectorised views for batches across keys: the slot of each key
+        # (-1: not cached) and the device address of each slot
+        self.slot_np, self.slot_ptr, self.ready_done = {}, {}, {}
         self.budget = cfg.a_budget_bytes
         self.reserve = cfg.reserve_bytes
         self.used = 0
@@ -115,6 +118,9 @@ class KeyStore:
             self.slot_of[n] = {}
             self.lru[n] = collections.OrderedDict()
             self.free[n], self.last_use[n], self.ready[n] = [], [], []
+            self.slot_np[n] = np.full(cfg.keys_per_n, -1, np.int64)
+            self.slot_ptr[n] = np.zeros(0, np.int64)
+            self.ready_done[n] = []
         if prefill:  # key k is the (k+1)-th most popular (Zipf rank)
             share = self._share()
             for n in self.params:
@@ -157,6 +163,9 @@ class KeyStore:
             self.slot_at[n].append(chunk[j])
             self.last_use[n].append(None)
             self.ready[n].append(None)
+            self.ready_done[n].append(False)
+        self.slot_ptr[n] = np.concatenate(
+            [self.slot_ptr[n], chunk.data_ptr() + 2 * n * n * np.arange(per, dtype=np.int64)])
         self.free[n].extend(range(base + per - 1, base - 1, -1))
         self.used += nbytes
         self.grows += 1
@@ -171,6 +180,7 @@ class KeyStore:
         else:
             old, s = self.lru[n].popitem(last=False)
             del self.slot_of[n][old]
+            self.slot_np[n][old] = -1
             if self.last_use[n][s] is not None:
                 stream.wait_event(self.last_use[n][s])
         with torch.cuda.stream(stream):
@@ -179,9 +189,22 @@ class KeyStore:
             ev = torch.cuda.Event()
             ev.record(stream)
         self.ready[n][s] = ev
+        self.ready_done[n][s] = False
         self.slot_of[n][key] = s
+        self.slot_np[n][key] = s
         self.lru[n][key] = s
         return s
+
+    def _wait_ready(self, n, s, stream):
+        """Order `stream` after the fill of slot s, until that fill is seen
+        complete (then no wait is needed any more)."""
+        if self.ready_done[n][s]:
+            return
+        ev = self.ready[n][s]
+        if ev.query():
+            self.ready_done[n][s] = True
+        else:
+            stream.wait_event(ev)
 
     def cached(self, n: int, key: int) -> bool:
         return key in self.slot_of[n]
@@ -194,7 +217,7 @@ class KeyStore:
         if s is not None:
             self.lru[n].move_to_end(key)
             self.hits += 1
-            stream.wait_event(self.ready[n][s])  # filled, possibly on another stream
+            self._wait_ready(n, s, stream)  # filled, possibly on another stream
             return self.slot_at[n][s]
         self.misses += 1
         if not admit:
@@ -202,12 +225,27 @@ class KeyStore:
         s = self._fill(n, key, stream)
         return None if s is None else self.slot_at[n][s]
 
+    def cached_slots(self, n: int, keys: np.ndarray) -> np.ndarray:
+        """The slot of each key of a batch (-1: not cached)."""
+        return self.slot_np[n][keys]
+
+    def A_ptrs(self, n: int, keys: np.ndarray, stream: torch.cuda.Stream) -> np.ndarray:
+        """Device addresses of the cached A of keys that are all cached:
+        each distinct key's LRU order refreshed once, each distinct slot's
+        fill ordered before `stream` once."""
+        slots = self.slot_np[n][keys]
+        for k in np.unique(keys).tolist():
+            self.lru[n].move_to_end(k)
+        for sl in np.unique(slots).tolist():
+            self._wait_ready(n, sl, stream)
+        self.hits += len(keys)
+        return self.slot_ptr[n][slots]
+
     def used_by(self, n: int, keys, event: torch.cuda.Event):
         """Record the batch that reads these keys' cached A."""
-        for k in keys:
-            s = self.slot_of[n].get(int(k))
-            if s is not None:
-                self.last_use[n][s] = event
+        slots = self.slot_np[n][np.asarray(list(keys), dtype=np.int64)]
+        for sl in np.unique(slots[slots >= 0]).tolist():
+            self.last_use[n][sl] = event
 
 
 class Slot:
@@ -345,15 +383,15 @@ class Engine:
             else:
                 # across keys: items whose A is cached, then the others (A
                 # regenerated); a few misses are admitted to the cache
-                keys = np.array([q.key for q in group], dtype=np.int64)
-                cached = np.array([self.store.cached(n, int(k)) for k in keys], dtype=bool)
+                keys = np.fromiter((q.key for q in group), dtype=np.int64, count=cnt)
+                cached = self.store.cached_slots(n, keys) >= 0
                 admitted = 0
-                for k in np.unique(keys[~cached]):
+                for k in np.unique(keys[~cached]).tolist():
                     if admitted >= self.ADMIT:
                         break
-                    if self.store.A(n, int(k), st) is not None:
+                    if self.store.A(n, k, st) is not None:
                         admitted += 1
-                cached = np.array([self.store.cached(n, int(k)) for k in keys], dtype=bool)
+                cached = self.store.cached_slots(n, keys) >= 0
                 order = np.concatenate([np.nonzero(cached)[0], np.nonzero(~cached)[0]])
                 keys = keys[order]
                 rows_o = rows[torch.from_numpy(order)]
@@ -364,8 +402,8 @@ class Engine:
                 hp[0, :cnt] = self._key_ptrs(n, keys, what)
                 if op == "encaps":
                     hp[1, :cnt] = self._key_ptrs(n, keys, "pkh")
-                for i in range(nst):
-                    hp[2, i] = self.store.A(n, int(keys[i]), st).data_ptr()
+                if nst:
+                    hp[2, :nst] = self.store.A_ptrs(n, keys[:nst], st)
                 slot.d_ptr.copy_(slot.h_ptr, non_blocking=True)
                 if op == "encaps":
                     torch.index_select(P["coins"], 0, rows_d, out=B["coins"][:cnt])
