@@ -797,6 +797,22 @@ def single_request_latency(lwe, torch, dev, reps: int = 300, name: str = "P640")
             t["decaps"].append(t3 - t2)
             t["cycle"].append(t3 - t0)
     assert torch.equal(K, K2)
+    # the same Encaps / Decaps against a key bound once (H(pk) not redone)
+    t["encaps_bound"], t["decaps_bound"] = [], []
+    ctx.bind_key(pk, sk, A)
+    torch.cuda.synchronize()
+    for i in range(reps):
+        t1 = time.perf_counter()
+        ctx.encaps(pk, cs[i:i + 1], ct, K, A=A)
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
+        ctx.decaps(sk, ct, K2, A=A)
+        torch.cuda.synchronize()
+        t3 = time.perf_counter()
+        if i >= 20:
+            t["encaps_bound"].append(t2 - t1)
+            t["decaps_bound"].append(t3 - t2)
+    assert torch.equal(K, K2)
     ctx.close()
     return {k: {"p50": float(np.percentile(v, 50) * 1e6), "p99": float(np.percentile(v, 99) * 1e6)}
             for k, v in t.items()}
