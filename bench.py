@@ -355,10 +355,10 @@ def algorithmic(p, count):
 CSRC = os.path.join(ROOT, "paper_2606_01211_gb300", "csrc")
 TRAFFIC = {
     # kernel: (bytes per step, launches per step, [(file, function or None)], fingerprint, profile)
-    "k_tree": (129.299456e6, 2,
+    "k_tree": (129.291776e6, 2,
                [("kem_kernels.cu", "k_tree_bal"), ("kem_kernels.cu", "launch_tree"),
                 ("keccak.cuh", None)],
-               "f8dd97dc415c0bb0", "profiles/k_tree_p976.md"),
+               "646bfdc17c4dccf0", "profiles/k_tree_p976.md"),
     "k_gemm_tc": (298.362880e6, 2, [("gemm_tc.cu", None)], "ea95752300b5b2b2",
                   "profiles/k_gemm_sa2_p976.md"),
     "k_noise": (67.432704e6, 2,

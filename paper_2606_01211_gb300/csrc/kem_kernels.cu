@@ -1169,13 +1169,13 @@ __global__ void __maxnreg__(96) k_tree_bal(TreeArgs a) {
   };
   // leaf k (k < NL): chunk ML - 1 - k / nmsg of message k % nmsg, so the
   // first TB_SLOTS leaves are the highest chunk indices
-  auto put_digest = [&](uint32_t li, uint32_t c) {
+  auto put_digest = [&](uint32_t li, uint32_t c, const uint64_t *st) {
     if (!LWE_BOUNDS(li < nmsg && c < a.m, 102)) return;
     uint64_t *d = sdig + (size_t)li * words + 4 * c;
-    d[0] = s[0];
-    d[1] = s[1];
-    d[2] = s[2];
-    d[3] = s[3];
+    d[0] = st[0];
+    d[1] = st[1];
+    d[2] = st[2];
+    d[3] = st[3];
   };
   if (warp < 13 && (warp & 3) == 0) {
     // SMSP 0: the first TB_SPLIT permutations of leaves 0 .. TB_SLOTS-1
@@ -1199,7 +1199,7 @@ __global__ void __maxnreg__(96) k_tree_bal(TreeArgs a) {
       sha3_init(s);
       if (LWE_BOUNDS((c + 1) * LWE_TREE_CHUNK <= a.len, 103))
         sha3_absorb_global(msg_of(li) + (size_t)c * LWE_TREE_CHUNK, LWE_TREE_CHUNK, 0, fullp, s);
-      put_digest(li, c);
+      put_digest(li, c, s);
     }
     __syncwarp();
     bar_arrive(1, 320);
@@ -1214,7 +1214,7 @@ __global__ void __maxnreg__(96) k_tree_bal(TreeArgs a) {
         for (int i = 0; i < 25; i++) s[i] = shand[i * TB_SLOTS + k];
         sha3_absorb_global(msg_of(li) + (size_t)c * LWE_TREE_CHUNK, LWE_TREE_CHUNK, TB_SPLIT,
                            fullp, s);
-        put_digest(li, c);
+        put_digest(li, c, s);
       }
     }
     __syncwarp();
@@ -1228,7 +1228,7 @@ __global__ void __maxnreg__(96) k_tree_bal(TreeArgs a) {
       sha3_init(s);
       if (LWE_BOUNDS(off < a.len && len <= LWE_TREE_CHUNK, 105))
         sha3_absorb_global(msg_of(li) + off, len, 0, len / SHA3_RATE + 1, s);
-      put_digest(li, c);
+      put_digest(li, c, s);
     }
     // root blocks whose digests all come from chunks below the lowest
     // chunk index held by SMSP 0 are absorbed before the helpers finish
@@ -1261,6 +1261,85 @@ __global__ void __maxnreg__(96) k_tree_bal(TreeArgs a) {
         sha3_digest(s, a.out + 32 * (size_t)e);
       }
     }
+  }
+}
+
+// Tree hash of batches whose full-length leaves fill at most 12 warps per
+// CTA (e.g. 4096 ciphertexts of n = 640: 27 per SM, 270 leaves): the leaves
+// are packed densely, leaf k on warp k / 32 of warps 0-11, so consecutive
+// warps fall on consecutive SM sub-partitions and every SMSP holds
+// floor or ceil of WL / 4 leaf warps (k_tree instead gives each message a
+// power-of-two group of threads, which leaves lanes idle).  The short last
+// chunks and then the roots (and Encaps' key) run on one warp of the SMSP
+// with the fewest leaf warps, `rw`.  One named barrier: the twelve leaf
+// warps (whether or not they hold leaves) -> the root warp (416 threads).
+__global__ void __maxnreg__(96) k_tree_dense(TreeArgs a) {
+  extern __shared__ uint64_t sm[];
+  pdl_trigger();
+  pdl_wait();
+  const uint32_t words = 4 * a.m + 1;
+  uint64_t *sdig = sm;  // [ipc][4 m + 1]
+  const uint32_t e0 = blockIdx.x * a.ipc;
+  const uint32_t nmsg = min(a.ipc, a.count - e0);
+  const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t ML = a.ml, NL = nmsg * ML;
+  const uint32_t fullp = LWE_TREE_CHUNK / SHA3_RATE + 1;
+  uint64_t s[25];
+  auto msg_of = [&](uint32_t li) -> const uint8_t * {
+    const uint32_t e = e0 + li;
+    return a.msg_ptrs ? a.msg_ptrs[e] : a.msgs + (size_t)e * a.stride;
+  };
+  auto put_digest = [&](uint32_t li, uint32_t c, const uint64_t *st) {
+    if (!LWE_BOUNDS(li < nmsg && c < a.m, 111)) return;
+    uint64_t *d = sdig + (size_t)li * words + 4 * c;
+    d[0] = st[0];
+    d[1] = st[1];
+    d[2] = st[2];
+    d[3] = st[3];
+  };
+  if (warp < 12) {
+    const uint32_t k = 32 * warp + lane;  // leaf k: chunk k % ML of message k / ML
+    if (k < NL) {
+      const uint32_t li = k / ML, c = k % ML;
+      sha3_init(s);
+      if (LWE_BOUNDS((c + 1) * LWE_TREE_CHUNK <= a.len, 112))
+        sha3_absorb_global(msg_of(li) + (size_t)c * LWE_TREE_CHUNK, LWE_TREE_CHUNK, 0, fullp, s);
+      put_digest(li, c, s);
+    }
+    __syncwarp();
+    bar_arrive(1, 416);
+    return;
+  }
+  if (warp != a.rw) return;
+  const uint32_t li = lane;
+  const bool mine = li < nmsg;
+  if (mine && ML < a.m) {
+    const uint32_t c = a.m - 1, off = c * LWE_TREE_CHUNK, len = a.len - off;
+    sha3_init(s);
+    if (LWE_BOUNDS(off < a.len && len <= LWE_TREE_CHUNK, 113))
+      sha3_absorb_global(msg_of(li) + off, len, 0, len / SHA3_RATE + 1, s);
+    put_digest(li, c, s);
+  }
+  __syncwarp();
+  bar_sync(1, 416);
+  if (!mine) return;
+  const uint32_t rlen = 32 * a.m;
+  sha3_init(s);
+  sha3_absorb_mem(reinterpret_cast<const uint8_t *>(sdig + (size_t)li * words), rlen, 0,
+                  rlen / SHA3_RATE + 1, s);
+  const uint32_t e = e0 + li;
+  if (a.mode == TREE_DIGEST) {
+    sha3_digest(s, a.out + (size_t)e * a.out_stride);
+    if (a.out2) sha3_digest(s, a.out2 + (size_t)e * a.out2_stride);
+  } else {
+    // Encaps (Alg. 4): K = H(K' || H(c))
+    uint64_t lanes[SHA3_RATE / 8];
+    lanes_zero(lanes);
+    const uint64_t *kp = reinterpret_cast<const uint64_t *>(a.kprime + 32 * (size_t)e);
+    for (int i = 0; i < 4; i++) lanes[i] = kp[i];
+    for (int i = 0; i < 4; i++) lanes[4 + i] = s[i];
+    sha3_256_lanes(lanes, 64, s);
+    sha3_digest(s, a.out + 32 * (size_t)e);
   }
 }
 
@@ -1679,6 +1758,26 @@ void launch_tree(TreeArgs &a, int num_sms, uint32_t warp_max, cudaStream_t st) {
       a.ipc = ipc;
       a.ml = ml;
       launch_k(k_tree_bal, (a.count + ipc - 1) / ipc, 512, smem, st, a);
+      return;
+    }
+    // leaves of at most 12 warps: dense packing, roots on the least loaded
+    // SMSP (warp 12 + s of SMSP s)
+    const size_t smem_d = (size_t)ipc * (4 * a.m + 1) * 8;
+    if (a.m >= 2 && ml >= 1 && nl <= 12 * 32 && ipc <= 32 && smem_d <= 48 * 1024 &&
+        (a.count + ipc - 1) / ipc <= sms) {
+      const uint32_t wl = (nl + 31) / 32;
+      uint32_t best = 3, load_best = 99;
+      for (int sp = 3; sp >= 0; sp--) {
+        const uint32_t load = wl > (uint32_t)sp ? (wl - 1 - sp) / 4 + 1 : 0;  // leaf warps on SMSP sp
+        if (load < load_best) {
+          load_best = load;
+          best = (uint32_t)sp;
+        }
+      }
+      a.ipc = ipc;
+      a.ml = ml;
+      a.rw = 12 + best;
+      launch_k(k_tree_dense, (a.count + ipc - 1) / ipc, 512, smem_d, st, a);
       return;
     }
   }

@@ -139,7 +139,8 @@ struct TreeArgs {
   uint32_t m;            // leaves per message
   uint32_t tpi;          // threads per message (power of two <= 256)
   uint32_t ipc;          // messages per CTA
-  uint32_t ml;           // full-length (1024-byte) chunks per message (k_tree_bal)
+  uint32_t ml;           // full-length (1024-byte) chunks per message (k_tree_bal, k_tree_dense)
+  uint32_t rw;           // k_tree_dense: the warp of the short chunks and roots
   int mode;
   uint8_t *out;
   uint64_t out_stride;

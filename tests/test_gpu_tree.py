@@ -1,10 +1,15 @@
 """The batched tree hash (H(c) in Encaps and Decaps, and the Encaps key)
 under each of its launch schedules, against the oracle over whole batches:
-the balanced schedule (k_tree_bal: leaves that fill 13 warps per SM, handed
-between SM sub-partitions, roots absorbed in two stages) at P976 with 26
-and 27 ciphertexts per SM (3801 and 4104 items, the last CTA ragged) and at
-P1344 (2800 items), and the one-leaf-per-thread schedule (k_tree) just
-outside that range (3800 items at P976, and P640)."""
+- the balanced schedule (k_tree_bal: leaves that fill 13 warps per SM,
+  handed between SM sub-partitions, roots absorbed in two stages) at P976
+  with 26 and 27 ciphertexts per SM (3801 and 4104 items, the last CTA
+  ragged) and at P1344 (2800 items);
+- the dense schedule (k_tree_dense: leaves of at most 12 warps packed one
+  per thread, roots on the least loaded sub-partition) at P976 with 25, 14
+  and 2 ciphertexts per SM (3800: 12 leaf warps; 2048; 300: one leaf warp)
+  and at P640 (4096: 9 leaf warps);
+- the one-leaf-per-thread schedule (k_tree) beyond both: P1344 with 27
+  ciphertexts per SM (567 leaves) and P640 with 40 per SM."""
 import numpy as np
 import pytest
 import torch
@@ -15,7 +20,8 @@ pytestmark = pytest.mark.gpu
 
 
 @pytest.mark.parametrize("name,count", [("P976", 3801), ("P976", 4104), ("P1344", 2800),
-                                        ("P976", 3800), ("P640", 4096)])
+                                        ("P976", 3800), ("P640", 4096), ("P976", 2048),
+                                        ("P976", 300), ("P1344", 4096), ("P640", 6000)])
 def test_batched_hashes_match_the_oracle(name, count):
     torch.cuda.set_device(0)
     cfg = PRESETS[name]
