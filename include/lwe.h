@@ -154,11 +154,21 @@ enum {
                                 latency), larger ones with one state per
                                 thread (higher throughput).  -1 (default):
                                 the number of SMs; 0: always per thread   */
-  LWE_OPT_PDL = 8            /* 1 (default): the kernels of Encaps / Decaps
+  LWE_OPT_PDL = 8,           /* 1 (default): the kernels of Encaps / Decaps
                                 are launched with programmatic stream
                                 serialisation (each may start while the
                                 previous one drains, and waits on the
                                 device for its results); 0: plain launches */
+  LWE_OPT_GEMM_GROUP = 9     /* tensor-core GEMM tile order: the persistent
+                                CTAs visit output tiles in groups of this
+                                many row blocks of S' (the row block varies
+                                fastest inside a group), 1..64; 1 is plain
+                                row-major order.  0 (default): 1 while one
+                                pass's [A | B] limbs fit in 32 MB (they stay
+                                in L2), else 8 (each limb tile is then read
+                                from HBM once per 8 row blocks instead of
+                                once per row block).  Results never depend
+                                on it. */
 };
 int lwe_ctx_set_option(lwe_ctx *ctx, int option, int64_t value);
 

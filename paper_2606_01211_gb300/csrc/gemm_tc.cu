@@ -509,6 +509,23 @@ LWE_DEV void epilogue_tile(const GemmSaArgs &a, uint32_t row, uint32_t n0, uint3
   }
 }
 
+// Tile order.  Tiles are visited in groups of g M-blocks (g = a.group_m):
+// inside a group the M-block varies fastest, so the tiles that the
+// persistent CTAs hold at one time share g row slabs of S' and about
+// (CTAs / g) limb slabs of [A | B].  With g = 1 this is the row-major order
+// (all column tiles of one M-block, then the next), which suits an [A | B]
+// that stays in L2; for a large n (limb slabs of several MB per pass) it
+// would re-stream every limb slab from HBM once per M-block.
+LWE_DEV void tile_mn(uint32_t tile, uint32_t num_m, uint32_t num_n, uint32_t g, uint32_t &tm,
+                     uint32_t &tn) {
+  g = g ? g : 1;
+  const uint32_t per = g * num_n;
+  const uint32_t m_first = (tile / per) * g, idx = tile % per;
+  const uint32_t gm = min(g, num_m - m_first);
+  tm = m_first + idx % gm;
+  tn = idx / gm;
+}
+
 template <int BN, bool ODDQ>
 __global__ void __launch_bounds__(NTHREADS, 1)
     k_gemm_sa(const __grid_constant__ CUtensorMap tmS, const __grid_constant__ CUtensorMap tmL,
@@ -573,8 +590,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     uint32_t last_phase = 0;  // bit s: phase of stage s's last load
     bool ok = true;
     for (uint32_t tile = blockIdx.x; ok && tile < num_tiles; tile += gridDim.x) {
-      const int m0 = (int)((tile / num_n) * BM);
-      const int n0 = (int)((tile % num_n) * BN);
+      uint32_t tm, tn;
+      tile_mn(tile, num_m, num_n, a.group_m, tm, tn);
+      const int m0 = (int)(tm * BM);
+      const int n0 = (int)(tn * BN);
       for (uint32_t kb = 0; kb < KB; kb++) {
         if (!wait_bar(empty(stage), phase ^ 1, abort_flag, a.dev_err)) {
           ok = false;
@@ -642,7 +661,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     uint32_t it = 0;
     for (uint32_t tile = blockIdx.x; tile < num_tiles; tile += gridDim.x, ++it) {
       const uint32_t acc = it & 1, use = it >> 1;
-      const uint32_t m0 = (tile / num_n) * BM, n0 = (tile % num_n) * BN;
+      uint32_t tm, tn;
+      tile_mn(tile, num_m, num_n, a.group_m, tm, tn);
+      const uint32_t m0 = tm * BM, n0 = tn * BN;
       const uint32_t row = m0 + 32 * q + lane;
       uint4 ev[BN / 16];
       epilogue_prefetch<BN / 16, ODDQ>(a, row, n0, ev, nullptr);
@@ -736,9 +757,10 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHREADS2, 1)
     uint32_t armed = 0, last_phase = 0;  // leader: stages with a phase in flight
     bool ok = true;
     for (uint32_t tile = cluster; ok && tile < num_tiles; tile += nclusters) {
-      const uint32_t tm = tile / num_n;
+      uint32_t tm, tn;
+      tile_mn(tile, num_m, num_n, a.group_m, tm, tn);
       const int m0 = (int)(tm * 2 * BM + rank * BM);
-      const int n0 = (int)((tile % num_n) * BN2);
+      const int n0 = (int)(tn * BN2);
       // a tail tile whose second half has no rows: the peer loads no S'
       // (its accumulator rows are never stored) but still its limb tile
       const bool peer_rows = tm * 2 * BM + BM < a.rows;
@@ -818,8 +840,16 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHREADS2, 1)
     const uint32_t q = warp & 3;  // TMEM lane quarter of this warp
     const uint32_t half = (warp - 2) >> 2;  // which 64 of the tile's 128 columns
     // this thread's row and first column in a tile
-    auto row_of = [&](uint32_t t) { return (t / num_n) * 2 * BM + rank * BM + 32 * q + lane; };
-    auto col_of = [&](uint32_t t) { return (t % num_n) * BN2 + half * (BN2 / 2); };
+    auto row_of = [&](uint32_t t) {
+      uint32_t tm, tn;
+      tile_mn(t, num_m, num_n, a.group_m, tm, tn);
+      return tm * 2 * BM + rank * BM + 32 * q + lane;
+    };
+    auto col_of = [&](uint32_t t) {
+      uint32_t tm, tn;
+      tile_mn(t, num_m, num_n, a.group_m, tm, tn);
+      return tn * BN2 + half * (BN2 / 2);
+    };
     // the next tile's E' / received B' are loaded while this tile drains
     uint4 ev[BN2 / 32], ov[BN2 / 16];
     uint32_t it = 0;
@@ -985,6 +1015,10 @@ int launch_gemm_sa(const GemmSaArgs &a, int num_sms, cudaStream_t st) {
     b.partial_out = p + 1 < passes ? a.partial_out : nullptr;
     // |partial sums| <= K c 128 (zero-filled K tail included)
     b.fast_fold = (uint64_t)b.kblocks * BK * a.clip * 128u < (1u << 22) ? 1 : 0;
+    // tile order: group the row blocks once this pass's limbs (2 limbs x 2
+    // bytes x ncols x K) outgrow a quarter of L2
+    if (!b.group_m)
+      b.group_m = 4ull * a.ncols * (uint64_t)b.kblocks * BK > (32ull << 20) ? 8u : 1u;
     const int rc = a.pair && num_sms >= 2 ? launch_pair(b, num_sms, st)
                    : a.bn == 64           ? launch_bn<64>(b, num_sms, st)
                                           : launch_bn<128>(b, num_sms, st);

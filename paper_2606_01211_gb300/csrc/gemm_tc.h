@@ -33,6 +33,8 @@ struct GemmSaArgs {
   int cmp;                // 0: write out; 1: compare with out
   int bn;                 // output columns per tile: 64 or 128
   int pair;               // 1: CTA-pair kernel (256 x 128 tiles, cta_group::2)
+  uint32_t group_m;       // tile order: M-blocks per group, M fastest inside
+                          // a group (0 or 1: row-major tiles)
   // K-split: this launch contracts K = [k0, k0 + 64 * kblocks) only.  The
   // partial sum of earlier passes (mod 2^16, [rows][ncols]) is added from
   // partial_in when set; a non-final pass writes its running sum to

@@ -167,6 +167,7 @@ struct lwe_ctx {
   int tensor_min = 64;
   int gemm_bn = 128;
   int gemm_pair = 1;
+  uint32_t gemm_group = 0;  // LWE_OPT_GEMM_GROUP; 0: chosen per launch
   bool serial = false;  // LWE_OPT_SERIAL: side-stream work on the caller's stream
   bool pdl = true;      // LWE_OPT_PDL
   int64_t tree_warp_max = -1;  // LWE_OPT_WARP_HASH_MAX; -1: the number of SMs
@@ -418,6 +419,7 @@ int run_encrypt(lwe_ctx *c, const uint8_t *pk, const uint16_t *A, uint32_t count
     ga.cmp = cmp ? 1 : 0;
     ga.bn = c->gemm_bn;
     ga.pair = c->gemm_pair;
+    ga.group_m = c->gemm_group;
     ga.clip = c->p.clip;
     ga.kchunk = c->kchunk;
     ga.partial_out = c->partial;
@@ -728,6 +730,10 @@ int lwe_ctx_set_option(lwe_ctx *c, int option, int64_t value) {
     case LWE_OPT_PDL:
       if (value != 0 && value != 1) return LWE_EINVAL;
       c->pdl = value != 0;
+      return LWE_OK;
+    case LWE_OPT_GEMM_GROUP:
+      if (value < 0 || value > 64) return LWE_EINVAL;
+      c->gemm_group = (uint32_t)value;
       return LWE_OK;
     case LWE_OPT_WARP_HASH_MAX:
       if (value < -1 || value > 0xffffffffLL) return LWE_EINVAL;
@@ -1075,6 +1081,7 @@ int lwe_matmul_modq(lwe_ctx *c, int side, const uint16_t *A, const uint8_t *seed
     ga.cmp = 0;
     ga.bn = c->gemm_bn;
     ga.pair = c->gemm_pair;
+    ga.group_m = c->gemm_group;
     ga.clip = c->p.clip;
     ga.kchunk = c->kchunk;
     ga.partial_out = c->partial;

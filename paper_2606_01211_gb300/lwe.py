@@ -32,7 +32,7 @@ LWE_NOALLOC_SCRATCH_BYTES = 1024 * 1024  # the built-in scratch of lwe_encaps_no
 
 PATH_AUTO, PATH_SKINNY, PATH_TENSOR = 0, 1, 2
 (OPT_PATH, OPT_TENSOR_MIN, OPT_TIMING, OPT_GEMM_BN, OPT_GEMM_KCHUNK, OPT_GEMM_PAIR,
- OPT_SERIAL, OPT_WARP_HASH_MAX, OPT_PDL) = 0, 1, 2, 3, 4, 5, 6, 7, 8
+ OPT_SERIAL, OPT_WARP_HASH_MAX, OPT_PDL, OPT_GEMM_GROUP) = 0, 1, 2, 3, 4, 5, 6, 7, 8, 9
 SIDE_AS, SIDE_SA = 0, 1
 PRESET_IDS = {"P640": 0, "P976": 1, "P1344": 2, "P4096": 3, "P16384": 4, "P32768": 5}
 

@@ -166,3 +166,36 @@ def test_serial_option_gives_the_same_results():
     for a, b in zip(*out):
         assert np.array_equal(a, b)
     assert np.array_equal(out[0][1], out[0][2])
+
+
+@pytest.mark.parametrize("pair", [1, 0])
+@pytest.mark.parametrize("group", [0, 1, 3, 8, 64])
+def test_tile_group_order_matches_oracle(pair, group):
+    """LWE_OPT_GEMM_GROUP changes only the order in which the persistent
+    CTAs visit the output tiles: 800 rows (4 CTA-pair row blocks, the last
+    with rows for one CTA only; 7 single-CTA blocks) x 976 columns (a ragged
+    last column tile), groups that divide the row blocks, that leave a
+    ragged last group, and that exceed them."""
+    n, items = 976, 100
+    k = 8 * items
+    r = np.random.default_rng(group + 101 * pair)
+    seed = r.integers(0, 256, 16, dtype=np.uint8)
+    A_o = O.expand_A(bytes(seed), n, 16)
+    S = r.integers(-10, 11, size=(k, n), dtype=np.int8)
+    E = r.integers(-10, 11, size=(k, n), dtype=np.int8)
+    ctx = lwe.Ctx(lwe.Params(**PRESETS["P976"]), max_batch=items)
+    ctx.set_path(lwe.PATH_TENSOR)
+    ctx.set_option(lwe.OPT_GEMM_PAIR, pair)
+    ctx.set_option(lwe.OPT_GEMM_GROUP, group)
+    out = torch.empty((k, n), dtype=torch.int16, device="cuda")
+    lwe.matmul_modq(lwe.SIDE_SA, dev(S), out, n, 16, A=dev(A_o.view(np.int16)), E=dev(E), ctx=ctx)
+    assert np.array_equal(as_u16(out), O.mul_SA(S, A_o, E, 16))
+    assert ctx.device_error() == 0
+
+
+def test_tile_group_option_range():
+    ctx = lwe.Ctx(lwe.Params(**PRESETS["P640"]), max_batch=8)
+    for bad in (-1, 65):
+        with pytest.raises(RuntimeError):
+            ctx.set_option(lwe.OPT_GEMM_GROUP, bad)
+    ctx.set_option(lwe.OPT_GEMM_GROUP, 0)
