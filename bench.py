@@ -355,13 +355,13 @@ def algorithmic(p, count):
 CSRC = os.path.join(ROOT, "paper_2606_01211_gb300", "csrc")
 TRAFFIC = {
     # kernel: (bytes per step, launches per step, [(file, function or None)], fingerprint, profile)
-    "k_tree": (129.291776e6, 2,
+    "k_tree": (129.321728e6, 2,
                [("kem_kernels.cu", "k_tree_bal"), ("kem_kernels.cu", "launch_tree"),
                 ("keccak.cuh", None)],
-               "646bfdc17c4dccf0", "profiles/k_tree_p976.md"),
-    "k_gemm_tc": (298.362880e6, 2, [("gemm_tc.cu", None)], "ea95752300b5b2b2",
+               "61a10e1e45bb906c", "profiles/k_tree_p976.md"),
+    "k_gemm_tc": (298.596352e6, 2, [("gemm_tc.cu", None)], "6d8cef265f3a54e8",
                   "profiles/k_gemm_sa2_p976.md"),
-    "k_noise": (67.432704e6, 2,
+    "k_noise": (67.690240e6, 2,
                 [("kem_kernels.cu", "k_noise"), ("kem_kernels.cu", "noise_runs"),
                  ("kem_kernels.cu", "noise_store"),
                  ("kem_kernels.cu", "noise_fill_table"), ("kem_kernels.cu", "launch_noise"),
@@ -625,7 +625,7 @@ def run_ours(args, rank, world, local_rank):
     latency_1344 = (single_request_latency(lwe, torch, dev, name="P1344")
                     if extras and not args.no_latency else None)
     sweep = kernel_sweep(lwe, torch, dev, flush) if extras and not args.no_sweep else None
-    large = large_n(lwe, torch, dev) if extras and not args.no_large else None
+    large = large_n(lwe, torch, dev, batch=args.large_batch) if extras and not args.no_large else None
     ppr = paper_profile(lwe, torch, dev, cpu=not args.no_cpu) if extras and not args.no_pp else None
 
     cpu = None
@@ -924,7 +924,7 @@ def paper_profile(lwe, torch, dev, cpu: bool = True,
     return res
 
 
-def large_n(lwe, torch, dev, batch: int = 1024):
+def large_n(lwe, torch, dev, batch: int = 1024, names=("P16384", "P32768")):
     """n = 16384 and 32768 (A = 0.5 / 2 GiB): one KeyGen, Encaps and Decaps
     per call with A stored in HBM vs regenerated tile by tile inside the
     kernels (CUDA-core path), and Encaps of `batch` items against one key
@@ -932,7 +932,7 @@ def large_n(lwe, torch, dev, batch: int = 1024):
     (median of 3); the batched figure also as Encaps/s."""
     stream = torch.cuda.current_stream()
     res = {}
-    for name in ("P16384", "P32768"):
+    for name in names:
         p = lwe.Params(**PRESETS[name])
         n = p.n
         ctx = lwe.Ctx(p, max_batch=batch, device=dev.index)
@@ -958,6 +958,8 @@ def large_n(lwe, torch, dev, batch: int = 1024):
         t = _event_ms(torch, stream, lambda: ctx.encaps(pk, cs, ct, K, A=A), reps=3)
         r["encaps_batched_%d_stored" % batch] = t
         r["encaps_batched_per_s"] = batch / (t / 1e3)
+        r["encaps_batched_kernels"] = batched_kernels(lwe, torch, ctx, n, batch,
+                                                      lambda: ctx.encaps(pk, cs, ct, K, A=A))
         ctx.decaps(sk, ct, K2, A=A)
         torch.cuda.synchronize()
         assert torch.equal(K, K2)
@@ -968,6 +970,32 @@ def large_n(lwe, torch, dev, batch: int = 1024):
         torch.cuda.empty_cache()
     res["unit"] = "ms per call"
     return res
+
+
+def batched_kernels(lwe, torch, ctx, n, batch, call):
+    """Per-kernel split of one batched call (CUDA events around each launch,
+    side-stream work on the caller's stream) and the rate of its tensor-core
+    GEMM: 2 limbs x 2 flops x (8 batch) rows x (n + 8) columns x n, over the
+    GEMM's K-split launches, against the bf16 burst peak (MEASURED_PEAKS.json,
+    else the fallback figure)."""
+    ctx.set_option(lwe.OPT_TIMING, 1)
+    ctx.set_option(lwe.OPT_SERIAL, 1)
+    ctx.reset_stats()
+    call()
+    torch.cuda.synchronize()
+    ks = ctx.kernel_stats()
+    ctx.set_option(lwe.OPT_TIMING, 0)
+    ctx.set_option(lwe.OPT_SERIAL, 0)
+    out = {"ms": {k: round(v[1], 4) for k, v in ks.items()},
+           "launches": {k: v[0] for k, v in ks.items()}}
+    g = ks.get("k_gemm_tc")
+    if g and g[1] > 0:
+        tflops = 4.0 * 8 * batch * (n + 8) * n / (g[1] * 1e-3) / 1e12
+        pk, how = peaks()
+        out["gemm_tflops"] = tflops
+        out["gemm_frac_of_bf16_burst"] = tflops / pk["bf16_tflops"]
+        out["peak_source"] = how
+    return out
 
 
 def row_split_times(lwe, torch, stream, A, n, worlds=(2, 4)):
@@ -1014,6 +1042,10 @@ def main():
     ap.add_argument("--no-pp", action="store_true")
     ap.add_argument("--sweep-only", type=str, default=None, metavar="N[,N...]",
                     help="only the standalone kernel sweep at these n (prints its JSON, not the bench line)")
+    ap.add_argument("--large-only", type=str, default=None, metavar="NAME[,NAME...]",
+                    help="only the large-n section for these presets (prints its JSON, not the bench line)")
+    ap.add_argument("--large-batch", type=int, default=1024,
+                    help="Encaps per batched call in the large-n section")
     ap.add_argument("--cpu-s", type=float, default=12.0)
     ap.add_argument("--ref-step-s", type=float, default=None,
                     help="CPU seconds per reference step (default: about 150 s in all)")
@@ -1026,6 +1058,14 @@ def main():
         flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.int32, device=dev)
         sizes = tuple(int(x) for x in args.sweep_only.split(","))
         print(json.dumps(kernel_sweep(lwe, torch, dev, flush, sizes=sizes)))
+        return 0
+    if args.large_only:
+        import torch
+        from paper_2606_01211_gb300 import lwe
+        dev = torch.device("cuda", 0)
+        torch.cuda.set_device(dev)
+        names = tuple(args.large_only.split(","))
+        print(json.dumps(large_n(lwe, torch, dev, batch=args.large_batch, names=names)))
         return 0
 
     world = int(os.environ.get("WORLD_SIZE", "1"))

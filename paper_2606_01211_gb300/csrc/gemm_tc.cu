@@ -518,7 +518,11 @@ LWE_DEV void epilogue_tile(const GemmSaArgs &a, uint32_t row, uint32_t n0, uint3
 // would re-stream every limb slab from HBM once per M-block.
 LWE_DEV void tile_mn(uint32_t tile, uint32_t num_m, uint32_t num_n, uint32_t g, uint32_t &tm,
                      uint32_t &tn) {
-  g = g ? g : 1;
+  if (g <= 1) {
+    tm = tile / num_n;
+    tn = tile - tm * num_n;
+    return;
+  }
   const uint32_t per = g * num_n;
   const uint32_t m_first = (tile / per) * g, idx = tile % per;
   const uint32_t gm = min(g, num_m - m_first);
@@ -839,34 +843,37 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHREADS2, 1)
     // ---------------- epilogue (both CTAs) ----------------
     const uint32_t q = warp & 3;  // TMEM lane quarter of this warp
     const uint32_t half = (warp - 2) >> 2;  // which 64 of the tile's 128 columns
-    // this thread's row and first column in a tile
-    auto row_of = [&](uint32_t t) {
+    // this thread's row and first column in tile t, worked out once per
+    // tile (before its accumulator is ready) and kept for its drain
+    uint32_t row = 0, col = 0;
+    auto coords = [&](uint32_t t) {
       uint32_t tm, tn;
       tile_mn(t, num_m, num_n, a.group_m, tm, tn);
-      return tm * 2 * BM + rank * BM + 32 * q + lane;
-    };
-    auto col_of = [&](uint32_t t) {
-      uint32_t tm, tn;
-      tile_mn(t, num_m, num_n, a.group_m, tm, tn);
-      return tn * BN2 + half * (BN2 / 2);
+      row = tm * 2 * BM + rank * BM + 32 * q + lane;
+      col = tn * BN2 + half * (BN2 / 2);
     };
     // the next tile's E' / received B' are loaded while this tile drains
     uint4 ev[BN2 / 32], ov[BN2 / 16];
     uint32_t it = 0;
-    if (cluster < num_tiles)
-      epilogue_prefetch<BN2 / 32, ODDQ>(a, row_of(cluster), col_of(cluster), ev, ov);
+    if (cluster < num_tiles) {
+      coords(cluster);
+      epilogue_prefetch<BN2 / 32, ODDQ>(a, row, col, ev, ov);
+    }
     for (uint32_t tile = cluster; tile < num_tiles; tile += nclusters, ++it) {
       const uint32_t acc = it & 1, use = it >> 1;
       if (!wait_bar_warp(tfull(acc), use & 1, abort_flag, a.dev_err)) break;
       tc_fence_after();
-      epilogue_tile<BN2 / 32, ODDQ>(a, row_of(tile), col_of(tile),
+      epilogue_tile<BN2 / 32, ODDQ>(a, row, col,
                               tmem_base + ((32 * q) << 16) + acc * (2 * BN2) + half * (BN2 / 2),
                               BN2, ev, ov);
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive_cluster(peer_addr(tempty(acc), 0));
       const uint32_t next = tile + nclusters;
-      if (next < num_tiles) epilogue_prefetch<BN2 / 32, ODDQ>(a, row_of(next), col_of(next), ev, ov);
+      if (next < num_tiles) {
+        coords(next);
+        epilogue_prefetch<BN2 / 32, ODDQ>(a, row, col, ev, ov);
+      }
     }
   }
   tc_fence_before();
@@ -1004,7 +1011,12 @@ bool lwe_gemm_supported(uint32_t n, uint32_t logq, uint32_t clip) {
 int launch_gemm_sa(const GemmSaArgs &a, int num_sms, cudaStream_t st) {
   if (!g_encode) return LWE_ECUDA;
   if (a.rows == 0) return LWE_OK;
-  const uint32_t kc = a.kchunk ? a.kchunk : a.n;
+  const uint32_t kmax = a.kchunk ? a.kchunk : a.n;
+  const uint32_t np = (a.n + kmax - 1) / kmax;
+  // passes of equal K (multiples of BK, none above kmax): a short last pass
+  // would be all epilogue (n = 32768 at kmax 10880: 8192 x 4 instead of
+  // 10880 x 3 + 128)
+  const uint32_t kc = np > 1 ? ((a.n + np - 1) / np + BK - 1) / BK * BK : kmax;
   const uint32_t passes = (a.n + kc - 1) / kc;
   if (passes > 1 && !a.partial_out) return LWE_EINVAL;
   for (uint32_t p = 0; p < passes; p++) {

@@ -1355,27 +1355,12 @@ LWE_DEV void st_cluster_u64(uint32_t addr, uint64_t v) {
   asm volatile("st.shared::cluster.u64 [%0], %1;" ::"r"(addr), "l"(v) : "memory");
 }
 
-__global__ void __launch_bounds__(TREE_WARP_MAX_THREADS, 1) k_tree_warp(TreeArgs a) {
-  extern __shared__ uint64_t sdig[];  // [m][4], used in the cluster's first CTA
-  pdl_trigger();
-  pdl_wait();
-  uint32_t q, nq;
-  asm("mov.u32 %0, %%cluster_ctarank;" : "=r"(q));
-  asm("mov.u32 %0, %%cluster_nctarank;" : "=r"(nq));
-  const uint32_t e = blockIdx.x / nq, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const uint32_t nw = blockDim.x >> 5, t = lane % 25;
-  const KeccakWarpMap km = keccak_warp_map(lane);
-  const uint8_t *msg = a.msg_ptrs ? a.msg_ptrs[e] : a.msgs + (size_t)e * a.stride;
-  const uint32_t dig0 = cluster_map(sdig, 0);
-  for (uint32_t c = q * nw + warp; c < a.m; c += nq * nw) {
-    const uint32_t off = c * LWE_TREE_CHUNK;
-    const uint64_t v =
-        sha3_256_warp_chunk(km, msg + off, min((uint32_t)LWE_TREE_CHUNK, a.len - off), lane);
-    if (lane < 4) st_cluster_u64(dig0 + 8 * (4 * c + lane), v);
-  }
-  cluster_barrier();  // every digest is in the first CTA's shared memory
-  if (q != 0 || warp != 0) return;
-  uint64_t v = sha3_256_warp_mem(km, sdig, 32 * a.m, lane);
+// The end of a tree hash on one warp (v: this lane of the root's final
+// state, lanes 0..3 the digest): digest mode stores H into out (and out2);
+// Encaps mode derives K = H(K' || H(c)) (Alg. 4), one 64-byte block.
+LWE_DEV void tree_warp_out(const TreeArgs &a, uint32_t e, const KeccakWarpMap &km, uint32_t lane,
+                           uint64_t v) {
+  const uint32_t t = lane % 25;
   uint8_t *out;
   if (a.mode == TREE_DIGEST) {
     if (a.out2 && lane < 4) {
@@ -1384,7 +1369,6 @@ __global__ void __launch_bounds__(TREE_WARP_MAX_THREADS, 1) k_tree_warp(TreeArgs
     }
     out = a.out + (size_t)e * a.out_stride;
   } else {
-    // Encaps (Alg. 4): K = H(K' || H(c)), one 64-byte block
     const uint64_t hc = shfl64(v, (lane - 4) & 31);  // lanes 4..7 take the digest
     uint64_t w = 0;
     if (t < 4) w = reinterpret_cast<const uint64_t *>(a.kprime + 32 * (size_t)e)[t];
@@ -1396,6 +1380,65 @@ __global__ void __launch_bounds__(TREE_WARP_MAX_THREADS, 1) k_tree_warp(TreeArgs
   }
   if (lane < 4)
     for (int b = 0; b < 8; b++) out[8 * lane + b] = (uint8_t)(v >> (8 * b));
+}
+
+__global__ void __launch_bounds__(TREE_WARP_MAX_THREADS, 1) k_tree_warp(TreeArgs a) {
+  extern __shared__ uint64_t sdig[];  // [m][4], used in the cluster's first CTA
+  pdl_trigger();
+  pdl_wait();
+  uint32_t q, nq;
+  asm("mov.u32 %0, %%cluster_ctarank;" : "=r"(q));
+  asm("mov.u32 %0, %%cluster_nctarank;" : "=r"(nq));
+  const uint32_t e = blockIdx.x / nq, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const uint32_t nw = blockDim.x >> 5;
+  const KeccakWarpMap km = keccak_warp_map(lane);
+  const uint8_t *msg = a.msg_ptrs ? a.msg_ptrs[e] : a.msgs + (size_t)e * a.stride;
+  const uint32_t dig0 = cluster_map(sdig, 0);
+  for (uint32_t c = q * nw + warp; c < a.m; c += nq * nw) {
+    const uint32_t off = c * LWE_TREE_CHUNK;
+    const uint64_t v =
+        sha3_256_warp_chunk(km, msg + off, min((uint32_t)LWE_TREE_CHUNK, a.len - off), lane);
+    if (lane < 4) st_cluster_u64(dig0 + 8 * (4 * c + lane), v);
+  }
+  cluster_barrier();  // every digest is in the first CTA's shared memory
+  if (q != 0 || warp != 0) return;
+  tree_warp_out(a, e, km, lane, sha3_256_warp_mem(km, sdig, 32 * a.m, lane));
+}
+
+// Tree hash of long messages (more than 32 chunks: ciphertexts and public
+// keys of n >= 4096) in two launches.  k_tree_leaves hashes every 1024-byte
+// chunk of the batch on its own thread (message e's chunk c on thread
+// e m + c, all SMs busy whatever the batch size) and writes the digests to
+// a.dig ([count][m][4] words); k_tree_roots then runs each message's root,
+// a sequential sponge over 32 m bytes, on one warp with the state spread
+// over the lanes, which shortens that chain about twofold against one
+// thread (and, for Encaps, derives the key).  k_tree instead gave each such
+// message a group of up to 256 threads and ran the root on one thread while
+// the group waited.
+__global__ void __launch_bounds__(256) k_tree_leaves(TreeArgs a) {
+  pdl_trigger();
+  pdl_wait();
+  const uint64_t L = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (L >= (uint64_t)a.count * a.m) return;
+  const uint32_t e = (uint32_t)(L / a.m), c = (uint32_t)(L % a.m);
+  const uint8_t *msg = a.msg_ptrs ? a.msg_ptrs[e] : a.msgs + (size_t)e * a.stride;
+  const uint32_t off = c * LWE_TREE_CHUNK;
+  if (!LWE_BOUNDS(off < a.len && 4 * (L + 1) <= a.dig_words, 114)) return;
+  uint64_t s[25];
+  sha3_256_global(msg + off, min((uint32_t)LWE_TREE_CHUNK, a.len - off), s);
+  uint4 *d = reinterpret_cast<uint4 *>(a.dig + 4 * L);
+  d[0] = make_uint4((uint32_t)s[0], (uint32_t)(s[0] >> 32), (uint32_t)s[1], (uint32_t)(s[1] >> 32));
+  d[1] = make_uint4((uint32_t)s[2], (uint32_t)(s[2] >> 32), (uint32_t)s[3], (uint32_t)(s[3] >> 32));
+}
+
+__global__ void __launch_bounds__(64) k_tree_roots(TreeArgs a) {
+  pdl_trigger();
+  pdl_wait();
+  const uint32_t e = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (e >= a.count) return;  // the whole warp
+  const KeccakWarpMap km = keccak_warp_map(lane);
+  if (!LWE_BOUNDS(4ull * (e + 1) * a.m <= a.dig_words, 115)) return;
+  tree_warp_out(a, e, km, lane, sha3_256_warp_mem(km, a.dig + 4ull * e * a.m, 32 * a.m, lane));
 }
 
 __global__ void __launch_bounds__(128) k_final_key(FinalKeyArgs a) {
@@ -1744,6 +1787,24 @@ void launch_tree(TreeArgs &a, int num_sms, uint32_t warp_max, cudaStream_t st) {
     return;
   }
   const uint32_t sms = num_sms > 0 ? (uint32_t)num_sms : 1u;
+  if (a.m > 32 && a.dig && (uint64_t)a.count * a.m * 4 <= a.dig_words) {
+    // long messages: every leaf on its own thread, then one warp per root,
+    // once k_tree (below: one thread per message runs its root) would have
+    // root chains of more than 128 chunks (31+ sequential permutations) or
+    // need more than one wave of two CTAs per SM
+    uint32_t t = 1;
+    while (t < a.m && t < 256) t <<= 1;
+    const uint32_t cap = std::max<uint32_t>(
+        1u, std::min<uint32_t>(TREE_MAX_THREADS / t, (48u * 1024u) / (8u * (4 * a.m + 1))));
+    if (a.m > 128 || a.count > 2 * sms * cap) {
+      // small leaf CTAs when the batch fills the SMs only a few warps deep
+      const uint64_t leaves = (uint64_t)a.count * a.m;
+      const uint32_t lt = leaves >= (uint64_t)sms * 1024 ? 256u : 64u;
+      launch_k(k_tree_leaves, (uint32_t)((leaves + lt - 1) / lt), lt, 0, st, a);
+      launch_k(k_tree_roots, (a.count + 1) / 2, 64, 0, st, a);
+      return;
+    }
+  }
   {
     // the balanced schedule of k_tree_bal: leaves of full length filling
     // more than 12 and at most 13 warps per CTA, every message's short

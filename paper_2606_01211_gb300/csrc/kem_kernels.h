@@ -147,6 +147,8 @@ struct TreeArgs {
   uint8_t *out2;
   uint64_t out2_stride;
   const uint8_t *kprime; // 32 per item
+  uint64_t *dig;         // scratch for the leaf digests of long messages
+  uint64_t dig_words;    // (count x m x 4 words), or NULL / 0
 };
 
 // Decaps' key selection (Alg. 5): K = H(K' || H(c)) when the re-encryption

@@ -168,6 +168,8 @@ struct lwe_ctx {
   int gemm_bn = 128;
   int gemm_pair = 1;
   uint32_t gemm_group = 0;  // LWE_OPT_GEMM_GROUP; 0: chosen per launch
+  uint64_t *tdig = nullptr;  // leaf digests of long tree hashes (n >= 4096)
+  uint64_t tdig_words = 0;
   bool serial = false;  // LWE_OPT_SERIAL: side-stream work on the caller's stream
   bool pdl = true;      // LWE_OPT_PDL
   int64_t tree_warp_max = -1;  // LWE_OPT_WARP_HASH_MAX; -1: the number of SMs
@@ -489,6 +491,8 @@ void tree_hash(lwe_ctx *c, const uint8_t *msgs, uint64_t stride, uint32_t len, u
   ta.out2 = out2;
   ta.out2_stride = out2_stride;
   ta.kprime = c->kp;
+  ta.dig = c->tdig;
+  ta.dig_words = c->tdig_words;
   const uint32_t warp_max = warp_hash_max(c);
   LAUNCH(c, count <= warp_max ? KID_TREE_WARP : KID_TREE, st,
          launch_tree(ta, c->num_sms, warp_max, st));
@@ -623,6 +627,11 @@ int lwe_ctx_create(const lwe_params *p, uint32_t max_batch, int device, lwe_ctx 
   const size_t o_rk = carve(176 * Bm), o_pkhs = carve(32 * Bm);
   const size_t o_hc = carve(32 * Bm);
   const size_t o_sp8 = carve(8 * n * Bm), o_ep8 = carve(8 * n * Bm), o_epp = carve(64 * Bm);
+  // tree hashes of messages of more than 32 chunks keep their leaf digests
+  // in global memory (32 bytes per chunk)
+  const size_t tchunks = (std::max(ct_bytes(*p), pk_bytes(*p)) + LWE_TREE_CHUNK - 1) / LWE_TREE_CHUNK;
+  const size_t tdig_bytes = tchunks > 32 ? 32 * tchunks * Bm : 0;
+  const size_t o_tdig = tdig_bytes ? carve(tdig_bytes) : 0;
   size_t o_spbf = 0, o_limbs = 0;
   size_t o_partial = 0;
   if (c->has_tensor) {
@@ -651,6 +660,10 @@ int lwe_ctx_create(const lwe_params *p, uint32_t max_batch, int device, lwe_ctx 
   c->sp8 = reinterpret_cast<int8_t *>(c->ws + o_sp8);
   c->ep8 = reinterpret_cast<int8_t *>(c->ws + o_ep8);
   c->epp = reinterpret_cast<int8_t *>(c->ws + o_epp);
+  if (tdig_bytes) {
+    c->tdig = reinterpret_cast<uint64_t *>(c->ws + o_tdig);
+    c->tdig_words = tdig_bytes / 8;
+  }
   if (c->has_tensor) {
     c->spbf = reinterpret_cast<uint16_t *>(c->ws + o_spbf);
     c->limbs = reinterpret_cast<uint16_t *>(c->ws + o_limbs);

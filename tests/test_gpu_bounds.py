@@ -19,16 +19,19 @@ sys.path.insert(0, ROOT)
 
 def workload():
     """Outputs of a fixed set of calls: the headline batch on the tensor
-    path (balanced tree hash, CTA-pair GEMM with bulk stores), a ragged
-    CUDA-core batch with regenerated A, the K-split GEMM, row blocks, and
-    the paper profile."""
+    path (balanced tree hash, CTA-pair GEMM), a ragged CUDA-core batch with
+    regenerated A, a P640 batch (dense tree schedule), a P4096 batch of
+    1000 (the two-launch tree of long messages, the GEMM's grouped tile
+    order), the K-split GEMM, row blocks, and the paper profile."""
     from paper_2606_01211_gb300 import lwe, rowsplit
     from paper_2606_01211_gb300.inputs import PRESETS, coins, master_seeds
     dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
     out = {}
     for name, count, path, stored in (("P976", 4096, lwe.PATH_TENSOR, True),
                                       ("P640", 21, lwe.PATH_SKINNY, False),
-                                      ("P1344", 19, lwe.PATH_TENSOR, False)):
+                                      ("P1344", 19, lwe.PATH_TENSOR, False),
+                                      ("P640", 4096, lwe.PATH_TENSOR, True),
+                                      ("P4096", 1000, lwe.PATH_TENSOR, False)):
         p = lwe.Params(**PRESETS[name])
         ctx = lwe.Ctx(p, max_batch=count)
         ctx.set_path(path)
@@ -40,9 +43,9 @@ def workload():
         K2 = torch.empty_like(K)
         ctx.encaps(pk, dev(coins(count, seed=6)), ct, K, A=A)
         ctx.decaps(sk, ct, K2, A=A)
-        out[name] = np.concatenate([pk.cpu().numpy().ravel(), sk.cpu().numpy().ravel(),
-                                    ct.cpu().numpy().ravel(), K.cpu().numpy().ravel(),
-                                    K2.cpu().numpy().ravel()])
+        out["%s_%d" % (name, count)] = np.concatenate(
+            [pk.cpu().numpy().ravel(), sk.cpu().numpy().ravel(), ct.cpu().numpy().ravel(),
+             K.cpu().numpy().ravel(), K2.cpu().numpy().ravel()])
         ctx.close()
     r = np.random.default_rng(1)
     n = 2048

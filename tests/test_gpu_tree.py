@@ -9,7 +9,12 @@ under each of its launch schedules, against the oracle over whole batches:
   and 2 ciphertexts per SM (3800: 12 leaf warps; 2048; 300: one leaf warp)
   and at P640 (4096: 9 leaf warps);
 - the one-leaf-per-thread schedule (k_tree) beyond both: P1344 with 27
-  ciphertexts per SM (567 leaves) and P640 with 40 per SM."""
+  ciphertexts per SM (567 leaves) and P640 with 40 per SM;
+- for long messages (more than 32 chunks) k_tree while it takes one wave
+  of CTAs (P4096 with 300 items, 65 chunks per ciphertext), and below, the
+  two-launch schedule (every leaf on its own thread, digests in global
+  memory, one warp per root) beyond that wave (P4096 with 1000 items) and
+  for root chains of more than 128 chunks (P16384, 257 chunks)."""
 import numpy as np
 import pytest
 import torch
@@ -21,7 +26,8 @@ pytestmark = pytest.mark.gpu
 
 @pytest.mark.parametrize("name,count", [("P976", 3801), ("P976", 4104), ("P1344", 2800),
                                         ("P976", 3800), ("P640", 4096), ("P976", 2048),
-                                        ("P976", 300), ("P1344", 4096), ("P640", 6000)])
+                                        ("P976", 300), ("P1344", 4096), ("P640", 6000),
+                                        ("P4096", 300)])
 def test_batched_hashes_match_the_oracle(name, count):
     torch.cuda.set_device(0)
     cfg = PRESETS[name]
@@ -101,4 +107,41 @@ def test_multi_key_encaps_hashes_each_pk_in_one_batch():
         pk_o, _ = O.keygen(po, bytes(ms[keys[i]]))
         ct_o, K_o = O.encaps(po, pk_o, bytes(cs[i]))
         assert np.array_equal(out[0][0][i], ct_o) and np.array_equal(out[0][1][i], K_o), i
+    assert ctx.device_error() == 0
+
+
+@pytest.mark.parametrize("name,count", [("P4096", 1000), ("P16384", 160)])
+def test_long_message_tree_hashes(name, count):
+    """Batches of long messages on the two-launch schedule:
+    KeyGen's H(pk) of every key equals the oracle's tree hash of the GPU's
+    pk; Decaps of tampered ciphertexts returns H(z || H(c)) with H(c) the
+    oracle's tree hash, for every item; Decaps of the untampered ones
+    returns Encaps' key, whose H(K' || H(c)) comes from the root warps."""
+    torch.cuda.set_device(0)
+    p, po = params(name)
+    n = p.n
+    ctx = lwe.Ctx(p, max_batch=count)
+    ms = master_seeds(count, seed=91)
+    pk, sk = ctx.empty_pk(count), ctx.empty_sk(count)
+    ctx.keygen(dev(ms), pk, sk)
+    pk_h, sk_h = host(pk), host(sk)
+    off = 8 * n + 32
+    for i in range(count):
+        assert sk_h[i, off:off + 32].tobytes() == O.htree(pk_h[i].tobytes()), i
+    ctx.set_path(lwe.PATH_TENSOR)
+    cs = coins(count, seed=92)
+    ct = ctx.empty_ct(count)
+    K = torch.empty((count, 32), dtype=torch.uint8, device="cuda")
+    ctx.encaps(pk[:1], dev(cs), ct, K)
+    K2 = torch.empty_like(K)
+    ctx.decaps(sk[:1], ct, K2)
+    assert torch.equal(K, K2)
+    bad = ct.clone()
+    bad[:, 7] ^= 1
+    Kb = torch.empty_like(K)
+    ctx.decaps(sk[:1], bad, Kb)
+    Kb_h, bad_h = host(Kb), host(bad)
+    z = sk_h[0, 8 * n:8 * n + 32].tobytes()
+    for i in range(count):
+        assert Kb_h[i].tobytes() == O.sha3_256(z + O.htree(bad_h[i].tobytes())), i
     assert ctx.device_error() == 0
