@@ -960,6 +960,13 @@ def large_n(lwe, torch, dev, batch: int = 1024, names=("P16384", "P32768")):
         r["encaps_batched_per_s"] = batch / (t / 1e3)
         r["encaps_batched_kernels"] = batched_kernels(lwe, torch, ctx, n, batch,
                                                       lambda: ctx.encaps(pk, cs, ct, K, A=A))
+        # the same calls against a bound key (H(pk) and the limbs of [A | B]
+        # made once, as a server holding the key does)
+        ctx.bind_key(pk, sk, A)
+        tb = _event_ms(torch, stream, lambda: ctx.encaps(pk, cs, ct, K, A=A), reps=3)
+        r["encaps_batched_%d_bound" % batch] = tb
+        r["encaps_batched_bound_per_s"] = batch / (tb / 1e3)
+        ctx.bind_key(None)
         ctx.decaps(sk, ct, K2, A=A)
         torch.cuda.synchronize()
         assert torch.equal(K, K2)

@@ -1466,10 +1466,22 @@ __global__ void __launch_bounds__(128) k_final_key(FinalKeyArgs a) {
 // signed 8-bit limbs, x = lo + 256 hi (mod 2^16), written K-major as bf16
 // (limbs[l][c][i]); a 64 x 64 tile is transposed through shared memory.
 // ---------------------------------------------------------------------------
+// The 64 x 64 tile sits in shared memory with its 16-byte chunks swizzled:
+// chunk q of row r at position q ^ ((r >> 3) & 7).  The transposed read
+// (each lane a column, lanes over rows 8 apart) then meets 8 different
+// chunks, all 32 banks, where an unswizzled (even a padded) row layout put
+// those rows on one or two banks.
+LWE_DEV uint32_t limb_tile_at(uint32_t r, uint32_t c) {
+  return r * 64 + 8 * ((c >> 3) ^ ((r >> 3) & 7)) + (c & 7);
+}
+
+// One instance per source of A: the stored one carries no AES state, so it
+// needs few registers and more CTAs per SM keep more loads in flight.
+template <bool FUSED>
 __global__ void __launch_bounds__(256) k_limbs(GemmLimbArgs a) {
   extern __shared__ uint32_t sT[];
-  __shared__ __align__(16) uint16_t tile[64][72];
-  const bool fused = (a.A == nullptr);
+  __shared__ __align__(16) uint16_t tile[64 * 64];
+  constexpr bool fused = FUSED;
   const uint32_t n = a.n, ncols = n + (a.B ? 8u : 0u);
   const uint32_t i0 = blockIdx.y * 64, c0 = blockIdx.x * 64;
   const uint32_t mq = (1u << a.logq) - 1u, mm = mq | (mq << 16);
@@ -1506,7 +1518,7 @@ __global__ void __launch_bounds__(256) k_limbs(GemmLimbArgs a) {
         v = ld_nc_u4(a.B + 16 * (size_t)i);
       }
     }
-    *reinterpret_cast<uint4 *>(&tile[r][8 * cq]) = v;
+    *reinterpret_cast<uint4 *>(&tile[limb_tile_at(r, 8 * cq)]) = v;
   }
   __syncthreads();
   for (uint32_t idx = threadIdx.x; idx < 512; idx += blockDim.x) {
@@ -1519,7 +1531,7 @@ __global__ void __launch_bounds__(256) k_limbs(GemmLimbArgs a) {
       float fl[2], fh[2];
 #pragma unroll
       for (int u = 0; u < 2; u++) {
-        const int x = tile[8 * ic + t + u][cl];
+        const int x = tile[limb_tile_at(8 * ic + t + u, cl)];
         const int l = (int)(int8_t)(uint8_t)(x & 0xff);
         const int h = (int)(int8_t)(uint8_t)(((x - l) >> 8) & 0xff);
         fl[u] = (float)l;
@@ -1672,7 +1684,7 @@ cudaError_t lwe_kernel_smem_setup() {
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_pp_noise, cudaFuncAttributeMaxDynamicSharedMemorySize, AES_SMEM_BYTES);
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_limbs, cudaFuncAttributeMaxDynamicSharedMemorySize, AES_SMEM_BYTES);
+  e = cudaFuncSetAttribute(k_limbs<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, AES_SMEM_BYTES);
   return e;
 }
 
@@ -1868,7 +1880,10 @@ void launch_gemm_limbs(const GemmLimbArgs &a, int num_sms, cudaStream_t st) {
   (void)num_sms;
   const uint32_t ncols = a.n + (a.B ? 8u : 0u);
   dim3 grid((ncols + 63) / 64, (a.n + 63) / 64);
-  launch_k(k_limbs, grid, 256, a.A ? 0 : AES_SMEM_BYTES, st, a);
+  if (a.A)
+    launch_k(k_limbs<false>, grid, 256, 0, st, a);
+  else
+    launch_k(k_limbs<true>, grid, 256, AES_SMEM_BYTES, st, a);
 }
 
 void launch_s_to_bf16(const int8_t *S, uint64_t count, uint16_t *out, int num_sms, cudaStream_t st) {
