@@ -966,6 +966,8 @@ def large_n(lwe, torch, dev, batch: int = 1024, names=("P16384", "P32768")):
         tb = _event_ms(torch, stream, lambda: ctx.encaps(pk, cs, ct, K, A=A), reps=3)
         r["encaps_batched_%d_bound" % batch] = tb
         r["encaps_batched_bound_per_s"] = batch / (tb / 1e3)
+        r["encaps_batched_bound_kernels"] = batched_kernels(
+            lwe, torch, ctx, n, batch, lambda: ctx.encaps(pk, cs, ct, K, A=A))["ms"]
         ctx.bind_key(None)
         ctx.decaps(sk, ct, K2, A=A)
         torch.cuda.synchronize()
@@ -1051,6 +1053,8 @@ def main():
                     help="only the standalone kernel sweep at these n (prints its JSON, not the bench line)")
     ap.add_argument("--large-only", type=str, default=None, metavar="NAME[,NAME...]",
                     help="only the large-n section for these presets (prints its JSON, not the bench line)")
+    ap.add_argument("--pp-only", type=str, default=None, metavar="NAME[,NAME...]",
+                    help="only the paper-profile section for these presets, without the oracle (prints its JSON)")
     ap.add_argument("--large-batch", type=int, default=1024,
                     help="Encaps per batched call in the large-n section")
     ap.add_argument("--cpu-s", type=float, default=12.0)
@@ -1065,6 +1069,14 @@ def main():
         flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.int32, device=dev)
         sizes = tuple(int(x) for x in args.sweep_only.split(","))
         print(json.dumps(kernel_sweep(lwe, torch, dev, flush, sizes=sizes)))
+        return 0
+    if args.pp_only:
+        import torch
+        from paper_2606_01211_gb300 import lwe
+        dev = torch.device("cuda", 0)
+        torch.cuda.set_device(dev)
+        names = tuple(args.pp_only.split(","))
+        print(json.dumps(paper_profile(lwe, torch, dev, cpu=False, names=names)))
         return 0
     if args.large_only:
         import torch
