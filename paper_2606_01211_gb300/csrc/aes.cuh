@@ -25,12 +25,20 @@
 #define AES_TABLE_WORDS (2 * 16384)
 #define AES_SMEM_BYTES (AES_TABLE_WORDS * 4)  // 128 KB
 
-LWE_DEV void aes_fill_smem(uint32_t *sT, const uint32_t *T0g) {
-  for (int i = threadIdx.x; i < AES_TABLE_WORDS; i += blockDim.x) {
-    const int k = 2 * (i >> 14) + ((i >> 5) & 1);
-    const uint32_t v = T0g[(i >> 6) & 255];
-    sT[i] = k ? rotl32(v, 8 * k) : v;
-  }
+// The tables in this layout, word i: table k = 2 (i >> 14) + ((i >> 5) & 1),
+// entry (i >> 6) & 255.  The host builds the whole 128 KB image once per
+// device (aes_table_image); a CTA copies it into shared memory with 16-byte
+// loads instead of working out every word.
+inline uint32_t aes_table_word(const uint32_t T0[256], uint32_t i) {
+  const uint32_t k = 2 * (i >> 14) + ((i >> 5) & 1);
+  const uint32_t v = T0[(i >> 6) & 255];
+  return k ? (v << (8 * k)) | (v >> (32 - 8 * k)) : v;
+}
+
+LWE_DEV void aes_fill_smem(uint32_t *sT, const uint4 *img) {
+  uint4 *d = reinterpret_cast<uint4 *>(sT);
+#pragma unroll 4
+  for (int i = threadIdx.x; i < AES_TABLE_WORDS / 4; i += blockDim.x) d[i] = img[i];
 }
 
 struct AesTab {

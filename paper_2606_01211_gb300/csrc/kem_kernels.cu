@@ -17,6 +17,7 @@
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <vector>
 
 #include "aes.cuh"
 #include "common.cuh"
@@ -25,8 +26,10 @@
 #include "pp_types.h"
 #include "keccak_warp.cuh"
 
-// The round table T0 (see aes.cuh); written by lwe_upload_aes_table.
+// The round table T0 (see aes.cuh) and the replicated shared-memory image of
+// all four tables; both written by lwe_upload_aes_table.
 __device__ uint32_t g_aes_T0[256];
+__device__ uint4 g_aes_img[AES_TABLE_WORDS / 4];
 
 // ---------------------------------------------------------------------------
 // A expansion: a warp per run of 128 counter blocks (16-byte blocks of A),
@@ -38,7 +41,7 @@ __global__ void __launch_bounds__(512, 1) k_expand_A(const uint8_t *__restrict__
                                                   uint64_t a_stride) {
   extern __shared__ uint32_t sT[];
   pdl_trigger();
-  aes_fill_smem(sT, g_aes_T0);
+  aes_fill_smem(sT, g_aes_img);
   __syncthreads();
   pdl_wait();
   const AesTab tab = aes_tab(sT);
@@ -198,8 +201,15 @@ LWE_DEV void noise_runs(const NoiseArgs &a, const AesTab &tab, const char *smem,
 __global__ void __launch_bounds__(512, 1) k_noise(NoiseArgs a) {
   extern __shared__ uint32_t sT[];
   pdl_trigger();
-  aes_fill_smem(sT, g_aes_T0);
-  noise_fill_table(sT + NOISE_TAB_OFF / 4, a);
+  aes_fill_smem(sT, g_aes_img);
+  if (a.tab_img) {
+    // the context's prebuilt sampler table (k_noise_table's output)
+    uint4 *d = reinterpret_cast<uint4 *>(sT + NOISE_TAB_OFF / 4);
+#pragma unroll 4
+    for (uint32_t i = threadIdx.x; i < 65536 / 16; i += blockDim.x) d[i] = a.tab_img[i];
+  } else {
+    noise_fill_table(sT + NOISE_TAB_OFF / 4, a);
+  }
   __syncthreads();
   pdl_wait();
   const AesTab tab = aes_tab(sT);
@@ -253,7 +263,7 @@ LWE_DEV void warp_allreduce8(int acc[8]) {
 __global__ void __launch_bounds__(512, 1) k_mul_as_fused(MulAsArgs a) {
   extern __shared__ uint32_t sT[];
   pdl_trigger();
-  aes_fill_smem(sT, g_aes_T0);
+  aes_fill_smem(sT, g_aes_img);
   __syncthreads();
   pdl_wait();
   const AesTab tab = aes_tab(sT);
@@ -682,7 +692,7 @@ __global__ void __launch_bounds__(512, 1) k_sa_fused(MulSaArgs a) {
   pdl_trigger();
   for (uint32_t i = tid; i < 2048; i += 512) red[i] = 0;
   uint32_t *sT = reinterpret_cast<uint32_t *>(base);
-  aes_fill_smem(sT, g_aes_T0);
+  aes_fill_smem(sT, g_aes_img);
   __syncthreads();
   pdl_wait();
   const AesTab tab = aes_tab(sT);
@@ -1489,7 +1499,7 @@ __global__ void __launch_bounds__(256) k_limbs(GemmLimbArgs a) {
   uint32_t rk[44];
   pdl_trigger();
   if (fused) {
-    aes_fill_smem(sT, g_aes_T0);
+    aes_fill_smem(sT, g_aes_img);
     __syncthreads();
   }
   pdl_wait();
@@ -1579,7 +1589,7 @@ __global__ void __launch_bounds__(256) k_probe_keccak(uint32_t iters, uint32_t *
 
 __global__ void __launch_bounds__(512, 1) k_probe_aes(uint32_t iters, uint32_t *sink) {
   extern __shared__ uint32_t sT[];
-  aes_fill_smem(sT, g_aes_T0);
+  aes_fill_smem(sT, g_aes_img);
   __syncthreads();
   const AesTab tab = aes_tab(sT);
   const uint32_t gid = blockIdx.x * blockDim.x + threadIdx.x;
@@ -1599,7 +1609,7 @@ __global__ void __launch_bounds__(512, 1) k_probe_aes(uint32_t iters, uint32_t *
 // run (window set up once), two at a time.
 __global__ void __launch_bounds__(512, 1) k_probe_aes_run(uint32_t iters, uint32_t *sink) {
   extern __shared__ uint32_t sT[];
-  aes_fill_smem(sT, g_aes_T0);
+  aes_fill_smem(sT, g_aes_img);
   __syncthreads();
   const AesTab tab = aes_tab(sT);
   const uint32_t gid = blockIdx.x * blockDim.x + threadIdx.x, lane = threadIdx.x & 31;
@@ -1657,7 +1667,11 @@ static int grid_for(uint64_t work, int per_cta, int max_ctas) {
 }
 
 cudaError_t lwe_upload_aes_table(const uint32_t T0[256]) {
-  return cudaMemcpyToSymbol(g_aes_T0, T0, 256 * sizeof(uint32_t));
+  cudaError_t e = cudaMemcpyToSymbol(g_aes_T0, T0, 256 * sizeof(uint32_t));
+  if (e != cudaSuccess) return e;
+  std::vector<uint32_t> img(AES_TABLE_WORDS);
+  for (uint32_t i = 0; i < AES_TABLE_WORDS; i++) img[i] = aes_table_word(T0, i);
+  return cudaMemcpyToSymbol(g_aes_img, img.data(), AES_TABLE_WORDS * sizeof(uint32_t));
 }
 
 cudaError_t lwe_kernel_smem_setup() {

@@ -33,6 +33,9 @@ struct NoiseArgs {
   uint32_t pad0, pad1, pad2;
   NoiseOut out[3];
   uint32_t T[16];        // CDF table, entries >= clip set to 0x7FFF
+  const uint4 *tab_img;  // the sampler table for T as k_noise_table writes it
+                         // (64 KB, byte w: the sample of word w), or NULL:
+                         // each CTA then builds it from T
 };
 
 struct MulAsArgs {

@@ -168,6 +168,7 @@ struct lwe_ctx {
   int gemm_bn = 128;
   int gemm_pair = 1;
   uint32_t gemm_group = 0;  // LWE_OPT_GEMM_GROUP; 0: chosen per launch
+  int8_t *ntab = nullptr;    // the sampler table for T (64 KB), built at creation
   uint64_t *tdig = nullptr;  // leaf digests of long tree hashes (n >= 4096)
   uint64_t tdig_words = 0;
   bool serial = false;  // LWE_OPT_SERIAL: side-stream work on the caller's stream
@@ -290,6 +291,7 @@ NoiseArgs noise_args(const lwe_ctx *c, uint32_t count) {
   a.rk = c->rk;
   a.count = count;
   for (int i = 0; i < 16; i++) a.T[i] = c->T[i];
+  a.tab_img = reinterpret_cast<const uint4 *>(c->ntab);
   return a;
 }
 
@@ -625,7 +627,7 @@ int lwe_ctx_create(const lwe_params *p, uint32_t max_batch, int device, lwe_ctx 
   const size_t o_flags = carve(4 * Bm), o_err = carve(16), o_pkh = carve(32);
   const size_t o_bpkh = carve(32);
   const size_t o_rk = carve(176 * Bm), o_pkhs = carve(32 * Bm);
-  const size_t o_hc = carve(32 * Bm);
+  const size_t o_hc = carve(32 * Bm), o_ntab = carve(65536);
   const size_t o_sp8 = carve(8 * n * Bm), o_ep8 = carve(8 * n * Bm), o_epp = carve(64 * Bm);
   // tree hashes of messages of more than 32 chunks keep their leaf digests
   // in global memory (32 bytes per chunk)
@@ -657,6 +659,7 @@ int lwe_ctx_create(const lwe_params *p, uint32_t max_batch, int device, lwe_ctx 
   c->pkh = c->ws + o_pkh;
   c->bpkh = c->ws + o_bpkh;
   c->hc = c->ws + o_hc;
+  c->ntab = reinterpret_cast<int8_t *>(c->ws + o_ntab);
   c->sp8 = reinterpret_cast<int8_t *>(c->ws + o_sp8);
   c->ep8 = reinterpret_cast<int8_t *>(c->ws + o_ep8);
   c->epp = reinterpret_cast<int8_t *>(c->ws + o_epp);
@@ -674,6 +677,12 @@ int lwe_ctx_create(const lwe_params *p, uint32_t max_batch, int device, lwe_ctx 
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_limbs, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaMemset(c->ws, 0, c->ws_bytes);
+  if (e == cudaSuccess) {
+    NoiseArgs na = noise_args(c, 0);
+    na.tab_img = nullptr;
+    launch_noise_table(na, c->ntab, 0);
+    e = cudaGetLastError();
+  }
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
   cudaSetDevice(prev);
   if (e != cudaSuccess) {

@@ -70,7 +70,7 @@ __global__ void __launch_bounds__(512, 1) k_pp_expand_A(const uint8_t *__restric
                                                      uint32_t n, ModQ M, uint32_t *__restrict__ A) {
   extern __shared__ uint32_t sT[];
   pdl_trigger();
-  aes_fill_smem(sT, g_aes_T0);
+  aes_fill_smem(sT, g_aes_img);
   __syncthreads();
   pdl_wait();
   const AesTab tab = aes_tab(sT);
@@ -114,7 +114,7 @@ LWE_DEV uint32_t pp_noise_blocks(const PpNoiseOut &o) {
 __global__ void __launch_bounds__(512, 1) k_pp_noise(PpNoiseArgs a) {
   extern __shared__ uint32_t sT[];
   pdl_trigger();
-  aes_fill_smem(sT, g_aes_T0);
+  aes_fill_smem(sT, g_aes_img);
   __syncthreads();
   pdl_wait();
   const AesTab tab = aes_tab(sT);
