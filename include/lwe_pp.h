@@ -79,7 +79,7 @@ int lwe_pp_ctx_destroy(lwe_pp_ctx *ctx);
 enum { LWE_PP_OPT_TENSOR = 0, LWE_PP_OPT_PDL = 1 };
 int lwe_pp_ctx_set_option(lwe_pp_ctx *ctx, int option, int64_t value);
 
-/* A = sample(seedA) (Alg. 1 line 1) into A (n x n uint32).  seedA: 16
+/* A = sample(seedA) (Alg. 1) into A (n x n uint32).  seedA: 16
  * device bytes. */
 int lwe_pp_expand_A(const lwe_pp_params *p, const uint8_t *seedA, uint32_t *A, void *stream);
 

@@ -19,7 +19,7 @@ Readings, where the paper is silent or at odds with itself:
 * Binomial eta = 3 from one keystream byte b:
   popcount(b & 7) - popcount((b >> 3) & 7).
 * Centred uniform from a 16-bit word w: floor((2k + 1) w / 2^16) - k.
-* A (Alg. 1 line 1, "sample(rho)"): uniform mod q by rejection.  Entry
+* A (Alg. 1, "sample(rho)"): uniform mod q by rejection.  Entry
   (i, j) takes 32-bit little-endian word i n + j of the stream (seedA,
   domain 16 + t); the word is accepted when w < q floor(2^32 / q), giving
   A = w mod q, else t + 1 is tried (t < 8).
@@ -30,7 +30,7 @@ Readings, where the paper is silent or at odds with itself:
 * Seeds as in the matrix form: seedA, seedSE, z from SHA3-256 of a prefix
   byte and the master seed; m = SHA3-256(0x4D || coins), bit k = bit k % 8
   of byte k / 8; K' = H(pkh || m); seedSE' = H(0x01 || pkh || m)[0:16]
-  derandomises Encrypt so that Decaps can re-encrypt (Alg. 5 line 2).
+  derandomises Encrypt so that Decaps can re-encrypt (Alg. 5).
 * Decode (Alg. 3): bit k is 1 iff q < 4 mu_k < 3q, i.e. 0 iff mu_k <= q/4
   or mu_k >= 3q/4.
 * Layouts: pk = seedA || t (n uint32 LE); sk = s (n int8) || z || pkh ||
@@ -155,7 +155,7 @@ def _bytes(key: bytes, domain: int, count: int) -> np.ndarray:
 
 
 def expand_A(seedA: bytes, p: PParams) -> np.ndarray:
-    """A in Z_q^{n x n}, row-major (Alg. 1 line 1)."""
+    """A in Z_q^{n x n}, row-major (Alg. 1)."""
     n = p.n
     limit = p.q * ((1 << 32) // p.q)
     tries = [_words32(seedA, A_DOMAIN, n * n)]

@@ -1933,13 +1933,13 @@ void launch_pp_encrypt(const PpEncArgs &a, bool cmp, cudaStream_t st) {
 
 void launch_pp_v(const PpVArgs &a, bool cmp, cudaStream_t st) {
   if (cmp)
-    launch_k(k_pp_v<true>, PP_MBITS / 8, 256, 0, st, a);
+    launch_k(k_pp_v<true>, PP_MBITS, 256, 0, st, a);
   else
-    launch_k(k_pp_v<false>, PP_MBITS / 8, 256, 0, st, a);
+    launch_k(k_pp_v<false>, PP_MBITS, 256, 0, st, a);
 }
 
 void launch_pp_decrypt(const PpDecArgs &a, cudaStream_t st) {
-  launch_k(k_pp_decrypt, PP_MBITS / 8, 256, 0, st, a);
+  launch_k(k_pp_decrypt, PP_MBITS, 256, 0, st, a);
 }
 
 void launch_pp_limbs(const uint32_t *A, uint32_t n, uint32_t q, uint16_t *limbs, cudaStream_t st) {

@@ -30,7 +30,7 @@ LWE_DEV int32_t centre(uint32_t a, uint32_t q) {
 }
 
 // ---------------------------------------------------------------------------
-// A (Alg. 1 line 1) uniform mod q by rejection: entry (i, j) is 32-bit word
+// A (Alg. 1) uniform mod q by rejection: entry (i, j) is 32-bit word
 // i n + j of the stream (seedA, domain 16 + t), accepted when below the
 // largest multiple of q under 2^32; a rejected word moves to the next try.
 // A counter block holds 4 consecutive entries of a row; a warp takes runs
@@ -173,7 +173,7 @@ __global__ void __launch_bounds__(512, 1) k_pp_noise(PpNoiseArgs a) {
 }
 
 // ---------------------------------------------------------------------------
-// KeyGen (Alg. 1 line 4): t = A s + e mod q, warp per row, written to the
+// KeyGen (Alg. 1): t = A s + e mod q, warp per row, written to the
 // public key and to the copy of it inside the secret key.
 // ---------------------------------------------------------------------------
 LWE_DEV uint32_t warp_sum_mod(uint32_t x, ModQ M) {  // x < q on every lane
@@ -212,7 +212,7 @@ __global__ void __launch_bounds__(256) k_pp_as(PpAsArgs a) {
 }
 
 // ---------------------------------------------------------------------------
-// Encrypt's products (Alg. 2 line 4 for the 256 columns r_k at once):
+// Encrypt's products (Alg. 2 for the 256 columns r_k at once):
 // U^T = R^T A + E1^T (mod q), R^T 256 x n int8, A n x n, as a CUDA-core GEMM.
 // CTA = 64 rows k x 64 columns j; thread (ty, tx) holds 4 x 4 sums; A tiles
 // of 32 x 64 (centred, int32) and R^T tiles of 64 x 32 (transposed to
@@ -307,32 +307,48 @@ __global__ void __launch_bounds__(256) k_pp_encrypt(PpEncArgs a) {
 }
 
 // ---------------------------------------------------------------------------
-// v_k = t^T r_k + e2_k + m_k floor(q/2) (mod q) (Alg. 2 line 5), warp per k;
+// v_k = t^T r_k + e2_k + m_k floor(q/2) (mod q) (Alg. 2), CTA per k;
 // CMP compares with the received v.
 // ---------------------------------------------------------------------------
+
+// sum_i centre(x_i) s_i (mod q) over i < n (n a multiple of 4) by a whole
+// CTA of 8 warps: a lane takes 4 consecutive entries, the warps interleave
+// in steps of 1024 entries, and the 8 warp sums meet in shared memory.  One
+// message bit per CTA keeps every SM busy where one warp per bit (256
+// warps in 32 CTAs) walked n / 128 dependent loads in a row.
+LWE_DEV uint32_t pp_cta_dot_mod(const uint32_t *x, const int8_t *s, uint32_t n, ModQ M) {
+  __shared__ uint32_t part[8];
+  const uint32_t lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  int32_t acc = 0;
+  uint32_t red = 0, since = 0;
+  for (uint32_t i = 4 * (lane + 32 * w); i < n; i += 1024) {
+    const uint4 v = ld_nc_u4(x + i);
+    const char4 c = *reinterpret_cast<const char4 *>(s + i);
+    acc += centre(v.x, M.q) * c.x + centre(v.y, M.q) * c.y + centre(v.z, M.q) * c.z +
+           centre(v.w, M.q) * c.w;
+    if ((since += 4) >= PP_REDUCE_EVERY) {
+      red = mod_u32(red + mod_s32(acc, M), M);
+      acc = 0;
+      since = 0;
+    }
+  }
+  red = mod_u32(red + mod_s32(acc, M), M);
+  const uint32_t ws = warp_sum_mod(red, M);
+  if (lane == 0) part[w] = ws;
+  __syncthreads();
+  uint32_t tot = 0;
+#pragma unroll
+  for (int j = 0; j < 8; j++) tot = mod_u32(tot + part[j], M);
+  return tot;
+}
 
 template <bool CMP>
 __global__ void __launch_bounds__(256) k_pp_v(PpVArgs a) {
   pdl_trigger();
   pdl_wait();
-  const uint32_t lane = threadIdx.x & 31, k = blockIdx.x * 8 + (threadIdx.x >> 5);
-  const int8_t *r = a.Rt + (size_t)k * a.n;
-  int32_t acc = 0;
-  uint32_t red = 0, since = 0;
-  for (uint32_t i = 4 * lane; i < a.n; i += 128) {
-    const uint4 x = ld_nc_u4(a.t + i);
-    const char4 s = *reinterpret_cast<const char4 *>(r + i);
-    acc += centre(x.x, a.M.q) * s.x + centre(x.y, a.M.q) * s.y + centre(x.z, a.M.q) * s.z +
-           centre(x.w, a.M.q) * s.w;
-    if ((since += 4) >= PP_REDUCE_EVERY) {
-      red = mod_u32(red + mod_s32(acc, a.M), a.M);
-      acc = 0;
-      since = 0;
-    }
-  }
-  red = mod_u32(red + mod_s32(acc, a.M), a.M);
-  const uint32_t sum = warp_sum_mod(red, a.M);
-  if (lane == 0) {
+  const uint32_t k = blockIdx.x;  // message bit
+  const uint32_t sum = pp_cta_dot_mod(a.t, a.Rt + (size_t)k * a.n, a.n, a.M);
+  if (threadIdx.x == 0) {
     const uint32_t bit = (a.m[k >> 3] >> (k & 7)) & 1u;
     const uint32_t v = mod_u32(mod_u32(sum + mod_s32(a.e2[k], a.M), a.M) + bit * (a.M.q / 2), a.M);
     if (CMP) {
@@ -344,31 +360,16 @@ __global__ void __launch_bounds__(256) k_pp_v(PpVArgs a) {
 }
 
 // ---------------------------------------------------------------------------
-// Decrypt (Alg. 3): mu_k = v_k - s^T u_k (mod q), warp per k; bit k of m is
+// Decrypt (Alg. 3): mu_k = v_k - s^T u_k (mod q), CTA per k; bit k of m is
 // 1 iff q < 4 mu_k < 3q.  m (8 words, zeroed by the caller) gathers the bits.
 // ---------------------------------------------------------------------------
 
 __global__ void __launch_bounds__(256) k_pp_decrypt(PpDecArgs a) {
   pdl_trigger();
   pdl_wait();
-  const uint32_t lane = threadIdx.x & 31, k = blockIdx.x * 8 + (threadIdx.x >> 5);
-  const uint32_t *u = a.Ut + (size_t)k * a.n;
-  int32_t acc = 0;
-  uint32_t red = 0, since = 0;
-  for (uint32_t j = 4 * lane; j < a.n; j += 128) {
-    const uint4 x = ld_nc_u4(u + j);
-    const char4 s = *reinterpret_cast<const char4 *>(a.s + j);
-    acc += centre(x.x, a.M.q) * s.x + centre(x.y, a.M.q) * s.y + centre(x.z, a.M.q) * s.z +
-           centre(x.w, a.M.q) * s.w;
-    if ((since += 4) >= PP_REDUCE_EVERY) {
-      red = mod_u32(red + mod_s32(acc, a.M), a.M);
-      acc = 0;
-      since = 0;
-    }
-  }
-  red = mod_u32(red + mod_s32(acc, a.M), a.M);
-  const uint32_t su = warp_sum_mod(red, a.M);
-  if (lane == 0) {
+  const uint32_t k = blockIdx.x;  // message bit
+  const uint32_t su = pp_cta_dot_mod(a.Ut + (size_t)k * a.n, a.s, a.n, a.M);
+  if (threadIdx.x == 0) {
     const uint32_t q = a.M.q, mu = mod_u32(a.v[k] + q - su, a.M);
     const uint64_t m4 = 4ull * mu;
     const uint32_t bit = (m4 > q && m4 < 3ull * q) ? 1u : 0u;
