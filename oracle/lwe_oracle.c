@@ -9,6 +9,12 @@
  * (rotation offsets and round constants derived from their defining
  * recurrences), the rounded-Gaussian CDF table from the normal CDF, and the
  * KEM from Alg. 1-5 of the paper in the matrix form B = A S + E.
+ *
+ * Parity unpinned: the domain bytes of the seed derivation, the domain
+ * numbering of the counter blocks and the pk / sk / ct byte layouts are
+ * readings of this project (the paper fixes none of them); nothing but this
+ * oracle fixes them.  Every function built on them is pinned otherwise
+ * (tests/test_oracle_pins.py).
  */
 #include "lwe_oracle.h"
 

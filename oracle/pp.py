@@ -38,6 +38,10 @@ Readings, where the paper is silent or at odds with itself:
   SHA3-256; H(pk) is the tree hash of the matrix form (``oracle.htree``),
   and H(c) = htree(htree(u_0) || ... || htree(u_255) || htree(v)), so that
   the multi-megabyte ciphertext needs no long sequential root.
+
+Parity unpinned: the stream domains, seed prefixes and byte layouts above
+are this project's readings, fixed only by this oracle; the word layout of
+A's stream is pinned only by range and a chi-square test.
 """
 from __future__ import annotations
 
