@@ -40,8 +40,9 @@ Readings, where the paper is silent or at odds with itself:
   the multi-megabyte ciphertext needs no long sequential root.
 
 Parity unpinned: the stream domains, seed prefixes and byte layouts above
-are this project's readings, fixed only by this oracle; the word layout of
-A's stream is pinned only by range and a chi-square test.
+are this project's readings, fixed only by this oracle.  (Given those
+readings, the word layout of the A, r, e1 and e2 streams is pinned against
+a library AES-CTR, tests/test_pp_oracle.py.)
 """
 from __future__ import annotations
 
