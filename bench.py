@@ -291,13 +291,13 @@ def keccak_perms(length: int, chunk: int = 1024) -> int:
 #  AES round tables: 160 conflict-free shared-memory lookups per 16-byte block,
 #    32 per clock per SM  ->  152 * 2.07e9 * 32 / 160 * 16 B = 1006 GB/s.
 #    k_noise's runs of 128 counter blocks share their first two rounds: 133
-#    lookups per block plus 27 per lane and run of 4 blocks = 139.75 per
-#    block  ->  1152 GB/s
+#    lookups per block, plus the window's 27, worked out for 32 runs at once
+#    (one per lane): 27 / (32 x 4) per block -> 133.21 per block -> 1209 GB/s
 #  Keccak-f[1600] on 32-bit lanes: 190 integer-ALU operations per round
 #    (three-input XORs / chi as LOP3, 64-bit rotations as funnel-shift pairs),
 #    64 ALU lanes per clock per SM  ->  152 * 2.07e9 * 64 / (190 * 24)
 #    = 4.42 G permutations/s
-AES_RUN_PEAK_GBS = 152 * 2.070e9 * 32 / (133 + 27 / 4) * 16 / 1e9
+AES_RUN_PEAK_GBS = 152 * 2.070e9 * 32 / (133 + 27 / 128) * 16 / 1e9
 KECCAK_PEAK_GPERMS = 152 * 2.070e9 * 64 / (190 * 24) / 1e9
 
 
@@ -361,12 +361,12 @@ TRAFFIC = {
                "61a10e1e45bb906c", "profiles/k_tree_p976.md"),
     "k_gemm_tc": (295.779584e6, 2, [("gemm_tc.cu", None)], "10f4eabbb5ca2195",
                   "profiles/k_gemm_sa2_p976.md"),
-    "k_noise": (69.743104e6, 2,
+    "k_noise": (69.913344e6, 2,
                 [("kem_kernels.cu", "k_noise"), ("kem_kernels.cu", "noise_runs"),
                  ("kem_kernels.cu", "noise_store"),
                  ("kem_kernels.cu", "noise_fill_table"), ("kem_kernels.cu", "launch_noise"),
                  ("aes.cuh", None)],
-                "2b58bca892842aa7", "profiles/k_noise_p976.md"),
+                "8c69346ce7bf41c6", "profiles/k_noise_p976.md"),
 }
 
 

@@ -384,8 +384,9 @@ int lwe_bounds_violations(uint64_t *count, uint32_t *first_site);
  *     regenerated).  Work: ctas * 512 * iters blocks.
  *   LWE_PROBE_AES_RUN: as LWE_PROBE_AES with the blocks of a warp taken
  *     four per lane from one 128-block run of counter indices, whose first
- *     two rounds are shared (the generator of the noise and of A); iters a
- *     multiple of 4.
+ *     two rounds are shared, the constants of 32 runs worked out at once,
+ *     under one key per warp (the generator of the noise and of A); iters
+ *     a multiple of 4.
  *   LWE_PROBE_KECCAK_WARP: `ctas` CTAs of one warp; each warp applies
  *     Keccak-f[1600] `iters` times to one state spread over its lanes (the
  *     permutation of k_tree_warp).  Work: ctas * iters permutations.

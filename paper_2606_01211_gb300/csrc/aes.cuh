@@ -168,6 +168,20 @@ LWE_DEV AesCtrRun aes_ctr_run(const AesTab &tab, const uint32_t rk[44], uint64_t
   return w;
 }
 
+// The window constants held by lane `src`, for the whole warp (every lane
+// calls it): a warp works out 32 windows at once, one per lane, and takes
+// them one after another.
+LWE_DEV AesCtrRun aes_ctr_run_shfl(const AesCtrRun &w, uint32_t src) {
+  AesCtrRun o;
+  o.s3 = __shfl_sync(0xffffffffu, w.s3, src);
+  o.k0 = __shfl_sync(0xffffffffu, w.k0, src);
+  o.k1 = __shfl_sync(0xffffffffu, w.k1, src);
+  o.k2 = __shfl_sync(0xffffffffu, w.k2, src);
+  o.k3 = __shfl_sync(0xffffffffu, w.k3, src);
+  o.k4 = __shfl_sync(0xffffffffu, w.k4, src);
+  return o;
+}
+
 // Keystream block of index (window base | x), x < 256; equal to
 // aes_ctr_block for that index.
 LWE_DEV uint4 aes_ctr_run_block(const AesTab &tab, const uint32_t rk[44], const AesCtrRun &w,

@@ -54,27 +54,35 @@ __global__ void __launch_bounds__(512, 1) k_expand_A(const uint8_t *__restrict__
   const uint64_t nblk = (uint64_t)n * n / 8;
   uint4 *out = reinterpret_cast<uint4 *>(A + (size_t)e * a_stride);
   // a warp takes runs of 128 consecutive blocks (4 per lane, two at a time);
-  // a run lies inside one 256-aligned counter window (aes_ctr_run)
+  // a run lies inside one 256-aligned counter window (aes_ctr_run), whose
+  // constants are worked out for 32 runs at a time, one per lane, and
+  // passed to the warp by shuffles as in noise_runs
   const uint32_t lane = threadIdx.x & 31;
   const uint64_t nruns = (nblk + 127) / 128, nw = (uint64_t)gridDim.x * (blockDim.x >> 5);
-  for (uint64_t run = (uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); run < nruns;
-       run += nw) {
-    const uint64_t first = run * 128;
-    const AesCtrRun win = aes_ctr_run(tab, rk, 0, first);
-    const uint32_t x0 = (uint32_t)(first & 255u) + lane;
-    if (first + 128 <= nblk) {
+  const uint64_t gw = (uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  for (uint64_t g = 0; gw + nw * g < nruns; g += 32) {
+    AesCtrRun mine{};
+    if (gw + nw * (g + lane) < nruns) mine = aes_ctr_run(tab, rk, 0, (gw + nw * (g + lane)) * 128);
+    for (uint32_t jr = 0; jr < 32; jr++) {
+      const uint64_t run = gw + nw * (g + jr);
+      if (run >= nruns) break;  // the same for every lane
+      const uint64_t first = run * 128;
+      const AesCtrRun win = aes_ctr_run_shfl(mine, jr);
+      const uint32_t x0 = (uint32_t)(first & 255u) + lane;
+      if (first + 128 <= nblk) {
 #pragma unroll
-      for (uint32_t j = 0; j < 4; j += 2) {
-        uint4 va = aes_ctr_run_block(tab, rk, win, x0 + 32 * j);
-        uint4 vb = aes_ctr_run_block(tab, rk, win, x0 + 32 * j + 32);
-        out[first + lane + 32 * j] = make_uint4(va.x & mm, va.y & mm, va.z & mm, va.w & mm);
-        out[first + lane + 32 * j + 32] = make_uint4(vb.x & mm, vb.y & mm, vb.z & mm, vb.w & mm);
-      }
-    } else {
+        for (uint32_t j = 0; j < 4; j += 2) {
+          uint4 va = aes_ctr_run_block(tab, rk, win, x0 + 32 * j);
+          uint4 vb = aes_ctr_run_block(tab, rk, win, x0 + 32 * j + 32);
+          out[first + lane + 32 * j] = make_uint4(va.x & mm, va.y & mm, va.z & mm, va.w & mm);
+          out[first + lane + 32 * j + 32] = make_uint4(vb.x & mm, vb.y & mm, vb.z & mm, vb.w & mm);
+        }
+      } else {
 #pragma unroll 1
-      for (uint32_t x = x0; first + (x - x0) + lane < nblk; x += 32) {
-        const uint4 v = aes_ctr_run_block(tab, rk, win, x);
-        out[first + (x - x0) + lane] = make_uint4(v.x & mm, v.y & mm, v.z & mm, v.w & mm);
+        for (uint32_t x = x0; first + (x - x0) + lane < nblk; x += 32) {
+          const uint4 v = aes_ctr_run_block(tab, rk, win, x);
+          out[first + (x - x0) + lane] = make_uint4(v.x & mm, v.y & mm, v.z & mm, v.w & mm);
+        }
       }
     }
   }
@@ -150,50 +158,85 @@ LWE_DEV void noise_store(const char *smem, const NoiseOut &o, uint8_t *base, uin
 }
 
 // The runs of one warp: warp `gwarp` of `nwarps` takes runs gwarp,
-// gwarp + nwarps, ...
+// gwarp + nwarps, ...  A run's window constants (aes_ctr_run: 27 lookups)
+// are the same for all 32 lanes, so they are worked out for 32 runs at a
+// time, lane l for the warp's run 32 g + l with that run's item key, and
+// passed to the whole warp by shuffles when the run comes up: 27 lookup
+// instructions per 32 runs instead of per run.
+struct NoiseRun {
+  uint32_t e, r, s;  // item, run within the item's streams, stream
+};
+
+LWE_DEV NoiseRun noise_run_of(const NoiseArgs &a, uint64_t run) {
+  NoiseRun x;
+  x.e = (uint32_t)(run / a.runs_per_item);
+  x.r = (uint32_t)(run % a.runs_per_item);
+  x.s = 0;
+  while (x.s + 1 < a.nout && x.r >= a.out[x.s].runs) {
+    x.r -= a.out[x.s].runs;
+    x.s++;
+  }
+  return x;
+}
+
+LWE_DEV void noise_load_rk(const NoiseArgs &a, uint32_t e, uint32_t rk[44]) {
+  const uint4 *rkp = reinterpret_cast<const uint4 *>(a.rk + 44 * (size_t)e);
+#pragma unroll
+  for (int i = 0; i < 11; i++) {
+    const uint4 v = __ldg(rkp + i);
+    rk[4 * i] = v.x;
+    rk[4 * i + 1] = v.y;
+    rk[4 * i + 2] = v.z;
+    rk[4 * i + 3] = v.w;
+  }
+}
+
 LWE_DEV void noise_runs(const NoiseArgs &a, const AesTab &tab, const char *smem, uint64_t gwarp,
                         uint64_t nwarps) {
   const uint32_t lane = threadIdx.x & 31;
   const uint64_t nruns = (uint64_t)a.count * a.runs_per_item;
-  for (uint64_t run = gwarp; run < nruns; run += nwarps) {
-    const uint32_t e = (uint32_t)(run / a.runs_per_item);
-    uint32_t r = (uint32_t)(run % a.runs_per_item);
-    if (!LWE_BOUNDS(e < a.count, 108)) continue;
-    uint32_t s = 0;
-    while (s + 1 < a.nout && r >= a.out[s].runs) {
-      r -= a.out[s].runs;
-      s++;
-    }
-    const NoiseOut o = a.out[s];
-    uint32_t rk[44];
-    const uint4 *rkp = reinterpret_cast<const uint4 *>(a.rk + 44 * (size_t)e);
-#pragma unroll
-    for (int i = 0; i < 11; i++) {
-      const uint4 v = __ldg(rkp + i);
-      rk[4 * i] = v.x;
-      rk[4 * i + 1] = v.y;
-      rk[4 * i + 2] = v.z;
-      rk[4 * i + 3] = v.w;
-    }
-    const uint32_t nblk = (o.nsamples + 7) / 8;
-    uint8_t *base = reinterpret_cast<uint8_t *>(o.base) + (size_t)e * o.item_stride;
-    // a run lies inside one 256-aligned window of counter indices, so the
-    // window's first two AES rounds are computed once (aes_ctr_run)
-    const uint32_t first = r * NOISE_RUN, b0 = first + lane, x0 = (first & 255u) + lane;
-    const AesCtrRun win = aes_ctr_run(tab, rk, o.domain, first);
-    if (first + NOISE_RUN <= nblk) {
-      // full run: two independent blocks in flight per lane
-#pragma unroll
-      for (uint32_t j = 0; j < NOISE_RUN / 32; j += 2) {
-        const uint4 va = aes_ctr_run_block(tab, rk, win, x0 + 32 * j);
-        const uint4 vb = aes_ctr_run_block(tab, rk, win, x0 + 32 * j + 32);
-        noise_store(smem, o, base, b0 + 32 * j, va);
-        noise_store(smem, o, base, b0 + 32 * j + 32, vb);
+  for (uint64_t g = 0; gwarp + nwarps * g < nruns; g += 32) {
+    // window constants of this warp's runs g .. g + 31, one per lane
+    AesCtrRun mine{};
+    {
+      const uint64_t run = gwarp + nwarps * (g + lane);
+      if (run < nruns) {
+        const NoiseRun x = noise_run_of(a, run);
+        if (LWE_BOUNDS(x.e < a.count, 108)) {
+          uint32_t rk[44];
+          noise_load_rk(a, x.e, rk);
+          mine = aes_ctr_run(tab, rk, a.out[x.s].domain, x.r * NOISE_RUN);
+        }
       }
-    } else {
+    }
+    for (uint32_t j = 0; j < 32; j++) {
+      const uint64_t run = gwarp + nwarps * (g + j);
+      if (run >= nruns) break;  // the same for every lane
+      const AesCtrRun win = aes_ctr_run_shfl(mine, j);
+      const NoiseRun x = noise_run_of(a, run);
+      if (!LWE_BOUNDS(x.e < a.count, 108)) continue;
+      const NoiseOut o = a.out[x.s];
+      uint32_t rk[44];
+      noise_load_rk(a, x.e, rk);
+      const uint32_t nblk = (o.nsamples + 7) / 8;
+      uint8_t *base = reinterpret_cast<uint8_t *>(o.base) + (size_t)x.e * o.item_stride;
+      // a run lies inside one 256-aligned window of counter indices, whose
+      // first two AES rounds are in `win`
+      const uint32_t first = x.r * NOISE_RUN, b0 = first + lane, x0 = (first & 255u) + lane;
+      if (first + NOISE_RUN <= nblk) {
+        // full run: two independent blocks in flight per lane
+#pragma unroll
+        for (uint32_t jj = 0; jj < NOISE_RUN / 32; jj += 2) {
+          const uint4 va = aes_ctr_run_block(tab, rk, win, x0 + 32 * jj);
+          const uint4 vb = aes_ctr_run_block(tab, rk, win, x0 + 32 * jj + 32);
+          noise_store(smem, o, base, b0 + 32 * jj, va);
+          noise_store(smem, o, base, b0 + 32 * jj + 32, vb);
+        }
+      } else {
 #pragma unroll 1
-      for (uint32_t b = b0; b < nblk; b += 32)
-        noise_store(smem, o, base, b, aes_ctr_run_block(tab, rk, win, x0 + (b - b0)));
+        for (uint32_t b = b0; b < nblk; b += 32)
+          noise_store(smem, o, base, b, aes_ctr_run_block(tab, rk, win, x0 + (b - b0)));
+      }
     }
   }
 }
@@ -1606,26 +1649,34 @@ __global__ void __launch_bounds__(512, 1) k_probe_aes(uint32_t iters, uint32_t *
 }
 
 // The windowed sequence of k_noise: per lane, NOISE_RUN / 32 blocks of one
-// run (window set up once), two at a time.
+// run, two at a time; the window constants of 32 runs worked out at once
+// (one per lane) and passed by shuffles.
 __global__ void __launch_bounds__(512, 1) k_probe_aes_run(uint32_t iters, uint32_t *sink) {
   extern __shared__ uint32_t sT[];
   aes_fill_smem(sT, g_aes_img);
   __syncthreads();
   const AesTab tab = aes_tab(sT);
   const uint32_t gid = blockIdx.x * blockDim.x + threadIdx.x, lane = threadIdx.x & 31;
-  uint32_t key[4] = {gid, gid * 0x9E3779B9u, ~gid, gid ^ 0x5A5A5A5Au}, rk[44];
+  // one key per warp, as for a run of the noise (the shared window
+  // constants depend on it)
+  const uint32_t wid = gid >> 5;
+  uint32_t key[4] = {wid, wid * 0x9E3779B9u, ~wid, wid ^ 0x5A5A5A5Au}, rk[44];
   aes_key_expand(tab, key, rk);
   uint32_t acc = 0;
-  const uint64_t base = (uint64_t)(gid >> 5) * iters * 32;
-  for (uint32_t b = 0; b < iters; b += NOISE_RUN / 32) {
-    const uint64_t first = base + 32 * (uint64_t)b;
-    const AesCtrRun win = aes_ctr_run(tab, rk, 3, first);
-    const uint32_t x0 = (uint32_t)(first & 255u) + lane;
+  const uint64_t base = (uint64_t)wid * iters * 32;
+  constexpr uint32_t PER = NOISE_RUN / 32;  // blocks per lane and run
+  for (uint32_t g = 0; g < iters; g += 32 * PER) {
+    const AesCtrRun mine = aes_ctr_run(tab, rk, 3, base + 32 * (uint64_t)(g + PER * lane));
+    for (uint32_t jr = 0; jr < 32 && g + PER * jr < iters; jr++) {
+      const uint64_t first = base + 32 * (uint64_t)(g + PER * jr);
+      const AesCtrRun win = aes_ctr_run_shfl(mine, jr);
+      const uint32_t x0 = (uint32_t)(first & 255u) + lane;
 #pragma unroll
-    for (uint32_t j = 0; j < NOISE_RUN / 32; j += 2) {
-      const uint4 v = aes_ctr_run_block(tab, rk, win, x0 + 32 * j);
-      const uint4 w = aes_ctr_run_block(tab, rk, win, x0 + 32 * j + 32);
-      acc ^= v.x ^ v.y ^ v.z ^ v.w ^ w.x ^ w.y ^ w.z ^ w.w;
+      for (uint32_t j = 0; j < PER; j += 2) {
+        const uint4 v = aes_ctr_run_block(tab, rk, win, x0 + 32 * j);
+        const uint4 w = aes_ctr_run_block(tab, rk, win, x0 + 32 * j + 32);
+        acc ^= v.x ^ v.y ^ v.z ^ v.w ^ w.x ^ w.y ^ w.z ^ w.w;
+      }
     }
   }
   sink[gid] = acc;

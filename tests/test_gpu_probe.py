@@ -104,8 +104,10 @@ def _aes_probe_word(gid, iters):
 def _aes_run_probe_word(gid, iters):
     """The windowed probe: thread gid's block i has counter index
     32 (warp iters + i) + lane, so a warp's 32 lanes cover runs of
-    consecutive indices, as a warp of the noise kernel does."""
-    kw = [gid, (gid * 0x9E3779B9) & 0xFFFFFFFF, ~gid & 0xFFFFFFFF, gid ^ 0x5A5A5A5A]
+    consecutive indices, under one key per warp, as a warp of the noise
+    kernel does."""
+    w = gid >> 5
+    kw = [w, (w * 0x9E3779B9) & 0xFFFFFFFF, ~w & 0xFFFFFFFF, w ^ 0x5A5A5A5A]
     key = b"".join(w.to_bytes(4, "little") for w in kw)
     acc = 0
     for i in range(iters):
