@@ -160,7 +160,7 @@ LWE_DEV void noise_store(const char *smem, const NoiseOut &o, uint8_t *base, uin
 // The runs of one warp: warp `gwarp` of `nwarps` takes runs gwarp,
 // gwarp + nwarps, ...  A run's window constants (aes_ctr_run: 27 lookups)
 // are the same for all 32 lanes, so they are worked out for 32 runs at a
-// time, lane l for the warp's run 32 g + l with that run's item key, and
+// time, lane l for the warp's (g + l)-th run with that run's item key, and
 // passed to the whole warp by shuffles when the run comes up: 27 lookup
 // instructions per 32 runs instead of per run.
 struct NoiseRun {
