@@ -145,3 +145,36 @@ def test_long_message_tree_hashes(name, count):
     for i in range(count):
         assert Kb_h[i].tobytes() == O.sha3_256(z + O.htree(bad_h[i].tobytes())), i
     assert ctx.device_error() == 0
+
+
+def test_multi_key_long_public_keys_hashed_by_pointer():
+    """lwe_encaps_multi over 1000 P4096 items with per-item public keys and
+    no precomputed H(pk): the keys' tree hashes (65 chunks each) go through
+    the two-launch schedule by pointer; the results equal those of the same
+    call given each key's stored H(pk), and a sampled item equals the
+    oracle's."""
+    torch.cuda.set_device(0)
+    name, count, nk = "P4096", 1000, 3
+    p, po = params(name)
+    ms = master_seeds(nk, seed=81)
+    ctx = lwe.Ctx(p, max_batch=count)
+    ctx.set_path(lwe.PATH_SKINNY)
+    pk, sk = ctx.empty_pk(nk), ctx.empty_sk(nk)
+    ctx.keygen(dev(ms), pk, sk)
+    keys = np.random.default_rng(82).integers(0, nk, size=count)
+    pk_ptrs = torch.tensor([pk[k].data_ptr() for k in keys], dtype=torch.int64, device="cuda")
+    pkh_ptrs = torch.tensor([sk[k].data_ptr() + 8 * p.n + 32 for k in keys], dtype=torch.int64,
+                            device="cuda")
+    cs = coins(count, seed=83)
+    out = []
+    for give in (None, pkh_ptrs):
+        ct = ctx.empty_ct(count)
+        K = torch.empty((count, 32), dtype=torch.uint8, device="cuda")
+        ctx.encaps_multi(pk_ptrs, dev(cs), ct, K, pkh_ptrs=give)
+        out.append((host(ct), host(K)))
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
+    i = 777
+    pk_o, _ = O.keygen(po, bytes(ms[keys[i]]))
+    ct_o, K_o = O.encaps(po, pk_o, bytes(cs[i]))
+    assert np.array_equal(out[0][0][i], ct_o) and np.array_equal(out[0][1][i], K_o)
+    assert ctx.device_error() == 0
